@@ -1,0 +1,108 @@
+"""Pins of the FP64 warm-start network oracle (oracle/mlp.py): central finite differences
+for every gradient, the GELU derivative, Adam's first-step and convergence properties, the
+NNLS targets against exhaustive enumeration, and the scale invariance of the features."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from oracle import ntf as o
+
+
+def _params(Din, H, Dout, seed=0):
+    rng = np.random.default_rng(seed)
+    return {
+        "W1": rng.standard_normal((H, Din)) / math.sqrt(Din),
+        "b1": rng.standard_normal(H) * 0.1,
+        "W2": rng.standard_normal((H, H)) / math.sqrt(H),
+        "b2": rng.standard_normal(H) * 0.1,
+        "W3": rng.standard_normal((Dout, H)) / math.sqrt(H),
+        "b3": rng.standard_normal(Dout) * 0.1,
+    }
+
+
+def test_gelu_grad_finite_difference():
+    z = np.linspace(-6, 6, 241)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(z), fd, atol=1e-8)
+    # GELU(z) = z * Phi(z): limits
+    assert abs(mlp.gelu(np.array([8.0]))[0] - 8.0) < 1e-12
+    assert abs(mlp.gelu(np.array([-8.0]))[0]) < 1e-12
+
+
+def test_backward_matches_central_differences():
+    R, H = 3, 7
+    Din, Dout = R * R + R, 2 * R
+    p = _params(Din, H, Dout)
+    rng = np.random.default_rng(1)
+    U = rng.standard_normal((5, Din))
+    T = rng.standard_normal((5, Dout))
+    out, cache = mlp.forward(p, U)
+    g = mlp.backward(p, cache, out, T)
+    h = 1e-6
+    for k, P in p.items():
+        flat = P.reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 17)):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = mlp.loss(mlp.forward(p, U)[0], T)
+            flat[idx] = old - h
+            lm = mlp.loss(mlp.forward(p, U)[0], T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(g[k].reshape(-1)[idx] - fd) <= 1e-7 * (1 + abs(fd)), (k, idx)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """With zero moments, bias correction makes the first Adam step lr * g / |g|."""
+    p = {"w": np.array([1.0, -2.0, 3.0])}
+    g = {"w": np.array([0.5, -1e-3, 20.0])}
+    m = {"w": np.zeros(3)}
+    v = {"w": np.zeros(3)}
+    mlp.adam_step(p, g, m, v, 1, lr=0.1, eps=0.0)
+    assert np.allclose(p["w"], [0.9, -1.9, 2.9], rtol=1e-12)
+
+
+def test_adam_minimises_quadratic():
+    rng = np.random.default_rng(2)
+    target = rng.standard_normal(10)
+    p = {"w": np.zeros(10)}
+    m = {"w": np.zeros(10)}
+    v = {"w": np.zeros(10)}
+    for t in range(1, 3001):
+        mlp.adam_step(p, {"w": 2 * (p["w"] - target)}, m, v, t, lr=0.01)
+    assert np.allclose(p["w"], target, atol=1e-3)
+
+
+@pytest.mark.parametrize("R", [3, 6])
+def test_nnls_row_against_exhaustive(R):
+    rng = np.random.default_rng(R)
+    K = rng.random((4 * R, R))
+    G = K.T @ K
+    for _ in range(8):
+        m = rng.standard_normal(R) * np.trace(G) / R
+        x, y = mlp.nnls_row(G, m)
+        assert np.allclose(x, o.nnls_exhaustive(G, m), atol=1e-9)
+        # KKT of eq. (KKT_NTF): y = m - G x <= 0 and y * x = 0
+        assert np.all(y <= 1e-9) and np.all(np.abs(x * y) <= 1e-9)
+
+
+def test_features_are_scale_invariant():
+    rng = np.random.default_rng(4)
+    K = rng.random((12, 4))
+    G = K.T @ K
+    M = rng.standard_normal((3, 4))
+    U1, s1 = mlp.features(G, M)
+    U2, s2 = mlp.features(7.5 * G, 7.5 * M)
+    assert np.allclose(U1, U2) and math.isclose(s2, 7.5 * s1)
+    # the NNLS solution is unchanged and the dual scales with the data
+    x1, y1 = mlp.nnls_row(G, M[0])
+    x2, y2 = mlp.nnls_row(7.5 * G, 7.5 * M[0])
+    assert np.allclose(x1, x2, atol=1e-10) and np.allclose(7.5 * y1, y2, atol=1e-9)
+    T1 = mlp.targets(G, x1[None], y1[None], s1)
+    T2 = mlp.targets(7.5 * G, x2[None], y2[None], s2)
+    assert np.allclose(T1, T2, atol=1e-9)
+    ax, dy = mlp.decode(T1, s1, 4)
+    assert np.allclose(ax[0], x1, atol=1e-12) and np.allclose(dy[0], np.minimum(y1, 0))
