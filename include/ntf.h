@@ -1,0 +1,199 @@
+/*
+ * ntf.h -- C ABI of the GB300 library for ADMoM non-negative CP factorization (NTF).
+ *
+ * Method: Liavas & Sidiropoulos, "Parallel Algorithms for Constrained Tensor Factorization
+ * via Alternating Direction Method of Multipliers" (arXiv 1409.2383).  For an N-way dense
+ * tensor X (N = 3 or 4) and rank R the library computes, per factor n,
+ *
+ *   M_n = X^(n) (Khatri-Rao of the other factors)               Sec. III-A item 1
+ *   G_n = Hadamard product of the other factors' Grams         Sec. III-A item 2
+ *   A   = (M_n + rho At - Y) (G_n + rho I)^{-1}                 eq. (ADMM_NTF_ALS_C)
+ *   At  = (A + Y / rho)_+ ,  Y = Y + rho (A - At)               eq. (ADMoM_NTF)
+ *
+ * the residuals of Sec. III-C, the penalty rule of Sec. III-D and the relative
+ * factorization error of Sec. V-A.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Layout: the tensor is row-major [I_1, ..., I_N] (last index fastest).  Every factor,
+ *   auxiliary, dual and MTTKRP matrix is row-major [I_n, R] FP32.  Gram, coefficient and
+ *   Cholesky matrices are row-major [R, R] FP64.
+ * - Memory: pointers named d_* are device pointers owned by the caller and only borrowed
+ *   for the duration of the call (the tensor: for the life of the context).  The context
+ *   owns its workspace, allocated in ntf_create and freed in ntf_destroy.  Arrays of
+ *   pointers (``const float* const* d_factors``) are host arrays of N device pointers.
+ * - Streams: every call is enqueued on the stream given to ntf_create and returns without
+ *   waiting, except where a host result is returned (stats, rel_err, norms), in which case
+ *   the call synchronizes that stream.
+ * - Errors: a status code; nothing is thrown across the ABI.  Argument errors are detected
+ *   on the host before any launch (NTF_ERR_INVALID_ARG).  Numerical failures found on the
+ *   device (a non-positive Cholesky pivot, a non-finite residual) are recorded in the
+ *   context and returned by the next synchronizing call or by ntf_sync.  ntf_last_error()
+ *   gives a message for the calling thread's most recent failure.  A context stays usable
+ *   after any error.
+ * - Limits: 3 <= N <= 4, 1 <= R <= 64, every I_n >= 1.
+ */
+#ifndef NTF_H
+#define NTF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ntf_ctx ntf_ctx;
+
+typedef enum {
+  NTF_OK = 0,
+  NTF_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unknown mode            */
+  NTF_ERR_CUDA = 2,          /* a CUDA runtime call failed                       */
+  NTF_ERR_OOM = 3,           /* workspace allocation failed                      */
+  NTF_ERR_NOT_SPD = 4,       /* Cholesky of G + rho I met a non-positive pivot   */
+  NTF_ERR_NONFINITE = 5,     /* a residual norm or the fit is NaN / Inf          */
+  NTF_ERR_NOT_CONVERGED = 6, /* ntf_run hit its iteration limit                  */
+  NTF_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up               */
+  NTF_ERR_UNSUPPORTED = 8    /* valid request this build does not implement      */
+} ntf_status;
+
+/* Storage type of the tensor; arithmetic is FP32 accumulation either way. */
+typedef enum { NTF_F32 = 0, NTF_BF16 = 1 } ntf_dtype;
+
+/* Which factors feed the Khatri-Rao products and Grams of the later updates.
+ * PRIMAL: the unconstrained A^{k+1} (eq. ADMM_NTF_ALS_C as printed).
+ * AUX:    the non-negative auxiliaries At^{k+1}. */
+typedef enum { NTF_KR_PRIMAL = 0, NTF_KR_AUX = 1 } ntf_kr_source;
+
+/* ADAPTIVE: rho per factor, adapted once per outer iteration by eq. (varying_penalty_rule).
+ * TRACE:    rho = trace(G_n)/R, recomputed at every factor update.
+ * FIXED:    rho stays at the value set by ntf_set_rho (default rho0). */
+typedef enum { NTF_RHO_ADAPTIVE = 0, NTF_RHO_TRACE = 1, NTF_RHO_FIXED = 2 } ntf_rho_policy;
+
+typedef struct {
+  int inner_iters;   /* L >= 1: update/projection/dual repetitions per factor (paper: 1) */
+  int kr_source;     /* ntf_kr_source                                                    */
+  int rho_policy;    /* ntf_rho_policy                                                   */
+  double rho0;       /* initial penalty (paper: 1)                                       */
+  double mu;         /* penalty rule parameters (paper: 8, 4, 2), Sec. V-A               */
+  double tau_incr;
+  double tau_decr;
+  double eps_abs;    /* stopping tolerances of Sec. III-C (paper: 1e-4, 1e-4)            */
+  double eps_rel;
+} ntf_params;
+
+/* Per-factor residuals of one update (Sec. III-C), all Frobenius norms. */
+typedef struct {
+  double primal_res; /* ||A - At||                                   */
+  double dual_res;   /* rho ||At_after - At_before||                 */
+  double norm_A;
+  double norm_At;
+  double norm_Y;
+  double rho;        /* penalty used by this update                  */
+} ntf_update_stats;
+
+typedef struct {
+  int iters;          /* outer iterations executed                          */
+  int converged;      /* 1 if the residual test held for every factor       */
+  int reached_target; /* 1 if rel_err <= target_rfe was observed            */
+  int reserved;
+  double rel_err;     /* relative error of the auxiliaries at the end       */
+} ntf_run_stats;
+
+/* Fill *p with the paper's settings (paper_mode != 0: L=1, PRIMAL, ADAPTIVE, rho0=1,
+ * mu=8, tau=4/2, eps=1e-4) or with the fixed-penalty inner-loop form (paper_mode == 0:
+ * L=5, AUX, TRACE, same stopping tolerances).  Never fails. */
+void ntf_default_params(ntf_params* p, int paper_mode);
+
+/* Create a context for a tensor of the given order, dims[order] and rank.  d_tensor
+ * (dtype NTF_F32 or NTF_BF16, row-major) must stay valid and unchanged until
+ * ntf_destroy.  stream: a cudaStream_t (NULL = legacy default stream).  Computes ||X||^2
+ * once (synchronizes).  On failure *out is NULL. */
+ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, int dtype,
+                      const void* d_tensor, const ntf_params* p, void* stream);
+
+/* Free the workspace.  Accepts NULL. */
+ntf_status ntf_destroy(ntf_ctx* ctx);
+
+/* ||X||_F^2 of the tensor, FP64 accumulation (computed at creation). */
+ntf_status ntf_tensor_norm2(ntf_ctx* ctx, double* out);
+
+/* MTTKRP of Sec. III-A item 1: d_M[I_mode, R] = X^(mode) (Khatri-Rao of d_factors[m],
+ * m != mode).  Streams the tensor from device memory once.  d_factors[mode] is ignored
+ * (may be NULL). */
+ntf_status ntf_mttkrp(ntf_ctx* ctx, int mode, const float* const* d_factors, float* d_M);
+
+/* Gram F^T F (FP64 accumulation) of factor d_F [I_mode, R]; stored in the context as the
+ * Gram of factor `mode` (used by later ntf_system / ntf_admm_update calls) and, if d_G is
+ * not NULL, also written to d_G [R, R]. */
+ntf_status ntf_gram(ntf_ctx* ctx, int mode, const float* d_F, double* d_G);
+
+/* Coefficient matrix of eq. (ADMM_NTF_ALS_C) from the stored Grams (Sec. III-A item 2):
+ * d_H = Hadamard_{m != mode} Gram_m + rho I and its lower Cholesky factor d_L (each may be
+ * NULL), rho chosen by the penalty policy.  Synchronizes and reports NTF_ERR_NOT_SPD. */
+ntf_status ntf_system(ntf_ctx* ctx, int mode, double* d_H, double* d_L, double* rho_out);
+
+/* One factor update (eq. ADMM_NTF_ALS_C then eq. ADMoM_NTF, repeated inner_iters times,
+ * with the coefficient matrix factored once): reads d_M and the stored Grams, updates
+ * d_A (primal, output only), d_At and d_Y in place, then refreshes the stored Gram of
+ * factor `mode` from the Khatri-Rao source (d_A or d_At) and, under the ADAPTIVE policy,
+ * applies the penalty rule to this factor's rho.  stats (host, may be NULL): residuals of
+ * Sec. III-C; when given, the call synchronizes. */
+ntf_status ntf_admm_update(ntf_ctx* ctx, int mode, const float* d_M, float* d_A, float* d_At,
+                           float* d_Y, ntf_update_stats* stats);
+
+/* Penalty of factor `mode` (used by ADAPTIVE and FIXED policies). */
+ntf_status ntf_set_rho(ntf_ctx* ctx, int mode, double rho);
+ntf_status ntf_get_rho(ntf_ctx* ctx, int mode, double* rho);
+
+/* Relative factorization error ||X - [F_1..F_N]||_F / ||X||_F of Sec. V-A, evaluated as
+ * sqrt(||X||^2 - 2 <M_N, F_N> + 1^T (Hadamard of all Grams) 1) / ||X|| with one MTTKRP of
+ * the last factor (one tensor pass).  Does not touch the stored Grams.  Synchronizes. */
+ntf_status ntf_fit(ntf_ctx* ctx, const float* const* d_factors, double* rel_err);
+
+/* Same, from a last-factor MTTKRP the caller already has (no tensor pass).  Uses the
+ * stored Grams, which must be those of d_F_last and of the factors d_M_last was formed
+ * with.  Synchronizes. */
+ntf_status ntf_fit_from_mttkrp(ntf_ctx* ctx, const float* d_M_last, const float* d_F_last,
+                               double* rel_err);
+
+/* Whole factorization: outer iterations of eq. (ADMoM_NTF) in Gauss-Seidel order starting
+ * from the given state (d_A, d_At, d_Y: host arrays of N device pointers, updated in
+ * place), until the residual test of Sec. III-C holds for every factor (if eps_abs or
+ * eps_rel > 0), rel_err <= target_rfe (if target_rfe > 0, checked every check_every
+ * iterations) or max_outer iterations.  Grams are (re)initialised from the Khatri-Rao
+ * source factors first.  rfe_hist (host, may be NULL, length max_outer) receives the error
+ * after every checked iteration (NaN elsewhere).  Returns NTF_ERR_NOT_CONVERGED if
+ * max_outer was reached without meeting a requested criterion (out is still filled). */
+ntf_status ntf_run(ntf_ctx* ctx, float* const* d_A, float* const* d_At, float* const* d_Y,
+                   int max_outer, double target_rfe, int check_every, double* rfe_hist,
+                   ntf_run_stats* out);
+
+/* Device-time accounting of the two tensor contractions inside ntf_run (the dominant
+ * kernels): CUDA events are recorded around each contraction launch on the context's
+ * stream and read back at every check of ntf_run.  Counters restart at enable. */
+typedef struct {
+  int64_t sweeps;             /* outer iterations run while profiling was on            */
+  int64_t kernel_launches;    /* library kernels launched by those sweeps               */
+  int64_t contractions[2];    /* timed launches: [0] X * KR_right, [1] X^T * KR_left     */
+  double contraction_ms[2];   /* summed device time of those launches, milliseconds     */
+  double contraction_bytes[2];/* tensor bytes each such launch reads (algorithmic)      */
+} ntf_profile;
+
+ntf_status ntf_profile_enable(ntf_ctx* ctx, int enable);
+ntf_status ntf_profile_get(ntf_ctx* ctx, ntf_profile* out);
+
+/* Synchronize the context's stream; return (and clear) a deferred device-side error. */
+ntf_status ntf_sync(ntf_ctx* ctx);
+
+/* FP32 -> BF16 storage conversion (round to nearest even), n elements, on `stream`. */
+ntf_status ntf_to_bf16(const float* d_in, uint16_t* d_out, int64_t n, void* stream);
+
+const char* ntf_status_string(ntf_status s);
+const char* ntf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTF_H */

@@ -115,6 +115,14 @@ def mttkrp(X: np.ndarray, factors: Sequence[np.ndarray], n: int) -> np.ndarray:
     return unfold(np.asarray(X, dtype=np.float64), n) @ kr_others(factors, n)
 
 
+def mttkrp_rows(X: np.ndarray, factors: Sequence[np.ndarray], n: int,
+                rows: Sequence[int]) -> np.ndarray:
+    """Selected rows of M_n: the mode-n slices X[..., i, ...] for i in ``rows`` unfolded and
+    multiplied by the explicit Khatri-Rao matrix (same definition as :func:`mttkrp`)."""
+    Xs = np.take(np.asarray(X), list(rows), axis=n).astype(np.float64)
+    return unfold(Xs, n) @ kr_others(factors, n)
+
+
 def gram(F: np.ndarray) -> np.ndarray:
     """F^T F in FP64."""
     F = np.asarray(F, dtype=np.float64)

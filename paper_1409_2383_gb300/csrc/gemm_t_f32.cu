@@ -1,0 +1,9 @@
+// Instantiation unit: GEMM-T MTTKRP contraction for f32 tensor storage.
+#include "mttkrp_kernels.cuh"
+
+namespace ntf {
+namespace detail {
+template cudaError_t gemm_t_typed<float>(const float*, int64_t, int64_t, int, const Group&,
+                                         const GemmPlan&, float*, cudaStream_t);
+}  // namespace detail
+}  // namespace ntf

@@ -1,0 +1,304 @@
+"""Python binding of the NTF C ABI (include/ntf.h): argument marshalling only.
+
+Every computation runs in ``libntf.so``; this module checks tensor devices, dtypes, shapes
+and contiguity, passes raw device pointers and the current CUDA stream, and turns status
+codes into exceptions.  There is no fallback: if the library is missing or cannot be
+loaded, importing the entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libntf.so")
+
+NTF_F32, NTF_BF16 = 0, 1
+NTF_KR_PRIMAL, NTF_KR_AUX = 0, 1
+NTF_RHO_ADAPTIVE, NTF_RHO_TRACE, NTF_RHO_FIXED = 0, 1, 2
+
+STATUS = {
+    0: "NTF_OK", 1: "NTF_ERR_INVALID_ARG", 2: "NTF_ERR_CUDA", 3: "NTF_ERR_OOM",
+    4: "NTF_ERR_NOT_SPD", 5: "NTF_ERR_NONFINITE", 6: "NTF_ERR_NOT_CONVERGED",
+    7: "NTF_ERR_TIMEOUT", 8: "NTF_ERR_UNSUPPORTED",
+}
+
+
+class NTFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("inner_iters", ctypes.c_int), ("kr_source", ctypes.c_int),
+                ("rho_policy", ctypes.c_int), ("rho0", ctypes.c_double),
+                ("mu", ctypes.c_double), ("tau_incr", ctypes.c_double),
+                ("tau_decr", ctypes.c_double), ("eps_abs", ctypes.c_double),
+                ("eps_rel", ctypes.c_double)]
+
+
+class UpdateStats(ctypes.Structure):
+    _fields_ = [("primal_res", ctypes.c_double), ("dual_res", ctypes.c_double),
+                ("norm_A", ctypes.c_double), ("norm_At", ctypes.c_double),
+                ("norm_Y", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("reached_target", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("rel_err", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("contractions", ctypes.c_int64 * 2), ("contraction_ms", ctypes.c_double * 2),
+                ("contraction_bytes", ctypes.c_double * 2)]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "ntf_default_params": (None, [ctypes.POINTER(Params), ctypes.c_int]),
+    "ntf_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_I64),
+                                  ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(Params), _P]),
+    "ntf_destroy": (ctypes.c_int, [_P]),
+    "ntf_tensor_norm2": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "ntf_mttkrp": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _P]),
+    "ntf_gram": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "ntf_system": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ntf_admm_update": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P,
+                                       ctypes.POINTER(UpdateStats)]),
+    "ntf_set_rho": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "ntf_get_rho": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "ntf_fit": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
+    "ntf_fit_from_mttkrp": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ntf_run": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                               ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(RunStats)]),
+    "ntf_sync": (ctypes.c_int, [_P]),
+    "ntf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ntf_profile_get": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "ntf_to_bf16": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ntf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ntf_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libntf.so (built in-tree by ``paper_1409_2383_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1409_2383_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise NTFError(status, lib().ntf_last_error().decode())
+
+
+def default_params(paper_mode: bool = False, **overrides) -> Params:
+    p = Params()
+    lib().ntf_default_params(ctypes.byref(p), 1 if paper_mode else 0)
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def _ptr_array(ts: Sequence[Optional[torch.Tensor]]):
+    arr = (_P * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t)
+    return arr
+
+
+def _mat(t: torch.Tensor, rows: int, R: int, name: str, dtype=torch.float32) -> None:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != (rows, R) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape ({rows}, {R}); "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
+def to_bf16(x: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """FP32 -> BF16 (round to nearest even) with the library's conversion kernel."""
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("to_bf16 needs a contiguous CUDA float32 tensor")
+    out = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    _check(lib().ntf_to_bf16(_ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)))
+    return out
+
+
+class Context:
+    """One tensor + rank + parameters; wraps ``ntf_ctx``.  Method names follow the ABI."""
+
+    def __init__(self, X: torch.Tensor, rank: int, params: Optional[Params] = None,
+                 stream: Optional[torch.cuda.Stream] = None):
+        if not isinstance(X, torch.Tensor) or not X.is_cuda or not X.is_contiguous():
+            raise ValueError("X must be a contiguous CUDA tensor")
+        if X.dtype == torch.float32:
+            dtype = NTF_F32
+        elif X.dtype == torch.bfloat16:
+            dtype = NTF_BF16
+        else:
+            raise ValueError("X must be float32 or bfloat16")
+        self.X = X  # keeps the borrowed tensor alive
+        self.dims = tuple(int(d) for d in X.shape)
+        self.N = X.dim()
+        self.R = int(rank)
+        self.params = params if params is not None else default_params()
+        self.stream = stream
+        self._h = _P()
+        dims = (_I64 * self.N)(*self.dims)
+        with torch.cuda.device(X.device):
+            _check(lib().ntf_create(ctypes.byref(self._h), self.N, dims, self.R, dtype,
+                                    _ptr(X), ctypes.byref(self.params), _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if self._h:
+            lib().ntf_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- entry points -------------------------------------------------------------
+    def tensor_norm2(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().ntf_tensor_norm2(self._h, ctypes.byref(v)))
+        return v.value
+
+    def _factors(self, F: Sequence[Optional[torch.Tensor]], skip: int = -1):
+        if len(F) != self.N:
+            raise ValueError(f"need {self.N} factors")
+        for m, t in enumerate(F):
+            if m != skip:
+                _mat(t, self.dims[m], self.R, f"factor {m}")
+        return _ptr_array(F)
+
+    def mttkrp(self, mode: int, F: Sequence[Optional[torch.Tensor]],
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.dims[mode], self.R, device=self.X.device)
+        _mat(out, self.dims[mode], self.R, "out")
+        _check(lib().ntf_mttkrp(self._h, mode, self._factors(F, skip=mode), _ptr(out)))
+        return out
+
+    def gram(self, mode: int, F: torch.Tensor, out: Optional[torch.Tensor] = None):
+        _mat(F, self.dims[mode], self.R, "F")
+        if out is not None:
+            _mat(out, self.R, self.R, "out", torch.float64)
+        _check(lib().ntf_gram(self._h, mode, _ptr(F), _ptr(out)))
+        return out
+
+    def system(self, mode: int, H: Optional[torch.Tensor] = None,
+               L: Optional[torch.Tensor] = None) -> float:
+        for t, n in ((H, "H"), (L, "L")):
+            if t is not None:
+                _mat(t, self.R, self.R, n, torch.float64)
+        rho = ctypes.c_double()
+        _check(lib().ntf_system(self._h, mode, _ptr(H), _ptr(L), ctypes.byref(rho)))
+        return rho.value
+
+    def admm_update(self, mode: int, M: torch.Tensor, A: torch.Tensor, At: torch.Tensor,
+                    Y: torch.Tensor, stats: bool = True):
+        for t, n in ((M, "M"), (A, "A"), (At, "At"), (Y, "Y")):
+            _mat(t, self.dims[mode], self.R, n)
+        st = UpdateStats() if stats else None
+        _check(lib().ntf_admm_update(self._h, mode, _ptr(M), _ptr(A), _ptr(At), _ptr(Y),
+                                     ctypes.byref(st) if st is not None else None))
+        if st is None:
+            return None
+        return {k: getattr(st, k) for k, _ in UpdateStats._fields_}
+
+    def set_rho(self, mode: int, rho: float) -> None:
+        _check(lib().ntf_set_rho(self._h, mode, float(rho)))
+
+    def get_rho(self, mode: int) -> float:
+        v = ctypes.c_double()
+        _check(lib().ntf_get_rho(self._h, mode, ctypes.byref(v)))
+        return v.value
+
+    def fit(self, F: Sequence[torch.Tensor]) -> float:
+        v = ctypes.c_double()
+        _check(lib().ntf_fit(self._h, self._factors(F), ctypes.byref(v)))
+        return v.value
+
+    def fit_from_mttkrp(self, M_last: torch.Tensor, F_last: torch.Tensor) -> float:
+        _mat(M_last, self.dims[-1], self.R, "M_last")
+        _mat(F_last, self.dims[-1], self.R, "F_last")
+        v = ctypes.c_double()
+        _check(lib().ntf_fit_from_mttkrp(self._h, _ptr(M_last), _ptr(F_last), ctypes.byref(v)))
+        return v.value
+
+    def run(self, A: Sequence[torch.Tensor], At: Sequence[torch.Tensor],
+            Y: Sequence[torch.Tensor], max_outer: int, target_rfe: float = 0.0,
+            check_every: int = 1, history: bool = False, raise_not_converged: bool = False):
+        """Outer iterations in place on (A, At, Y); returns a dict of run statistics."""
+        pa, pt, py = self._factors(A), self._factors(At), self._factors(Y)
+        hist = (ctypes.c_double * max_outer)() if history else None
+        rs = RunStats()
+        st = lib().ntf_run(self._h, pa, pt, py, int(max_outer), float(target_rfe),
+                           int(check_every), hist, ctypes.byref(rs))
+        if st != 0 and (st != 6 or raise_not_converged):
+            _check(st)
+        out = {k: getattr(rs, k) for k, _ in RunStats._fields_ if k != "reserved"}
+        if history:
+            out["history"] = [hist[i] for i in range(max_outer)]
+        return out
+
+    def sync(self) -> None:
+        _check(lib().ntf_sync(self._h))
+
+    def profile_enable(self, enable: bool = True) -> None:
+        _check(lib().ntf_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_get(self) -> dict:
+        p = Profile()
+        _check(lib().ntf_profile_get(self._h, ctypes.byref(p)))
+        return {"sweeps": p.sweeps, "kernel_launches": p.kernel_launches,
+                "contractions": list(p.contractions), "contraction_ms": list(p.contraction_ms),
+                "contraction_bytes": list(p.contraction_bytes)}
+
+
+def zeros_state(dims: Sequence[int], R: int, device="cuda") -> List[torch.Tensor]:
+    return [torch.zeros(d, R, device=device) for d in dims]
+
+
+__all__ = ["Context", "Params", "NTFError", "default_params", "to_bf16", "lib", "zeros_state",
+           "NTF_F32", "NTF_BF16", "NTF_KR_PRIMAL", "NTF_KR_AUX", "NTF_RHO_ADAPTIVE",
+           "NTF_RHO_TRACE", "NTF_RHO_FIXED", "LIB_PATH"]

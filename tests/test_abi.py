@@ -1,0 +1,73 @@
+"""Host-side checks of the C-ABI library: it builds for sm_103a, loads, exports every entry
+point declared in include/ntf.h, and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1409_2383_gb300 import build, ntf
+    build.build()
+    return ntf.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ntf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ntf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "ntf_create" in names and "ntf_mttkrp" in names and "ntf_admm_update" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_1409_2383_gb300 import ntf
+    assert set(_declared()) == set(ntf._SIGS)
+
+
+def test_default_params(lib):
+    from paper_1409_2383_gb300 import ntf
+    p = ntf.default_params(paper_mode=True)
+    assert (p.inner_iters, p.kr_source, p.rho_policy) == (1, ntf.NTF_KR_PRIMAL, ntf.NTF_RHO_ADAPTIVE)
+    assert (p.rho0, p.mu, p.tau_incr, p.tau_decr, p.eps_abs, p.eps_rel) == (1, 8, 4, 2, 1e-4, 1e-4)
+    q = ntf.default_params(paper_mode=False)
+    assert (q.inner_iters, q.kr_source, q.rho_policy) == (5, ntf.NTF_KR_AUX, ntf.NTF_RHO_TRACE)
+
+
+@pytest.mark.parametrize("order,rank,dtype,ptr", [(5, 3, 0, 16), (2, 3, 0, 16), (3, 0, 0, 16),
+                                                   (3, 65, 0, 16), (3, 3, 7, 16), (3, 3, 0, 0)])
+def test_create_rejects_bad_arguments_before_any_launch(lib, order, rank, dtype, ptr):
+    from paper_1409_2383_gb300 import ntf
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 5)(4, 5, 6, 7, 8)
+    p = ntf.default_params()
+    st = lib.ntf_create(ctypes.byref(h), order, dims, rank, dtype, ptr or None, ctypes.byref(p), None)
+    assert st == 1 and not h.value
+    assert lib.ntf_last_error()
+
+
+def test_create_rejects_bad_params(lib):
+    from paper_1409_2383_gb300 import ntf
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    for bad in (dict(inner_iters=0), dict(rho0=-1.0), dict(mu=1.0, rho_policy=0),
+                dict(kr_source=3), dict(rho_policy=9), dict(eps_abs=-1.0)):
+        p = ntf.default_params(**bad)
+        assert lib.ntf_create(ctypes.byref(h), 3, dims, 3, 0, 16, ctypes.byref(p), None) == 1
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.ntf_destroy(None) == 0
+    assert lib.ntf_sync(None) == 1
+    assert lib.ntf_mttkrp(None, 0, None, None) == 1
+    assert lib.ntf_to_bf16(None, None, 4, None) == 1
+    assert lib.ntf_status_string(4) == b"coefficient matrix not positive definite"

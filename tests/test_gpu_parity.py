@@ -1,0 +1,350 @@
+"""GPU parity of every hot-path step against the FP64 oracle, through the C ABI.
+
+Tolerances: one MTTKRP, Gram or factor update from identical inputs must match the oracle to
+relative Frobenius error <= 1e-5 (FP32 storage and accumulation); Grams, coefficient matrix
+and Cholesky factor (FP64) to 1e-12; the relative factorization error to 1e-4 absolute.
+Sizes span several tiles and ragged tails, both halves of the tensor matricization, both
+storage types, 3- and 4-way tensors, R from 1 to 64, and the unaligned fallback path."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import ntf as o
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ntf():
+    from paper_1409_2383_gb300 import build, ntf as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cuda(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def host(t):
+    return t.detach().float().cpu().numpy() if t.dtype != torch.float64 else t.cpu().numpy()
+
+
+def _problem(dims, R, seed=0, signed=False):
+    rng = np.random.default_rng(seed)
+    X = rng.random(dims).astype(np.float32)
+    if signed:
+        X -= 0.5
+    fs = [rng.random((d, R)).astype(np.float32) for d in dims]
+    return X, fs
+
+
+SHAPES = [
+    ((13, 17, 11), 5),          # odd extents: unaligned fallback path
+    ((24, 40, 36), 7),          # ragged rank, aligned rows
+    ((64, 48, 40), 20),
+    ((1, 5, 8), 3),             # a unit extent
+    ((33, 65, 96), 1),          # rank 1
+    ((70, 30, 40), 64),         # maximum rank
+    ((100, 120, 140), 32),
+    ((60, 70, 80), 50),
+    ((9, 10, 12, 8), 3),        # 4-way
+    ((20, 24, 16, 50), 16),     # 4-way with the short fastest mode of the stress workload
+    ((7, 5, 9, 11), 6),         # 4-way, unaligned
+]
+
+
+@pytest.mark.parametrize("dims,R", SHAPES)
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_mttkrp_all_modes(ntf, dims, R, storage):
+    X, fs = _problem(dims, R, seed=len(dims) * 100 + R, signed=True)
+    if storage == "bf16":
+        Xt = torch.as_tensor(X).to(torch.bfloat16).cuda()
+        Xref = torch.as_tensor(X).to(torch.bfloat16).double().numpy()
+    else:
+        Xt, Xref = cuda(X), X.astype(np.float64)
+    Fd = [cuda(F) for F in fs]
+    with ntf.Context(Xt, R) as ctx:
+        for n in range(len(dims)):
+            M = host(ctx.mttkrp(n, Fd))
+            want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], n)
+            assert rel(M, want) <= TOL, (n, rel(M, want))
+
+
+def test_to_bf16_matches_round_to_nearest_even(ntf):
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(100003) * 10.0 ** rng.integers(-20, 20, 100003)).astype(np.float32)
+    # exact ties of the 16-bit truncation: low half 0x8000 with odd and even high halves
+    ties = np.array([0x3F808000, 0x3F818000, 0xBF808000, 0x40C08000], np.uint32).view(np.float32)
+    x = np.concatenate([x, ties, np.float32([0.0, -0.0, np.inf, -np.inf])])
+    got = ntf.to_bf16(cuda(x)).cpu().view(torch.int16).numpy()
+    want = torch.as_tensor(x).to(torch.bfloat16).view(torch.int16).numpy()
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("dims,R", [((30, 20, 10), 6), ((50, 40, 30, 20), 13), ((1000, 9, 8), 64)])
+def test_gram_and_system(ntf, dims, R):
+    X, fs = _problem(dims, R, seed=7)
+    Fd = [cuda(F) for F in fs]
+    F64 = [F.astype(np.float64) for F in fs]
+    p = ntf.default_params(paper_mode=False)
+    with ntf.Context(cuda(X), R, p) as ctx:
+        for m in range(len(dims)):
+            G = torch.empty(R, R, dtype=torch.float64, device="cuda")
+            ctx.gram(m, Fd[m], G)
+            assert rel(G.cpu().numpy(), o.gram(F64[m])) <= 1e-13
+        for n in range(len(dims)):
+            H = torch.empty(R, R, dtype=torch.float64, device="cuda")
+            L = torch.empty(R, R, dtype=torch.float64, device="cuda")
+            rho = ctx.system(n, H, L)
+            Gn = o.coeff_matrix(F64, n)
+            assert math.isclose(rho, o.rho_trace(Gn), rel_tol=1e-13)
+            Hw = Gn + rho * np.eye(R)
+            assert rel(H.cpu().numpy(), Hw) <= 1e-13
+            assert rel(L.cpu().numpy(), np.linalg.cholesky(Hw)) <= 1e-10
+
+
+def test_system_reports_not_spd(ntf):
+    """Host-side fault injection: a factor corrupted with NaN makes the coefficient matrix
+    non-positive-definite; the status is reported and the context stays usable."""
+    R = 4
+    X, fs = _problem((8, 9, 10), R)
+    p = ntf.default_params(paper_mode=True)
+    with ntf.Context(cuda(X), R, p) as ctx:
+        bad = fs[1].copy()
+        bad[3, 2] = np.nan
+        ctx.gram(0, cuda(fs[0]))
+        ctx.gram(1, cuda(bad))
+        ctx.gram(2, cuda(fs[2]))
+        with pytest.raises(ntf.NTFError) as e:
+            ctx.system(0)
+        assert e.value.status == 4
+        At = torch.ones(8, R, device="cuda")
+        before = At.clone()
+        with pytest.raises(ntf.NTFError):
+            ctx.admm_update(0, torch.ones(8, R, device="cuda"), torch.empty(8, R, device="cuda"),
+                            At, torch.zeros(8, R, device="cuda"))
+        assert torch.equal(At, before)                  # a failed update leaves the state
+        ctx.gram(1, cuda(fs[1]))                        # repaired input: usable again
+        assert ctx.system(0) == 1.0
+
+
+@pytest.mark.parametrize("dims,R,L,policy", [((40, 30, 20), 5, 1, "trace"),
+                                              ((64, 48, 40), 20, 5, "trace"),
+                                              ((90, 30, 20), 50, 5, "trace"),
+                                              ((33, 20, 10), 40, 3, "fixed"),
+                                              ((12, 10, 9, 8), 9, 2, "fixed")])
+def test_admm_update(ntf, dims, R, L, policy):
+    X, fs = _problem(dims, R, seed=11, signed=True)
+    rng = np.random.default_rng(5)
+    F64 = [F.astype(np.float64) for F in fs]
+    pol = ntf.NTF_RHO_TRACE if policy == "trace" else ntf.NTF_RHO_FIXED
+    p = ntf.default_params(inner_iters=L, rho_policy=pol, kr_source=ntf.NTF_KR_AUX)
+    with ntf.Context(cuda(X), R, p) as ctx:
+        for m in range(len(dims)):
+            ctx.gram(m, cuda(fs[m]))
+        for n in range(len(dims)):
+            I = dims[n]
+            M = o.mttkrp(X.astype(np.float64), F64, n).astype(np.float32)
+            At0 = np.maximum(rng.standard_normal((I, R)), 0).astype(np.float32)
+            Y0 = (-np.abs(rng.standard_normal((I, R))) * (At0 == 0)).astype(np.float32)
+            G = o.coeff_matrix(F64, n)
+            rho = o.rho_trace(G) if policy == "trace" else 0.37 * o.rho_trace(G)
+            if policy == "fixed":
+                ctx.set_rho(n, rho)
+            A_d, At_d, Y_d = torch.empty(I, R, device="cuda"), cuda(At0), cuda(Y0)
+            st = ctx.admm_update(n, cuda(M), A_d, At_d, Y_d)
+            A, At, Y, s = o.admm_factor_update(M.astype(np.float64), G, At0.astype(np.float64),
+                                               Y0.astype(np.float64), rho, L)
+            assert rel(host(A_d), A) <= TOL
+            assert rel(host(At_d), At) <= TOL
+            assert rel(host(Y_d), Y) <= TOL
+            assert math.isclose(st["rho"], rho, rel_tol=1e-12)
+            for k in ("primal_res", "dual_res", "norm_A", "norm_At", "norm_Y"):
+                want = getattr(s, k)
+                assert abs(st[k] - want) <= TOL * max(want, s.norm_At), k
+            # the stored Gram of this factor now comes from the new auxiliary factor
+            # (kr_source = aux); check through the next system's coefficient matrix
+            F64[n] = host(At_d).astype(np.float64)
+            ctx.gram(n, At_d)
+
+
+@pytest.mark.parametrize("dims,R", [((30, 40, 50), 4), ((10, 12, 14, 16), 6), ((17, 13, 11), 3)])
+def test_fit(ntf, dims, R):
+    fs = synth.factors(dims, R, 1)
+    X = synth.tensor(fs, 1, snr_db=15.0)
+    G = [np.clip(F + 0.1 * np.random.default_rng(2).standard_normal(F.shape), 0, None)
+         .astype(np.float32) for F in fs]
+    with ntf.Context(cuda(X), R) as ctx:
+        got = ctx.fit([cuda(F) for F in G])
+        want = o.rfe(X.astype(np.float64), [F.astype(np.float64) for F in G])
+        assert abs(got - want) <= 1e-4 * max(want, 1e-2)
+        assert math.isclose(ctx.tensor_norm2(), float(np.sum(X.astype(np.float64) ** 2)),
+                            rel_tol=1e-12)
+
+
+def _run_gpu(ntf, X, init, p, iters, stream=None, paper=False):
+    R = init[0].shape[1]
+    dims = X.shape
+    A = [cuda(F) for F in init]
+    if paper:
+        At = [torch.zeros(d, R, device="cuda") for d in dims]
+    else:
+        At = [cuda(F) for F in init]
+    Y = [torch.zeros(d, R, device="cuda") for d in dims]
+    with ntf.Context(cuda(X), R, p, stream=stream) as ctx:
+        rs = ctx.run(A, At, Y, iters, check_every=1, history=True)
+    torch.cuda.synchronize()
+    return rs, [host(t) for t in A], [host(t) for t in At], [host(t) for t in Y]
+
+
+def test_full_run_matches_oracle_ao_mode(ntf):
+    """50^3, R = 5, 20 dB, 100 outer iterations, L = 5, rho = trace(G)/R, uniform start."""
+    dims, R = (50, 50, 50), 5
+    X, fs, init = synth.workload(dims, R, seed=0, snr_db=20.0)
+    init = [F.astype(np.float32).astype(np.float64) for F in init]
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    rs, A, At, Y = _run_gpu(ntf, X, init, p, 100)
+    params = o.Params(inner_iters=5, kr_source="aux", rho_policy="trace")
+    st, _, _ = o.factorize(X.astype(np.float64), init, params, 100, stop_on_residuals=False,
+                           record_rfe=False)
+    want = o.rfe(X.astype(np.float64), st.aux)
+    assert rs["iters"] == 100
+    assert abs(rs["rel_err"] - want) <= 1e-4
+    assert abs(o.rfe(X.astype(np.float64), [F.astype(np.float64) for F in At]) - want) <= 1e-4
+
+
+def test_full_run_matches_oracle_paper_mode(ntf):
+    """Paper settings: L = 1, primal Khatri-Rao, adaptive rho; first iterations track the
+    oracle closely and the final fit agrees."""
+    dims, R = (30, 30, 30), 3
+    X, fs, init = synth.workload(dims, R, seed=0, snr_db=20.0)
+    init = [F.astype(np.float32).astype(np.float64) for F in init]
+    p = ntf.default_params(paper_mode=True, eps_abs=0.0, eps_rel=0.0)
+    rs, A, At, Y = _run_gpu(ntf, X, init, p, 5, paper=True)
+    st = o.init_state(init, o.PAPER)
+    for _ in range(5):
+        o.outer_iteration(X.astype(np.float64), st, o.PAPER)
+    for n in range(3):
+        assert rel(At[n], st.aux[n]) <= 1e-4
+        assert rel(A[n], st.primal[n]) <= 1e-4
+
+
+def test_graph_replay_is_bitwise_equal_to_eager(ntf):
+    dims, R = (40, 36, 32), 6
+    X, fs, init = synth.workload(dims, R, seed=4, snr_db=20.0)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    s = torch.cuda.Stream()
+    r1 = _run_gpu(ntf, X, init, p, 12)                 # legacy default stream: eager launches
+    with torch.cuda.stream(s):
+        r2 = _run_gpu(ntf, X, init, p, 12, stream=s)   # captured sweep replayed as a graph
+    for a, b in zip(r1[2], r2[2]):
+        assert np.array_equal(a, b)
+    assert r1[0]["history"] == r2[0]["history"]
+
+
+def test_resume_from_saved_state_is_bitwise_equal(ntf):
+    dims, R = (30, 28, 26), 4
+    X, fs, init = synth.workload(dims, R, seed=6, snr_db=20.0)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    full = _run_gpu(ntf, X, init, p, 10)
+    A = [cuda(F) for F in init]
+    At = [cuda(F) for F in init]
+    Y = [torch.zeros(d, R, device="cuda") for d in dims]
+    with ntf.Context(cuda(X), R, p) as ctx:
+        ctx.run(A, At, Y, 4)
+    saved = [[t.clone().cpu() for t in S] for S in (A, At, Y)]
+    A, At, Y = [[t.cuda() for t in S] for S in saved]
+    with ntf.Context(cuda(X), R, p) as ctx:
+        ctx.run(A, At, Y, 6)
+    for a, b in zip(full[2], [host(t) for t in At]):
+        assert np.array_equal(a, b)
+
+
+def test_stopping_rule_and_target(ntf):
+    dims, R = (30, 30, 30), 3
+    X, fs, init = synth.workload(dims, R, seed=0, snr_db=20.0)
+    p = ntf.default_params(paper_mode=False, eps_abs=1e-4, eps_rel=1e-4)
+    rs = _run_gpu(ntf, X, init, p, 400)[0]
+    assert rs["converged"] == 1 and rs["iters"] < 400
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    A = [cuda(F) for F in init]
+    At = [cuda(F) for F in init]
+    Y = [torch.zeros(d, R, device="cuda") for d in dims]
+    with ntf.Context(cuda(X), R, p) as ctx:
+        rs = ctx.run(A, At, Y, 400, target_rfe=0.2)
+    assert rs["reached_target"] == 1 and rs["rel_err"] <= 0.2 and rs["iters"] < 400
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def _sampled_rows(ntf, dims, R, structure="uniform", storage="f32", snr=20.0, nrows=3):
+    X, fs, init = synth.workload(dims, R, seed=0, snr_db=snr, structure=structure)
+    if storage == "bf16":
+        Xd = torch.as_tensor(X).to(torch.bfloat16).cuda()
+        Xh = torch.as_tensor(X).to(torch.bfloat16).float().numpy()
+    else:
+        Xd, Xh = cuda(X), X
+    F = [F.astype(np.float32) for F in init]
+    Fd = [cuda(f) for f in F]
+    rng = np.random.default_rng(1)
+    with ntf.Context(Xd, R) as ctx:
+        for n in range(len(dims)):
+            M = host(ctx.mttkrp(n, Fd))
+            rows = sorted(set(rng.integers(0, dims[n], nrows).tolist()) | {0, dims[n] - 1})
+            want = o.mttkrp_rows(Xh, [f.astype(np.float64) for f in F], n, rows)
+            assert rel(M[rows], want) <= TOL, (n, rel(M[rows], want))
+    del Xd
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_full_size_400_cubed_r20(ntf, storage):
+    _sampled_rows(ntf, (400, 400, 400), 20, storage=storage)
+
+
+def test_full_size_600_cubed_r50_sparse(ntf):
+    _sampled_rows(ntf, (600, 600, 600), 50, structure="sparse")
+
+
+def test_full_size_4way_200x200x200x50_r16_bf16(ntf):
+    _sampled_rows(ntf, (200, 200, 200, 50), 16, structure="collinear", storage="bf16", snr=10.0)
+
+
+def test_profiling_under_graph_replay(ntf):
+    """Contraction timing events recorded inside the captured sweep; no stale error left."""
+    dims, R = (64, 48, 40), 8
+    X, fs, init = synth.workload(dims, R, seed=2, snr_db=20.0)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        A = [cuda(F) for F in init]
+        At = [cuda(F) for F in init]
+        Y = [torch.zeros(d, R, device="cuda") for d in dims]
+        with ntf.Context(cuda(X), R, p, stream=s) as ctx:
+            ctx.run(A, At, Y, 3)                      # records the graph
+            ctx.profile_enable(True)
+            ctx.run(A, At, Y, 6)                      # eager first sweep, then a new graph
+            ctx.run(A, At, Y, 4)                      # graph replays only
+            prof = ctx.profile_get()
+            assert prof["sweeps"] == 10
+            assert prof["contractions"] == [10, 10]
+            assert all(ms > 0 for ms in prof["contraction_ms"])
+            assert prof["contraction_bytes"] == [X.size * 4.0] * 2
+            assert prof["kernel_launches"] >= 10 * 14
+            ctx.profile_enable(False)
+            ctx.run(A, At, Y, 2)                      # back to a graph without events
+            M = ctx.mttkrp(0, At)
+    torch.cuda.synchronize()
+    want = o.mttkrp(X.astype(np.float64), [host(t).astype(np.float64) for t in At], 0)
+    assert rel(host(M), want) <= TOL
