@@ -322,6 +322,26 @@ def run_ntf(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernel_case(args):
+    """Standalone MTTKRP calls on a small-but-larger-than-L2 tensor (for ncu captures):
+    mode 0 runs the X * KR_right contraction, the last mode the X^T * KR_left one."""
+    import torch
+    from paper_1409_2383_gb300 import ntf
+    dims = tuple(int(d) for d in args.dims.split("x"))
+    rng = np.random.default_rng(0)
+    X = torch.as_tensor(rng.random(dims, dtype=np.float32)).cuda()
+    if args.storage == "bf16":
+        X = ntf.to_bf16(X)
+    F = [torch.as_tensor(rng.random((d, args.rank), dtype=np.float32)).cuda() for d in dims]
+    with ntf.Context(X, args.rank) as ctx:
+        for _ in range(args.steps):
+            for n in (0, len(dims) - 1):
+                ctx.mttkrp(n, F)
+        torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.dims, "rank": args.rank, "storage": args.storage,
+                      "calls": 2 * args.steps}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,9 +349,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ntf", choices=["ntf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="standalone MTTKRP calls only (profiling case)")
+    ap.add_argument("--dims", default="384x384x384")
+    ap.add_argument("--rank", type=int, default=RANK)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ntf(args)
