@@ -348,3 +348,8 @@ def test_profiling_under_graph_replay(ntf):
     torch.cuda.synchronize()
     want = o.mttkrp(X.astype(np.float64), [host(t).astype(np.float64) for t in At], 0)
     assert rel(host(M), want) <= TOL
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_full_size_1000_cubed_r32(ntf, storage):
+    _sampled_rows(ntf, (1000, 1000, 1000), 32, storage=storage, snr=30.0, nrows=2)
