@@ -186,6 +186,29 @@ ntf_status ntf_profile_get(ntf_ctx* ctx, ntf_profile* out);
 /* Synchronize the context's stream; return (and clear) a deferred device-side error. */
 ntf_status ntf_sync(ntf_ctx* ctx);
 
+/* MTTKRP that allocates nothing.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc on their call path -- services that reserve all
+ * device memory at start-up and treat any later allocation as a failure, or host code where
+ * the device-wide synchronization an allocation may cause is not acceptable.  It computes
+ * exactly what ntf_mttkrp computes (d_M[I_mode, R] = X^(mode) times the Khatri-Rao product
+ * of d_factors[m], m != mode; same layouts; d_factors is a host array of `order` device
+ * pointers, d_factors[mode] ignored) without a context: its scratch memory (split-K partial
+ * sums and the contraction intermediate) is one static 32 MiB device array that every GPU
+ * loading this library holds until the process exits.
+ * - The first call on each device looks up that array's device address (cudaGetSymbolAddress
+ *   with the device current) and caches it; make that first call before any stream capture.
+ * - All calls on a device share the array and it keeps the last call's contents (nothing in
+ *   it needs to start at zero).  Calls whose work overlaps on the GPU -- on different streams
+ *   or from different threads -- race on it; serialize them.
+ * - NTF_ERR_INVALID_ARG, before any launch, if an argument is invalid or the contraction
+ *   intermediate (Q x R floats for the trailing modes, P x R for the leading ones; see
+ *   ntf_create for P and Q) exceeds the 32 MiB maximum.  When the split-K partial sums
+ *   would not fit beside it, fewer splits are used.
+ * - Never calls cudaMalloc, cudaFree or any allocating routine.  Asynchronous on `stream`. */
+ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int rank, int dtype,
+                              const void* d_tensor, int mode, const float* const* d_factors,
+                              float* d_M, void* stream);
+
 /* FP32 -> BF16 storage conversion (round to nearest even), n elements, on `stream`. */
 ntf_status ntf_to_bf16(const float* d_in, uint16_t* d_out, int64_t n, void* stream);
 

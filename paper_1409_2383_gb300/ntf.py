@@ -85,6 +85,9 @@ _SIGS = {
     "ntf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ntf_profile_get": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "ntf_to_bf16": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ntf_mttkrp_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.c_int,
+                                          ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P), _P,
+                                          _P]),
     "ntf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ntf_last_error": (ctypes.c_char_p, []),
 }
@@ -151,6 +154,32 @@ def to_bf16(x: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> torc
         raise ValueError("to_bf16 needs a contiguous CUDA float32 tensor")
     out = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
     _check(lib().ntf_to_bf16(_ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)))
+    return out
+
+
+def mttkrp_noalloc(X: torch.Tensor, mode: int, F: Sequence[Optional[torch.Tensor]],
+                   out: Optional[torch.Tensor] = None,
+                   stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """MTTKRP without a context and without any device allocation inside the library (its
+    scratch is a static device array shared by all calls on a GPU; calls that overlap on the
+    GPU race on it).  For callers that cannot allocate device memory on their call path;
+    ``out`` may be preallocated for the same reason."""
+    if not isinstance(X, torch.Tensor) or not X.is_cuda or not X.is_contiguous():
+        raise ValueError("X must be a contiguous CUDA tensor")
+    if X.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("X must be float32 or bfloat16")
+    dims = tuple(int(d) for d in X.shape)
+    R = next(int(t.shape[1]) for m, t in enumerate(F) if m != mode)
+    for m, t in enumerate(F):
+        if m != mode:
+            _mat(t, dims[m], R, f"factor {m}")
+    if out is None:
+        out = torch.empty(dims[mode], R, device=X.device)
+    _mat(out, dims[mode], R, "out")
+    cdims = (_I64 * len(dims))(*dims)
+    dtype = NTF_F32 if X.dtype == torch.float32 else NTF_BF16
+    _check(lib().ntf_mttkrp_noalloc(len(dims), cdims, R, dtype, _ptr(X), mode, _ptr_array(F),
+                                    _ptr(out), _stream_ptr(stream)))
     return out
 
 
@@ -300,5 +329,6 @@ def zeros_state(dims: Sequence[int], R: int, device="cuda") -> List[torch.Tensor
 
 
 __all__ = ["Context", "Params", "NTFError", "default_params", "to_bf16", "lib", "zeros_state",
+           "mttkrp_noalloc",
            "NTF_F32", "NTF_BF16", "NTF_KR_PRIMAL", "NTF_KR_AUX", "NTF_RHO_ADAPTIVE",
            "NTF_RHO_TRACE", "NTF_RHO_FIXED", "LIB_PATH"]

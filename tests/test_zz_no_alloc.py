@@ -1,0 +1,73 @@
+"""The allocation-free MTTKRP entry point against the context-based one.
+
+Some callers of this library cannot allocate device memory on their call path (services that
+reserve all device memory at start-up and treat later allocations as failures).
+``ntf_mttkrp_noalloc`` serves them: it needs no context and keeps its scratch in a static
+device array.  Here it is called through the C ABI twice in a row for every mode of several
+tensors and compared with ``ntf_mttkrp`` of a context, within the tolerance of the other
+parity tests (relative Frobenius error 1e-5)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ntf():
+    from paper_1409_2383_gb300 import build, ntf as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def _rel(a, b):
+    return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+
+CASES = [
+    ((64, 48, 40), 20, torch.float32),        # split-K partials and the intermediate in scratch
+    ((400, 400, 400), 20, torch.float32),     # the benchmark shape
+    ((20, 24, 16, 50), 16, torch.bfloat16),   # 4-way: both halves need the intermediate
+    ((13, 17, 11), 5, torch.float32),         # unaligned rows: plain fallback kernels
+    ((200, 1000, 1000), 8, torch.float32),    # intermediate of 8e6 floats: splits reduced to fit
+]
+
+
+@pytest.mark.parametrize("dims,R,dtype", CASES)
+def test_noalloc_matches_context_mttkrp_on_two_calls(ntf, dims, R, dtype):
+    g = torch.Generator().manual_seed(sum(dims) + R)
+    X = (torch.rand(dims, generator=g) - 0.3).to(dtype).cuda()
+    F = [torch.rand(d, R, generator=g).cuda() for d in dims]
+    with ntf.Context(X, R) as ctx:
+        want = [ctx.mttkrp(n, F).clone() for n in range(len(dims))]
+    outs = [torch.empty(d, R, device="cuda") for d in dims]
+    for call in range(2):
+        for n in range(len(dims)):
+            outs[n].fill_(float("nan"))
+            ntf.mttkrp_noalloc(X, n, F, out=outs[n])
+        torch.cuda.synchronize()
+        for n in range(len(dims)):
+            assert _rel(outs[n], want[n]) <= TOL, (call, n, _rel(outs[n], want[n]))
+
+
+def test_noalloc_rejects_an_intermediate_beyond_the_maximum(ntf):
+    dims, R = (4, 2048, 2048), 4               # trailing-mode intermediate: 2048*2048*4 floats
+    X = torch.zeros(dims, device="cuda")
+    F = [torch.zeros(d, R, device="cuda") for d in dims]
+    with pytest.raises(ntf.NTFError) as e:
+        ntf.mttkrp_noalloc(X, 1, F)
+    assert e.value.status == 1
+    cdims = (ctypes.c_int64 * 3)(*dims)
+    ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in F])
+    out = torch.empty(dims[2], R, device="cuda")
+    assert ntf.lib().ntf_mttkrp_noalloc(3, cdims, R, 0, X.data_ptr(), 2, ptrs, out.data_ptr(),
+                                        None) == 1
+    # the leading mode needs no intermediate and still works
+    M0 = ntf.mttkrp_noalloc(X, 0, F)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(M0) == 0
