@@ -178,6 +178,8 @@ typedef struct {
   int64_t contractions[2];    /* timed launches: [0] X * KR_right, [1] X^T * KR_left     */
   double contraction_ms[2];   /* summed device time of those launches, milliseconds     */
   double contraction_bytes[2];/* tensor bytes each such launch reads (algorithmic)      */
+  int64_t ws_rows_considered; /* warm start: rows offered a prediction                  */
+  int64_t ws_rows_accepted;   /* warm start: rows whose prediction the judge kept       */
 } ntf_profile;
 
 ntf_status ntf_profile_enable(ntf_ctx* ctx, int enable);
@@ -185,6 +187,53 @@ ntf_status ntf_profile_get(ntf_ctx* ctx, ntf_profile* out);
 
 /* Synchronize the context's stream; return (and clear) a deferred device-side error. */
 ntf_status ntf_sync(ntf_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper; an addition evaluated against the plain method).
+ * With the other factors fixed each row of a factor solves the non-negative least squares
+ * min_{x >= 0} 1/2 x^T G x - m^T x (G: coefficient matrix of eq. ADMM_NTF_ALS_C without rho,
+ * m: MTTKRP row), whose solution x* and dual y* = m - G x* satisfy eq. (KKT_NTF).  The network
+ * maps [vec(G/s) ; m/s], s = trace(G)/R, to [x* ; y* / s]: layers R^2+R -> H -> H -> 2R with the
+ * exact GELU, BF16 weights in every product (FP32 master copies, FP32 accumulation).
+ * Parameters are one flat FP32 array in the order W1 [H, R^2+R], b1 [H], W2 [H, H], b2 [H],
+ * W3 [2R, H], b3 [2R] (row-major), of ntf_mlp_param_count(R, H) floats.  Batches: `groups`
+ * normalised coefficient matrices d_Gn [groups, R^2] (G/s), CSR offsets d_offsets
+ * [groups + 1] (device ints; the rows of group g are offsets[g] .. offsets[g+1]-1) and
+ * normalised MTTKRP rows d_mrows [rows, R] (m/s); targets [rows, 2R].  All calls run on the
+ * stream given at creation. */
+typedef struct ntf_mlp ntf_mlp;
+
+/* Number of floats in the parameter array (-1 for an invalid rank / width). */
+int64_t ntf_mlp_param_count(int rank, int hidden);
+
+/* Create a network from host parameters (copied); workspaces for up to max_rows rows and
+ * max_groups coefficient matrices per call.  Adam moments start at zero. */
+ntf_status ntf_mlp_create(ntf_mlp** out, int rank, int hidden, const float* h_params,
+                          int max_rows, int max_groups, void* stream);
+ntf_status ntf_mlp_destroy(ntf_mlp* net);
+
+/* Copy the FP32 master parameters to host memory (synchronizes). */
+ntf_status ntf_mlp_get_params(ntf_mlp* net, float* h_params);
+
+/* d_out [rows, 2R] = network output for the batch. */
+ntf_status ntf_mlp_forward(ntf_mlp* net, const float* d_Gn, const int* d_offsets, int groups,
+                           const float* d_mrows, int rows, float* d_out);
+
+/* Mean-squared-error gradient of the batch against d_targets; if apply != 0 one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr).  loss (host, may be NULL: the call
+ * then does not synchronize) receives the batch loss; d_grad_out (device, may be NULL) the
+ * gradient in the parameter layout. */
+ntf_status ntf_mlp_train_step(ntf_mlp* net, const float* d_Gn, const int* d_offsets, int groups,
+                              const float* d_mrows, const float* d_targets, int rows, float lr,
+                              int apply, double* loss, float* d_grad_out);
+const char* ntf_mlp_last_error(void);
+
+/* Use `net` (same rank, max_rows >= the largest tensor extent) to warm-start every factor
+ * update of the context: before the inner iterations each row is offered the network's
+ * (max(0, x), min(0, s y)) and keeps it in place of the carried-over (At, Y) row if its KKT
+ * natural residual ||min(x, G x - m)|| is smaller; the plain iterations then refine either
+ * way.  net = NULL detaches.  The context does not own the network. */
+ntf_status ntf_attach_warmstart(ntf_ctx* ctx, ntf_mlp* net);
 
 /* MTTKRP that allocates nothing.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc on their call path -- services that reserve all
@@ -200,10 +249,11 @@ ntf_status ntf_sync(ntf_ctx* ctx);
  * - All calls on a device share the array and it keeps the last call's contents (nothing in
  *   it needs to start at zero).  Calls whose work overlaps on the GPU -- on different streams
  *   or from different threads -- race on it; serialize them.
- * - NTF_ERR_INVALID_ARG, before any launch, if an argument is invalid or the contraction
- *   intermediate (Q x R floats for the trailing modes, P x R for the leading ones; see
- *   ntf_create for P and Q) exceeds the 32 MiB maximum.  When the split-K partial sums
- *   would not fit beside it, fewer splits are used.
+ * - NTF_ERR_INVALID_ARG, before any launch, if an argument is invalid or if the scratch the
+ *   mode needs exceeds the 32 MiB maximum: the contraction intermediate of the mode's group
+ *   (I_1 I_2 R floats for modes 1-2, I_2 I_3 R floats for mode 3 of a 3-way tensor; I_1 I_2 R
+ *   or I_3 I_4 R floats for a 4-way tensor) plus a Khatri-Rao table of the other group.
+ *   Partial sums that would not fit beside them are avoided by not splitting the contraction.
  * - Never calls cudaMalloc, cudaFree or any allocating routine.  Asynchronous on `stream`. */
 ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int rank, int dtype,
                               const void* d_tensor, int mode, const float* const* d_factors,

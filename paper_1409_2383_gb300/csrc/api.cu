@@ -1,13 +1,15 @@
 // C ABI of the NTF library (include/ntf.h): context management, argument checking, the
 // per-step entry points and the native outer-iteration driver.
 //
-// Tensor passes per outer iteration.  The tensor is handled as X[P, Q] with P = I_1..I_s,
-// Q = I_{s+1}..I_N (s = 1 for N = 3, s = 2 for N = 4).  Factors 1..s are updated from one
-// contraction T_R = X * KR(factors s+1..N), factors s+1..N from one contraction
-// T_L = X^T * KR(factors 1..s).  Gauss-Seidel order (eq. ADMM_NTF_ALS_C) is respected: T_R
-// only involves factors that are not updated before the factors it serves, and T_L is
-// formed after factors 1..s have been updated.  So a sweep reads the tensor twice, whatever
-// N is, and every M_n equals the MTTKRP of its definition up to summation order.
+// Tensor passes per outer iteration.  Factors 1..s_R are updated from one contraction
+// T_R = X[P_R, Q_R] * KR(factors s_R+1..N) (P_R = I_1..I_{s_R}), the remaining factors from
+// one contraction T_L = X[P_L, Q_L]^T * KR(factors 1..s_L) (s_L <= s_R); s_R = 2, s_L = 1 for
+// N = 3 and s_R = s_L = 2 for N = 4, so that each Khatri-Rao operand of a 3-way tensor is a
+// single factor and no contraction range needs splitting.  Gauss-Seidel order (eq.
+// ADMM_NTF_ALS_C) is respected: T_R only involves factors that are not updated before the
+// factors it serves, and T_L only involves factors already updated.  So a sweep reads the
+// tensor twice, whatever N is, and every M_n equals the MTTKRP of its definition up to
+// summation order.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -22,32 +24,45 @@ using ntf::GemmPlan;
 using ntf::Group;
 
 struct ntf_ctx {
-  int N = 0, R = 0, dtype = 0, s = 0, num_sms = 0;
+  int N = 0, R = 0, dtype = 0, num_sms = 0;
+  int s_R = 0, s_L = 0;           // split points of the two contractions
   int64_t dims[ntf::kMaxOrder] = {0, 0, 0, 0};
-  int64_t P = 0, Q = 0, max_dim = 0;
+  int64_t P_R = 0, Q_R = 0, P_L = 0, Q_L = 0, numel = 0, max_dim = 0;
   const void* X = nullptr;
   cudaStream_t st = nullptr;
   ntf_params prm{};
   GemmPlan pn{}, pt{};
   int post_split_left = 1, post_split_right = 1;
   // workspace
-  float* partial = nullptr;      // split-K partials
-  float* TR = nullptr;           // [P, R]
-  float* TL = nullptr;           // [Q, R]
+  float* partial = nullptr;      // partial sums of the first contraction and of the posts
+  float* partial_b = nullptr;    // partial sums of the second contraction (its own stream)
+  float* TR = nullptr;           // [P_R, R]
+  float* TL = nullptr;           // [Q_L, R]
+  float* W = nullptr;            // Khatri-Rao table of the first contraction [K_pad, RP]
+  float* W_b = nullptr;          // Khatri-Rao table of the second contraction
+  // side streams of a sweep: B runs the second contraction, C the coefficient systems
+  cudaStream_t sB = nullptr, sC = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_tl = nullptr, ev_b = nullptr, ev_c = nullptr;
+  cudaEvent_t ev_sys[ntf::kMaxOrder] = {}, ev_rows[ntf::kMaxOrder] = {},
+              ev_red[ntf::kMaxOrder] = {};
   float* Mbuf = nullptr;         // [max_dim, R]
   double* grams = nullptr;       // [N, R, R] stored Grams
   double* grams_tmp = nullptr;   // [N, R, R] for ntf_fit
   double* chol = nullptr;        // [N, R, R]
-  double* norm_part = nullptr;   // [row blocks, 5]
+  double* sys = nullptr;         // per-factor H^{-1} (FP64, FP32) and H (FP32)
+  double* gram_part = nullptr;   // [update blocks, R, R] per-CTA Gram partial sums
+  double* scal_part = nullptr;   // [update blocks, 8] per-CTA residual / fit partial sums
   double* fit_part = nullptr;    // [64]
   double* dpart = nullptr;       // [1024] misc FP64 partials
   Ctrl* d_ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;        // pinned
   double x_norm2 = 0.0;
+  ntf_mlp* ws = nullptr;         // attached warm-start network (not owned)
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[3 * ntf::kMaxOrder] = {};
   int graph_launches = 0;        // kernels in the recorded sweep
   bool graph_prof = false;       // whether the recorded sweep holds profiling events
+  ntf_mlp* graph_ws = nullptr;   // warm-start network recorded in the sweep
   // profiling
   bool prof = false;
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -138,43 +153,45 @@ ntf_status take_status(ntf_ctx* c) {
 // Events around contraction k when profiling (recorded into the graph when capturing).
 // While the stream is being captured the record must become a graph node of its own
 // (external event record), so that every replay records the event.
-ntf_status prof_mark(ntf_ctx* c, int k, int which) {
+ntf_status prof_mark(ntf_ctx* c, int k, int which, cudaStream_t st) {
   if (!c->prof) return NTF_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  NTF_CUDA(cudaStreamIsCapturing(c->st, &cs));
+  NTF_CUDA(cudaStreamIsCapturing(st, &cs));
   if (cs == cudaStreamCaptureStatusActive)
-    NTF_CUDA(cudaEventRecordWithFlags(c->ev[k][which], c->st, cudaEventRecordExternal));
+    NTF_CUDA(cudaEventRecordWithFlags(c->ev[k][which], st, cudaEventRecordExternal));
   else
-    NTF_CUDA(cudaEventRecord(c->ev[k][which], c->st));
+    NTF_CUDA(cudaEventRecord(c->ev[k][which], st));
   if (which == 1) c->ev_pending[k] = true;
   return NTF_OK;
 }
 
-// T_R[P, R] = X * KR(factors s..N-1)
-ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst) {
-  const Group g = make_group(c, c->s, c->N - c->s, F);
-  float* out = c->pn.splits > 1 ? c->partial : dst;
-  NTF_TRY(prof_mark(c, 0, 0));
-  NTF_CUDA(ntf::launch_gemm_n(c->X, c->dtype, c->P, c->Q, c->R, g, c->pn, out, c->st));
-  NTF_TRY(prof_mark(c, 0, 1));
-  c->launches += 1;
-  if (c->pn.splits > 1) {
-    NTF_CUDA(ntf::launch_sum_splits(c->partial, c->pn.splits, c->P * c->R, dst, c->st));
+// T_R[P_R, R] = X[P_R, Q_R] * KR(factors s_R..N-1), on stream st
+ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st) {
+  const Group g = make_group(c, c->s_R, c->N - c->s_R, F);
+  NTF_CUDA(ntf::launch_kr_table(g, c->Q_R, c->R, c->W, st));
+  float* out = c->pn.chunks > 1 ? c->partial : dst;
+  NTF_TRY(prof_mark(c, 0, 0, st));
+  NTF_CUDA(ntf::launch_gemm_n(c->X, c->dtype, c->P_R, c->Q_R, c->R, c->W, c->pn, out, st));
+  NTF_TRY(prof_mark(c, 0, 1, st));
+  c->launches += 2;
+  if (c->pn.chunks > 1) {
+    NTF_CUDA(ntf::launch_sum_splits(c->partial, c->pn.chunks, c->P_R * c->R, dst, st));
     c->launches += 1;
   }
   return NTF_OK;
 }
 
-// T_L[Q, R] = X^T * KR(factors 0..s-1)
-ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst) {
-  const Group g = make_group(c, 0, c->s, F);
-  float* out = c->pt.splits > 1 ? c->partial : dst;
-  NTF_TRY(prof_mark(c, 1, 0));
-  NTF_CUDA(ntf::launch_gemm_t(c->X, c->dtype, c->P, c->Q, c->R, g, c->pt, out, c->st));
-  NTF_TRY(prof_mark(c, 1, 1));
-  c->launches += 1;
-  if (c->pt.splits > 1) {
-    NTF_CUDA(ntf::launch_sum_splits(c->partial, c->pt.splits, c->Q * c->R, dst, c->st));
+// T_L[Q_L, R] = X[P_L, Q_L]^T * KR(factors 0..s_L-1), on stream st
+ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st) {
+  const Group g = make_group(c, 0, c->s_L, F);
+  NTF_CUDA(ntf::launch_kr_table(g, c->P_L, c->R, c->W_b, st));
+  float* out = c->pt.chunks > 1 ? c->partial_b : dst;
+  NTF_TRY(prof_mark(c, 1, 0, st));
+  NTF_CUDA(ntf::launch_gemm_t(c->X, c->dtype, c->P_L, c->Q_L, c->R, c->W_b, c->pt, out, st));
+  NTF_TRY(prof_mark(c, 1, 1, st));
+  c->launches += 2;
+  if (c->pt.chunks > 1) {
+    NTF_CUDA(ntf::launch_sum_splits(c->partial_b, c->pt.chunks, c->Q_L * c->R, dst, st));
     c->launches += 1;
   }
   return NTF_OK;
@@ -196,79 +213,149 @@ void prof_collect(ntf_ctx* c) {
 }
 
 // Second tree level: M of `mode` from the group's contraction T (group of 1 or 2 modes).
-ntf_status finish_mode(ntf_ctx* c, int mode, const float* T, const float* const* F, float* M) {
-  const bool left = mode < c->s;
-  const int first = left ? 0 : c->s;
-  const int count = left ? c->s : c->N - c->s;
+ntf_status finish_mode(ntf_ctx* c, int mode, const float* T, const float* const* F, float* M,
+                       cudaStream_t st) {
+  const bool left = mode < c->s_R;
+  const int first = left ? 0 : c->s_L;
+  const int count = left ? c->s_R : c->N - c->s_L;
   if (count == 1) {
     if (T != M)
       NTF_CUDA(cudaMemcpyAsync(M, T, c->dims[mode] * c->R * sizeof(float),
-                               cudaMemcpyDeviceToDevice, c->st));
+                               cudaMemcpyDeviceToDevice, st));
     return NTF_OK;
   }
   const int64_t Ia = c->dims[first], Ib = c->dims[first + 1];
   if (mode == first) {
-    NTF_CUDA(ntf::launch_post_fast(T, Ia, Ib, c->R, F[first + 1], M, c->st));
+    NTF_CUDA(ntf::launch_post_fast(T, Ia, Ib, c->R, F[first + 1], M, st));
     c->launches += 1;
   } else {
     const int sp = left ? c->post_split_left : c->post_split_right;
-    NTF_CUDA(ntf::launch_post_slow(T, Ia, Ib, c->R, F[first], sp, c->partial, M, c->st));
+    NTF_CUDA(ntf::launch_post_slow(T, Ia, Ib, c->R, F[first], sp, c->partial, M, st));
     c->launches += sp > 1 ? 2 : 1;
   }
   return NTF_OK;
 }
 
-ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float* At, float* Y) {
-  const int64_t I = c->dims[mode];
+ntf::UpdateCall make_call(ntf_ctx* c, int mode, const float* M, float* A, float* At, float* Y,
+                          bool want_fit) {
+  ntf::UpdateCall u{};
   const int R = c->R;
-  double* L = c->chol + static_cast<int64_t>(mode) * R * R;
-  NTF_CUDA(ntf::launch_system(c->grams, c->N, mode, R, c->prm.rho_policy, c->d_ctrl, nullptr, L,
-                              c->st));
-  NTF_CUDA(ntf::launch_admm_rows(M, A, At, Y, L, I, R, c->prm.inner_iters, mode, c->d_ctrl,
-                                 c->norm_part, c->st));
-  NTF_CUDA(ntf::launch_update_finalize(c->norm_part, ntf::admm_row_blocks(I), mode,
-                                       c->prm.rho_policy, c->prm.mu, c->prm.tau_incr,
-                                       c->prm.tau_decr, c->d_ctrl, c->st));
-  const float* src = c->prm.kr_source == NTF_KR_AUX ? At : A;
-  NTF_CUDA(ntf::launch_gram(src, I, R, c->grams + static_cast<int64_t>(mode) * R * R, c->st));
-  c->launches += 4;
+  u.grams = c->grams;
+  u.sys = c->sys;
+  u.M = M;
+  u.A = A;
+  u.At = At;
+  u.Y = Y;
+  u.ctrl = c->d_ctrl;
+  u.gram_part = c->gram_part;
+  u.scal_part = c->scal_part;
+  u.gram_out = c->grams + static_cast<int64_t>(mode) * R * R;
+  u.I = c->dims[mode];
+  u.N = c->N;
+  u.mode = mode;
+  u.R = R;
+  u.inner = c->prm.inner_iters;
+  u.rho_policy = c->prm.rho_policy;
+  u.kr_aux = c->prm.kr_source == NTF_KR_AUX;
+  u.want_fit = want_fit;
+  u.mu = c->prm.mu;
+  u.tau_incr = c->prm.tau_incr;
+  u.tau_decr = c->prm.tau_decr;
+  return u;
+}
+
+ntf_status warm_start(ntf_ctx* c, int mode, const float* M, float* At, float* Y,
+                      cudaStream_t st) {
+  if (!c->ws) return NTF_OK;
+  NTF_CUDA(ntf::mlp_warm_start(c->ws, c->sys, mode, M, At, Y, c->dims[mode],
+                               c->d_ctrl->ws_rows, st));
+  c->launches += 8;
   return NTF_OK;
 }
 
-// One outer iteration in Gauss-Seidel order with two tensor passes, then the fit terms.
+ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float* At, float* Y,
+                          bool want_fit) {
+  const ntf::UpdateCall u = make_call(c, mode, M, A, At, Y, want_fit);
+  NTF_CUDA(ntf::launch_update_system(u, c->st));
+  NTF_TRY(warm_start(c, mode, M, At, Y, c->st));
+  NTF_CUDA(ntf::launch_update_rows(u, c->st));
+  NTF_CUDA(ntf::launch_update_reduce(u, c->st));
+  c->launches += 3;
+  return NTF_OK;
+}
+
+// One outer iteration in Gauss-Seidel order with two tensor passes.  Three streams: the main
+// stream A runs the first contraction and every factor's rows; B builds the first system and
+// then runs the second contraction as soon as the factors it needs are updated; C builds the
+// coefficient systems of the later factors as soon as their Grams are final.  The last
+// factor's update also forms the fit terms.
 ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* const* Y) {
   const float* const* src = c->prm.kr_source == NTF_KR_AUX ? At : A;
-  const float* T = c->s == 1 ? c->Mbuf : c->TR;
-  NTF_TRY(contract_right(c, src, const_cast<float*>(T)));
-  for (int m = 0; m < c->s; ++m) {
-    NTF_TRY(finish_mode(c, m, T, src, c->Mbuf));
-    NTF_TRY(enqueue_update(c, m, c->Mbuf, A[m], At[m], Y[m]));
+  cudaStream_t sa = c->st, sb = c->sB, sc = c->sC;
+  NTF_CUDA(cudaEventRecord(c->ev_start, sa));
+  NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_start, 0));
+  NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_start, 0));
+  NTF_CUDA(ntf::launch_update_system(make_call(c, 0, c->Mbuf, A[0], At[0], Y[0], false), sb));
+  NTF_CUDA(cudaEventRecord(c->ev_sys[0], sb));
+  const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
+  NTF_TRY(contract_right(c, src, const_cast<float*>(T), sa));
+  for (int m = 0; m < c->N; ++m) {
+    const bool left = m < c->s_R;
+    if (m == c->s_R) NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_tl, 0));
+    NTF_TRY(finish_mode(c, m, left ? T : c->TL, src, c->Mbuf, sa));
+    const ntf::UpdateCall u = make_call(c, m, c->Mbuf, A[m], At[m], Y[m], m == c->N - 1);
+    NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_sys[m], 0));
+    NTF_TRY(warm_start(c, m, c->Mbuf, At[m], Y[m], sa));
+    NTF_CUDA(ntf::launch_update_rows(u, sa));
+    NTF_CUDA(cudaEventRecord(c->ev_rows[m], sa));
+    NTF_CUDA(ntf::launch_update_reduce(u, sa));
+    NTF_CUDA(cudaEventRecord(c->ev_red[m], sa));
+    if (m == c->s_L - 1) {
+      NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_rows[m], 0));
+      NTF_TRY(contract_left(c, src, c->TL, sb));
+      NTF_CUDA(cudaEventRecord(c->ev_tl, sb));
+    }
+    if (m + 1 < c->N) {
+      NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_red[m], 0));
+      NTF_CUDA(ntf::launch_update_system(
+          make_call(c, m + 1, c->Mbuf, A[m + 1], At[m + 1], Y[m + 1], false), sc));
+      NTF_CUDA(cudaEventRecord(c->ev_sys[m + 1], sc));
+    }
+    c->launches += 3;
   }
-  NTF_TRY(contract_left(c, src, c->TL));
-  for (int m = c->s; m < c->N; ++m) {
-    NTF_TRY(finish_mode(c, m, c->TL, src, c->Mbuf));
-    NTF_TRY(enqueue_update(c, m, c->Mbuf, A[m], At[m], Y[m]));
-  }
-  NTF_CUDA(ntf::launch_fit(c->Mbuf, src[c->N - 1], c->dims[c->N - 1], c->R, c->grams, c->N,
-                           c->fit_part, c->d_ctrl, c->st));
-  c->launches += 2;
+  NTF_CUDA(cudaEventRecord(c->ev_b, sb));
+  NTF_CUDA(cudaEventRecord(c->ev_c, sc));
+  NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_b, 0));
+  NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_c, 0));
   return NTF_OK;
 }
 
 void free_ctx(ntf_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaEvent_t e : {c->ev_start, c->ev_tl, c->ev_b, c->ev_c})
+    if (e) cudaEventDestroy(e);
+  for (int m = 0; m < ntf::kMaxOrder; ++m)
+    for (cudaEvent_t e : {c->ev_sys[m], c->ev_rows[m], c->ev_red[m]})
+      if (e) cudaEventDestroy(e);
+  if (c->sB) cudaStreamDestroy(c->sB);
+  if (c->sC) cudaStreamDestroy(c->sC);
   for (auto& pair : c->ev)
     for (auto& e : pair)
       if (e) cudaEventDestroy(e);
   cudaFree(c->partial);
   cudaFree(c->TR);
   cudaFree(c->TL);
+  cudaFree(c->W);
+  cudaFree(c->W_b);
+  cudaFree(c->partial_b);
   cudaFree(c->Mbuf);
   cudaFree(c->grams);
   cudaFree(c->grams_tmp);
   cudaFree(c->chol);
-  cudaFree(c->norm_part);
+  cudaFree(c->sys);
+  cudaFree(c->gram_part);
+  cudaFree(c->scal_part);
   cudaFree(c->fit_part);
   cudaFree(c->dpart);
   cudaFree(c->d_ctrl);
@@ -333,16 +420,21 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   c->X = d_tensor;
   c->st = static_cast<cudaStream_t>(stream);
   c->prm = *p;
-  c->s = order / 2;
-  c->P = 1;
-  c->Q = 1;
+  c->s_R = order == 3 ? 2 : 2;
+  c->s_L = order == 3 ? 1 : 2;
+  c->P_R = c->P_L = 1;
+  c->numel = 1;
   for (int m = 0; m < order; ++m) {
     c->dims[m] = dims[m];
     c->max_dim = std::max(c->max_dim, dims[m]);
-    if (m < c->s) c->P *= dims[m];
-    else c->Q *= dims[m];
+    c->numel *= dims[m];
+    if (m < c->s_R) c->P_R *= dims[m];
+    if (m < c->s_L) c->P_L *= dims[m];
   }
-  if (c->P >= (int64_t{1} << 31) || c->Q >= (int64_t{1} << 31)) {
+  c->Q_R = c->numel / c->P_R;
+  c->Q_L = c->numel / c->P_L;
+  if (c->P_R >= (int64_t{1} << 31) || c->Q_R >= (int64_t{1} << 31) ||
+      c->P_L >= (int64_t{1} << 31) || c->Q_L >= (int64_t{1} << 31)) {
     delete c;
     return fail(NTF_ERR_UNSUPPORTED, "tensor halves must each have < 2^31 entries");
   }
@@ -354,33 +446,49 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     return fail(NTF_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
   }
   const int R = rank;
-  c->pn = ntf::plan_gemm_n(c->P, c->Q, R, dtype, d_tensor, c->num_sms);
-  c->pt = ntf::plan_gemm_t(c->P, c->Q, R, dtype, d_tensor, c->num_sms);
-  int64_t part = 0;
-  if (c->pn.splits > 1) part = std::max<int64_t>(part, c->pn.splits * c->P * R);
-  if (c->pt.splits > 1) part = std::max<int64_t>(part, c->pt.splits * c->Q * R);
-  if (c->s == 2) {
+  c->pn = ntf::plan_gemm_n(c->P_R, c->Q_R, dtype, d_tensor, c->num_sms);
+  c->pt = ntf::plan_gemm_t(c->P_L, c->Q_L, dtype, d_tensor, c->num_sms);
+  int64_t part = 0, part_b = 0;
+  if (c->pn.chunks > 1) part = std::max<int64_t>(part, c->pn.chunks * c->P_R * R);
+  if (c->pt.chunks > 1) part_b = c->pt.chunks * c->Q_L * R;
+  if (c->s_R == 2) {
     c->post_split_left = ntf::post_slow_splits(dims[0], dims[1], R, c->num_sms);
     part = std::max<int64_t>(part, c->post_split_left * dims[1] * R);
   }
-  if (order - c->s == 2) {
-    c->post_split_right = ntf::post_slow_splits(dims[c->s], dims[c->s + 1], R, c->num_sms);
-    part = std::max<int64_t>(part, c->post_split_right * dims[c->s + 1] * R);
+  if (order - c->s_L == 2) {
+    c->post_split_right = ntf::post_slow_splits(dims[c->s_L], dims[c->s_L + 1], R, c->num_sms);
+    part = std::max<int64_t>(part, c->post_split_right * dims[c->s_L + 1] * R);
   }
+  const int64_t w_rows = ntf::kr_rows_padded(c->Q_R), w_rows_b = ntf::kr_rows_padded(c->P_L);
   const int64_t RR = static_cast<int64_t>(R) * R;
-  const int row_blocks = ntf::admm_row_blocks(c->max_dim);
+  const int upd_blocks = ntf::update_blocks(c->max_dim);
   auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
     return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
   };
   e = cudaSuccess;
   if (e == cudaSuccess) e = alloc((void**)&c->partial, part * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->TR, c->P * R * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->TL, c->Q * R * sizeof(float));
+  if (e == cudaSuccess) e = alloc((void**)&c->TR, c->P_R * R * sizeof(float));
+  if (e == cudaSuccess) e = alloc((void**)&c->TL, c->Q_L * R * sizeof(float));
+  if (e == cudaSuccess) e = alloc((void**)&c->W, w_rows * ntf::round_rp(R) * sizeof(float));
+  if (e == cudaSuccess) e = alloc((void**)&c->W_b, w_rows_b * ntf::round_rp(R) * sizeof(float));
+  if (e == cudaSuccess) e = alloc((void**)&c->partial_b, part_b * sizeof(float));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sC, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&c->ev_start, &c->ev_tl, &c->ev_b, &c->ev_c})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  for (int m = 0; m < order && e == cudaSuccess; ++m) {
+    e = cudaEventCreateWithFlags(&c->ev_sys[m], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_rows[m], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red[m], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = alloc((void**)&c->Mbuf, c->max_dim * R * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->grams, order * RR * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->grams_tmp, order * RR * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->chol, order * RR * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->norm_part, row_blocks * 5 * sizeof(double));
+  if (e == cudaSuccess) e = alloc((void**)&c->sys, ntf::update_sys_bytes(order, R));
+  if (e == cudaSuccess) e = alloc((void**)&c->gram_part, upd_blocks * RR * sizeof(double));
+  if (e == cudaSuccess)
+    e = alloc((void**)&c->scal_part, upd_blocks * ntf::update_scalars() * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->fit_part, 64 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->dpart, 1024 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->d_ctrl, sizeof(Ctrl));
@@ -394,9 +502,8 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   for (int m = 0; m < order; ++m) c->h_ctrl->rho[m] = p->rho0;
   e = cudaMemcpyAsync(c->d_ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->grams, 0, order * RR * sizeof(double), c->st);
-  int64_t numel = c->P * c->Q;
   if (e == cudaSuccess)
-    e = ntf::launch_norm2(d_tensor, dtype, numel, c->dpart, 1024, &c->d_ctrl->x_norm2, c->st);
+    e = ntf::launch_norm2(d_tensor, dtype, c->numel, c->dpart, 1024, &c->d_ctrl->x_norm2, c->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&c->x_norm2, &c->d_ctrl->x_norm2, sizeof(double), cudaMemcpyDeviceToHost,
                         c->st);
@@ -429,13 +536,13 @@ ntf_status ntf_mttkrp(ntf_ctx* c, int mode, const float* const* F, float* d_M) {
   if (!F || !d_M) return fail(NTF_ERR_INVALID_ARG, "null factors or output");
   for (int m = 0; m < c->N; ++m)
     if (m != mode && !F[m]) return fail(NTF_ERR_INVALID_ARG, "null factor %d", m);
-  if (mode < c->s) {
-    float* T = c->s == 1 ? d_M : c->TR;
-    NTF_TRY(contract_right(c, F, T));
-    NTF_TRY(finish_mode(c, mode, T, F, d_M));
+  if (mode < c->s_R) {
+    float* T = c->s_R == 1 ? d_M : c->TR;
+    NTF_TRY(contract_right(c, F, T, c->st));
+    NTF_TRY(finish_mode(c, mode, T, F, d_M, c->st));
   } else {
-    NTF_TRY(contract_left(c, F, c->TL));
-    NTF_TRY(finish_mode(c, mode, c->TL, F, d_M));
+    NTF_TRY(contract_left(c, F, c->TL, c->st));
+    NTF_TRY(finish_mode(c, mode, c->TL, F, d_M, c->st));
   }
   return NTF_OK;
 }
@@ -469,7 +576,7 @@ ntf_status ntf_admm_update(ntf_ctx* c, int mode, const float* d_M, float* d_A, f
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's
   NTF_TRY(check_mode(c, mode));
   if (!d_M || !d_A || !d_At || !d_Y) return fail(NTF_ERR_INVALID_ARG, "null matrix argument");
-  NTF_TRY(enqueue_update(c, mode, d_M, d_A, d_At, d_Y));
+  NTF_TRY(enqueue_update(c, mode, d_M, d_A, d_At, d_Y, false));
   if (!stats) return NTF_OK;
   NTF_TRY(read_ctrl(c));
   const double* s = c->h_ctrl->stats[mode];
@@ -537,16 +644,31 @@ ntf_status ntf_profile_enable(ntf_ctx* c, int enable) {
   c->pr = ntf_profile{};
   c->ev_pending[0] = c->ev_pending[1] = false;
   c->launches = 0;
+  NTF_CUDA(cudaMemsetAsync(c->d_ctrl->ws_rows, 0, sizeof(c->d_ctrl->ws_rows), c->st));
   const double esize = c->dtype == NTF_BF16 ? 2.0 : 4.0;
-  c->pr.contraction_bytes[0] = c->pr.contraction_bytes[1] =
-      static_cast<double>(c->P) * static_cast<double>(c->Q) * esize;
+  c->pr.contraction_bytes[0] = c->pr.contraction_bytes[1] = static_cast<double>(c->numel) * esize;
   return NTF_OK;
 }
 
 ntf_status ntf_profile_get(ntf_ctx* c, ntf_profile* out) {
   if (!c || !out) return fail(NTF_ERR_INVALID_ARG, "null argument");
+  NTF_TRY(read_ctrl(c));
   *out = c->pr;
   out->kernel_launches = c->launches;
+  out->ws_rows_considered = static_cast<int64_t>(c->h_ctrl->ws_rows[0]);
+  out->ws_rows_accepted = static_cast<int64_t>(c->h_ctrl->ws_rows[1]);
+  return NTF_OK;
+}
+
+ntf_status ntf_attach_warmstart(ntf_ctx* c, ntf_mlp* net) {
+  if (!c) return fail(NTF_ERR_INVALID_ARG, "null context");
+  if (net && ntf::mlp_rank(net) != c->R)
+    return fail(NTF_ERR_INVALID_ARG, "network rank %d differs from the context rank %d",
+                ntf::mlp_rank(net), c->R);
+  if (net && ntf::mlp_max_rows(net) < c->max_dim)
+    return fail(NTF_ERR_INVALID_ARG, "network workspace (%d rows) smaller than a factor (%lld)",
+                ntf::mlp_max_rows(net), static_cast<long long>(c->max_dim));
+  c->ws = net;
   return NTF_OK;
 }
 
@@ -575,7 +697,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
 
   // The sweep is recorded once as a CUDA graph (after one eager sweep has set every kernel
   // attribute) and replayed; it is re-recorded only if the state pointers change.
-  bool same = c->graph != nullptr && c->graph_prof == c->prof;
+  bool same = c->graph != nullptr && c->graph_prof == c->prof && c->graph_ws == c->ws;
   for (int m = 0; m < c->N && same; ++m)
     same = c->graph_key[3 * m] == A[m] && c->graph_key[3 * m + 1] == At[m] &&
            c->graph_key[3 * m + 2] == Y[m];
@@ -608,11 +730,19 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
       if (!ok) {
         (void)cudaGetLastError();
         if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaEvent_t e : {c->ev_start, c->ev_tl, c->ev_b, c->ev_c})
+    if (e) cudaEventDestroy(e);
+  for (int m = 0; m < ntf::kMaxOrder; ++m)
+    for (cudaEvent_t e : {c->ev_sys[m], c->ev_rows[m], c->ev_red[m]})
+      if (e) cudaEventDestroy(e);
+  if (c->sB) cudaStreamDestroy(c->sB);
+  if (c->sC) cudaStreamDestroy(c->sC);
         c->graph = nullptr;
         can_graph = false;
         NTF_TRY(enqueue_sweep(c, A, At, Y));
       } else {
         c->graph_prof = c->prof;
+        c->graph_ws = c->ws;
         for (int m = 0; m < c->N; ++m) {
           c->graph_key[3 * m] = A[m];
           c->graph_key[3 * m + 1] = At[m];

@@ -3,7 +3,7 @@
 
 namespace ntf {
 namespace detail {
-template cudaError_t gemm_t_typed<float>(const float*, int64_t, int64_t, int, const Group&,
+template cudaError_t gemm_t_typed<float>(const float*, int64_t, int64_t, int, const float*,
                                          const GemmPlan&, float*, cudaStream_t);
 }  // namespace detail
 }  // namespace ntf

@@ -1,0 +1,412 @@
+// Warm-start network for the per-row non-negative least squares of a factor update.
+//
+// With the other factors fixed, every row of the factor solves min_{x >= 0} 1/2 x^T G x - m^T x
+// (G: coefficient matrix of eq. ADMM_NTF_ALS_C without rho, m: MTTKRP row); ADMoM converges to
+// x* with dual y* = m - G x* (eq. KKT_NTF).  The network maps [vec(G/s) ; m/s], s = trace(G)/R,
+// to [x* ; y*/s] (the problem is invariant under (G, m) -> (cG, cm) with x* fixed and y*
+// scaled by c).  Layers: R^2+R -> H -> H -> 2R, exact GELU, BF16 weights in the products with
+// FP32 master copies and FP32 accumulation everywhere.  The first layer is split
+// W1 = [W1_G | W1_m]: W1_G vec(G/s) is formed once per coefficient matrix and shared by all
+// of its rows.  Training: mean squared error, Adam (Kingma & Ba).  All reductions run in a
+// fixed order.
+#include <cmath>
+#include <cstdint>
+
+#include "ntf_internal.cuh"
+
+namespace ntf {
+namespace {
+
+// ------------------------------------------------------------------------ GEMM
+// C[M, N] = op(A)[M, K] * op(B)[K, N] (+ bias[N]) (+ C if accumulate), FP32 accumulation.
+// TA: A is stored [K, M] (else [M, K]); TB: B is stored [N, K] (else [K, N]).  64 x 64 tiles,
+// 16-deep K slices through shared memory, 4 x 4 outputs per thread.
+template <typename T>
+__device__ __forceinline__ float to_f(T v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <bool TA, bool TB, typename TBt>
+__global__ void __launch_bounds__(256)
+    k_gemm(int M, int N, int K, const float* __restrict__ A, int lda, const TBt* __restrict__ B,
+           int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias, int accumulate) {
+  __shared__ float As[16][65];
+  __shared__ float Bs[16][65];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+      const int kk = idx / 64, mm = idx % 64;
+      const int gm = m0 + mm, gk = k0 + kk;
+      float a = 0.0f;
+      if (gm < M && gk < K) a = TA ? A[static_cast<int64_t>(gk) * lda + gm] : A[static_cast<int64_t>(gm) * lda + gk];
+      As[kk][mm] = a;
+      const int gn = n0 + mm;
+      float b = 0.0f;
+      if (gn < N && gk < K)
+        b = TB ? to_f<TBt>(B[static_cast<int64_t>(gn) * ldb + gk]) : to_f<TBt>(B[static_cast<int64_t>(gk) * ldb + gn]);
+      Bs[kk][mm] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      float v = acc[i][j];
+      if (bias) v += bias[gn];
+      float* c = C + static_cast<int64_t>(gm) * ldc + gn;
+      *c = accumulate ? *c + v : v;
+    }
+  }
+}
+
+template <bool TA, bool TB, typename TBt>
+cudaError_t gemm(int M, int N, int K, const float* A, int lda, const TBt* B, int ldb, float* C,
+                 int ldc, const float* bias, bool accumulate, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  k_gemm<TA, TB, TBt><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias,
+                                            accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- elementwise
+__device__ __forceinline__ float gelu(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+  const float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
+  return cdf + z * pdf;
+}
+
+__global__ void k_gelu(const float* __restrict__ z, float* __restrict__ h, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    h[i] = gelu(z[i]);
+}
+
+__global__ void k_gelu_back(const float* __restrict__ z, float* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    d[i] *= gelu_grad(z[i]);
+}
+
+// z1[i, :] += hG[group(i), :] + b1, group given by CSR offsets (rows of a group contiguous)
+__global__ void k_first_layer_add(float* __restrict__ z1, const float* __restrict__ hG,
+                                  const float* __restrict__ b1, const int* __restrict__ row_group,
+                                  int rows, int H) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < static_cast<int64_t>(rows) * H; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i / H), h = static_cast<int>(i % H);
+    z1[i] += hG[static_cast<int64_t>(row_group[r]) * H + h] + b1[h];
+  }
+}
+
+// d_out = 2 (out - T) / (rows * D); per-block partial sums of the squared error
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ T,
+                      float* __restrict__ d, int64_t n, double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const float scale = 2.0f / static_cast<float>(n);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float e = out[i] - T[i];
+    d[i] = scale * e;
+    s += static_cast<double>(e) * e;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int n, double scale,
+                            double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s * scale;
+  }
+}
+
+// out[seg, c] = sum over rows of segment seg (CSR offsets) of X[row, c]  (fixed order)
+__global__ void k_segment_sum(const float* __restrict__ X, const int* __restrict__ offs,
+                              int nseg, int cols, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < static_cast<int64_t>(nseg) * cols; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int sgi = static_cast<int>(i / cols), c = static_cast<int>(i % cols);
+    float s = 0.0f;
+    for (int r = offs[sgi]; r < offs[sgi + 1]; ++r) s += X[static_cast<int64_t>(r) * cols + c];
+    out[i] = s;
+  }
+}
+
+// Adam (bias-corrected moments), FP32 master weights, refreshed BF16 copies (weights only).
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, __nv_bfloat16* __restrict__ pb, int64_t n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = w;
+    if (pb) pb[i] = __float2bfloat16_rn(w);
+  }
+}
+
+// row_group[r] = g for offs[g] <= r < offs[g + 1]
+__global__ void k_row_groups(const int* __restrict__ offs, int groups, int* __restrict__ rg) {
+  for (int g = blockIdx.x; g < groups; g += gridDim.x)
+    for (int r = offs[g] + threadIdx.x; r < offs[g + 1]; r += blockDim.x) rg[r] = g;
+}
+
+__global__ void k_to_bf16_copy(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                               int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[i] = __float2bfloat16_rn(in[i]);
+}
+
+unsigned blocks_for(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return static_cast<unsigned>(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- host side
+MlpShape mlp_shape(int R, int H) {
+  MlpShape s{};
+  s.R = R;
+  s.H = H;
+  s.Din = R * R + R;
+  s.Dout = 2 * R;
+  s.oW1 = 0;
+  s.ob1 = s.oW1 + static_cast<int64_t>(H) * s.Din;
+  s.oW2 = s.ob1 + H;
+  s.ob2 = s.oW2 + static_cast<int64_t>(H) * H;
+  s.oW3 = s.ob2 + H;
+  s.ob3 = s.oW3 + static_cast<int64_t>(s.Dout) * H;
+  s.count = s.ob3 + s.Dout;
+  return s;
+}
+
+// Forward for `rows` rows given per-group first-layer terms hG [groups, H] (already W1_G
+// vec(G/s)), row_group[rows] and the normalised MTTKRP rows mrows [rows, R].  Work buffers:
+// z1, h1, z2, h2 [rows, H], out [rows, Dout].
+cudaError_t mlp_forward_rows(const MlpShape& s, const float* p, const __nv_bfloat16* pb,
+                             const float* hG, const int* row_group, const float* mrows, int rows,
+                             float* z1, float* h1, float* z2, float* h2, float* out,
+                             cudaStream_t st) {
+  const int H = s.H, R = s.R;
+  // z1 = mrows W1_m^T (columns R^2 .. R^2+R-1 of W1), then + hG[group] + b1
+  cudaError_t e = gemm<false, true, __nv_bfloat16>(rows, H, R, mrows, R, pb + s.oW1 + R * R,
+                                                   s.Din, z1, H, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  k_first_layer_add<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(
+      z1, hG, p + s.ob1, row_group, rows, H);
+  k_gelu<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(z1, h1, static_cast<int64_t>(rows) * H);
+  e = gemm<false, true, __nv_bfloat16>(rows, H, H, h1, H, pb + s.oW2, H, z2, H, p + s.ob2, false, st);
+  if (e != cudaSuccess) return e;
+  k_gelu<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(z2, h2, static_cast<int64_t>(rows) * H);
+  e = gemm<false, true, __nv_bfloat16>(rows, s.Dout, H, h2, H, pb + s.oW3, H, out, s.Dout,
+                                       p + s.ob3, false, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// hG[g, :] = W1_G vec(Gn[g])  for `groups` normalised coefficient matrices Gn [groups, R^2]
+cudaError_t mlp_group_terms(const MlpShape& s, const __nv_bfloat16* pb, const float* Gn,
+                            int groups, float* hG, cudaStream_t st) {
+  return gemm<false, true, __nv_bfloat16>(groups, s.H, s.R * s.R, Gn, s.R * s.R, pb + s.oW1,
+                                          s.Din, hG, s.H, nullptr, false, st);
+}
+
+// Gradients of the mean squared error for one batch (rows sorted by group, CSR offsets
+// offs[groups + 1]); writes grad [count] and the loss.  Expects the forward buffers filled.
+cudaError_t mlp_backward(const MlpShape& s, const __nv_bfloat16* pb, const float* Gn,
+                         const int* offs, int groups, const int* all_offs, const float* mrows,
+                         int rows,
+                         const float* T, const float* z1, const float* h1, const float* z2,
+                         const float* h2, const float* out, float* d_out, float* d_h2,
+                         float* d_h1, float* gsum, float* grad, double* loss_part,
+                         double* loss, cudaStream_t st) {
+  const int H = s.H, R = s.R, D = s.Dout;
+  const int64_t n_out = static_cast<int64_t>(rows) * D;
+  const unsigned lb = blocks_for(n_out) > 64 ? 64 : blocks_for(n_out);
+  k_mse<<<lb, 256, 0, st>>>(out, T, d_out, n_out, loss_part);
+  k_sum_parts<<<1, 32, 0, st>>>(loss_part, static_cast<int>(lb), 1.0 / static_cast<double>(n_out), loss);
+  // layer 3: dW3 = d_out^T h2, db3 = colsum(d_out), d_h2 = d_out W3
+  cudaError_t e = gemm<true, false, float>(D, H, rows, d_out, D, h2, H, grad + s.oW3, H, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  e = gemm<false, false, __nv_bfloat16>(rows, H, D, d_out, D, pb + s.oW3, H, d_h2, H, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  k_gelu_back<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(z2, d_h2, static_cast<int64_t>(rows) * H);
+  // layer 2 (d_h2 now holds dz2)
+  e = gemm<true, false, float>(H, H, rows, d_h2, H, h1, H, grad + s.oW2, H, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  e = gemm<false, false, __nv_bfloat16>(rows, H, H, d_h2, H, pb + s.oW2, H, d_h1, H, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  k_gelu_back<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(z1, d_h1, static_cast<int64_t>(rows) * H);
+  // layer 1 (d_h1 holds dz1): dW1_m = dz1^T mrows into columns R^2.., dW1_G = gsum^T Gn
+  e = gemm<true, false, float>(H, R, rows, d_h1, H, mrows, R, grad + s.oW1 + R * R, s.Din, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  k_segment_sum<<<blocks_for(static_cast<int64_t>(groups) * H), 256, 0, st>>>(d_h1, offs, groups, H, gsum);
+  e = gemm<true, false, float>(H, R * R, groups, gsum, H, Gn, R * R, grad + s.oW1, s.Din, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  // biases: column sums over all rows (all_offs = {0, rows}: one segment)
+  k_segment_sum<<<blocks_for(D), 256, 0, st>>>(d_out, all_offs, 1, D, grad + s.ob3);
+  k_segment_sum<<<blocks_for(H), 256, 0, st>>>(d_h2, all_offs, 1, H, grad + s.ob2);
+  k_segment_sum<<<blocks_for(H), 256, 0, st>>>(d_h1, all_offs, 1, H, grad + s.ob1);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(const MlpShape& s, float* p, const float* grad, float* m, float* v,
+                     __nv_bfloat16* pb, float lr, int step, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.0f - powf(b1, static_cast<float>(step));
+  const float c2 = 1.0f - powf(b2, static_cast<float>(step));
+  k_adam<<<blocks_for(s.count), 256, 0, st>>>(p, grad, m, v, pb, s.count, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_row_groups(const int* offs, int groups, int* row_group, cudaStream_t st) {
+  k_row_groups<<<groups < 1024 ? (groups > 0 ? groups : 1) : 1024, 128, 0, st>>>(offs, groups, row_group);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_refresh_bf16(const MlpShape& s, const float* p, __nv_bfloat16* pb, cudaStream_t st) {
+  k_to_bf16_copy<<<blocks_for(s.count), 256, 0, st>>>(p, pb, s.count);
+  return cudaGetLastError();
+}
+
+}  // namespace ntf
+
+// --------------------------------------------------------------------- warm start
+namespace ntf {
+namespace {
+
+// Gn = G / s and mrows = M / s with s = trace(G) / R (G: FP32 coefficient matrix, no rho).
+__global__ void k_ws_prepare(const float* __restrict__ G, const float* __restrict__ M, int R,
+                             int64_t I, float* __restrict__ Gn, float* __restrict__ mrows,
+                             float* __restrict__ s_out) {
+  float tr = 0.0f;
+  for (int i = 0; i < R; ++i) tr += G[i * R + i];
+  const float s = tr / R, inv = 1.0f / s;
+  const int64_t nG = static_cast<int64_t>(R) * R, nM = I * R;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < nG + nM;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (i < nG) Gn[i] = G[i] * inv;
+    else mrows[i - nG] = M[i - nG] * inv;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s_out = s;
+}
+
+// Per row (one warp): candidate from the network, x = max(0, out[:R]), y = min(0, s out[R:]);
+// keep it in place of the carried-over (At, Y) if its KKT natural residual
+// ||min(x, G x - m)|| is smaller.  Counts considered / accepted rows.
+__global__ void k_ws_judge(const float* __restrict__ out, const float* __restrict__ G,
+                           const float* __restrict__ M, const float* __restrict__ s_ptr,
+                           float* __restrict__ At, float* __restrict__ Y, int64_t I, int R,
+                           unsigned long long* counters) {
+  __shared__ float xs[8][2][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * 8 + warp;
+  if (row >= I) return;
+  const float s = *s_ptr;
+  const int D = 2 * R;
+  float xc[2], yc[2], xo[2], m[2];
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    xc[h] = yc[h] = xo[h] = m[h] = 0.0f;
+    if (j < R) {
+      xc[h] = fmaxf(0.0f, out[row * D + j]);
+      yc[h] = fminf(0.0f, s * out[row * D + R + j]);
+      xo[h] = At[row * R + j];
+      m[h] = M[row * R + j];
+      xs[warp][0][j] = xc[h];
+      xs[warp][1][j] = xo[h];
+    }
+  }
+  __syncwarp();
+  float rc = 0.0f, ro = 0.0f;
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    if (j >= R) continue;
+    float gc = -m[h], go = -m[h];
+    for (int k = 0; k < R; ++k) {
+      const float gk = G[k * R + j];  // G symmetric
+      gc = fmaf(gk, xs[warp][0][k], gc);
+      go = fmaf(gk, xs[warp][1][k], go);
+    }
+    const float a = fminf(xc[h], gc), b = fminf(xo[h], go);
+    rc += a * a;
+    ro += b * b;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    rc += __shfl_xor_sync(0xffffffffu, rc, off);
+    ro += __shfl_xor_sync(0xffffffffu, ro, off);
+  }
+  const bool take = rc < ro;
+  if (take) {
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      if (j < R) {
+        At[row * R + j] = xc[h];
+        Y[row * R + j] = yc[h];
+      }
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&counters[0], 1ull);
+    if (take) atomicAdd(&counters[1], 1ull);
+  }
+}
+
+}  // namespace
+
+cudaError_t ws_prepare(const float* G, const float* M, int R, int64_t I, float* Gn, float* mrows,
+                       float* s_out, cudaStream_t st) {
+  const int64_t n = static_cast<int64_t>(R) * R + I * R;
+  k_ws_prepare<<<blocks_for(n), 256, 0, st>>>(G, M, R, I, Gn, mrows, s_out);
+  return cudaGetLastError();
+}
+
+cudaError_t ws_judge(const float* out, const float* G, const float* M, const float* s_ptr,
+                     float* At, float* Y, int64_t I, int R, unsigned long long* counters,
+                     cudaStream_t st) {
+  k_ws_judge<<<static_cast<unsigned>((I + 7) / 8), 256, 0, st>>>(out, G, M, s_ptr, At, Y, I, R,
+                                                                 counters);
+  return cudaGetLastError();
+}
+
+}  // namespace ntf

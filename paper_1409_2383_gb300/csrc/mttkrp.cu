@@ -1,17 +1,17 @@
 // MTTKRP building blocks (Sec. III-A item 1 of Liavas & Sidiropoulos).
 //
-// The tensor is viewed as a row-major matrix X[P, Q] with P = I_1...I_s and Q =
-// I_{s+1}...I_N.  Every MTTKRP is one of two skinny contractions of that matrix followed by
-// a small reduction that applies the remaining factor of the mode's group:
+// The tensor is viewed as a row-major matrix X[P, Q] (P = product of the leading modes,
+// Q = product of the trailing ones).  Every MTTKRP is one of two skinny contractions of such a
+// view followed by a small reduction that applies the remaining factor of the mode's group:
 //
-//   GEMM-N:  T_R[p, r] = sum_q X[p, q] * KR_right[q, r]   (modes 1..s)
-//   GEMM-T:  T_L[q, r] = sum_p X[p, q] * KR_left[p, r]    (modes s+1..N)
+//   GEMM-N:  T_R[p, r] = sum_q X[p, q] * W[q, r]     W = Khatri-Rao rows of the trailing factors
+//   GEMM-T:  T_L[q, r] = sum_p X[p, q] * W[p, r]     W = Khatri-Rao rows of the leading factors
 //
-// KR_* rows are Khatri-Rao rows of the group's factors, built on the fly in shared memory
-// for each stage and never materialised.  Both contractions stream X from HBM exactly once;
-// X tiles are staged with 16-byte cp.async in a multi-stage ring; FP32 accumulation for FP32
-// and BF16 storage alike.  Split-K partial sums are reduced by a separate kernel in a fixed
-// order, so results are deterministic.
+// W is built once per contraction into a zero-padded [K_pad, RP] table (K = contraction
+// length) and read through L1 by every CTA.  Both contractions stream X from HBM exactly once
+// with 16-byte cp.async and FP32 accumulation (FP32 or BF16 storage).  When the contraction
+// range is split across CTAs the partial sums are added by a separate kernel in a fixed order,
+// so every result is deterministic.
 #include <algorithm>
 #include <cstdio>
 
@@ -21,19 +21,46 @@ namespace ntf {
 namespace detail {
 // One instantiation unit per storage type and contraction (gemm_{n,t}_{f32,bf16}.cu).
 extern template cudaError_t gemm_n_typed<float>(const float*, int64_t, int64_t, int,
-                                                const Group&, const GemmPlan&, float*, cudaStream_t);
+                                                const float*, const GemmPlan&, float*,
+                                                cudaStream_t);
 extern template cudaError_t gemm_n_typed<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t,
-                                                        int, const Group&, const GemmPlan&,
+                                                        int, const float*, const GemmPlan&,
                                                         float*, cudaStream_t);
 extern template cudaError_t gemm_t_typed<float>(const float*, int64_t, int64_t, int,
-                                                const Group&, const GemmPlan&, float*, cudaStream_t);
+                                                const float*, const GemmPlan&, float*,
+                                                cudaStream_t);
 extern template cudaError_t gemm_t_typed<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t,
-                                                        int, const Group&, const GemmPlan&,
+                                                        int, const float*, const GemmPlan&,
                                                         float*, cudaStream_t);
 }  // namespace detail
 
 namespace {
 using namespace detail;
+// Entry r of Khatri-Rao row q of a group (last mode fastest).
+__device__ __forceinline__ float kr_entry(const Group& g, int64_t q, int r, int R) {
+  float v = 1.0f;
+#pragma unroll
+  for (int j = 2; j >= 0; --j) {
+    if (j < g.n) {
+      const int64_t d = g.dim[j];
+      const int64_t i = q % d;
+      q /= d;
+      v *= __ldg(g.F[j] + i * R + r);
+    }
+  }
+  return v;
+}
+
+// W[q, r] = Khatri-Rao row q of the group for q < K and r < R; 0 in the padding.
+__global__ void k_kr_table(Group g, int64_t K, int R, int RP, int64_t n, float* __restrict__ W) {
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < n;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t q = idx / RP;
+    const int r = static_cast<int>(idx % RP);
+    W[idx] = (q < K && r < R) ? kr_entry(g, q, r, R) : 0.0f;
+  }
+}
+
 // --------------------------------------------------------------------- reductions
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, int64_t n,
                              float* __restrict__ out) {
@@ -54,12 +81,19 @@ __global__ void k_post_fast(const float* __restrict__ T, int64_t Ia, int64_t Ib,
   const int groups = blockDim.x / R;
   const int grp = tid / R, r = tid % R;
   for (int64_t a = blockIdx.x; a < Ia; a += gridDim.x) {
-    float s = 0.0f;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
     if (grp < groups) {
       const float* Ta = T + a * Ib * R;
-      for (int64_t b = grp; b < Ib; b += groups) s = fmaf(Ta[b * R + r], __ldg(F + b * R + r), s);
+      int64_t b = grp;
+      for (; b + 3 * groups < Ib; b += 4 * groups) {
+        s0 = fmaf(Ta[b * R + r], __ldg(F + b * R + r), s0);
+        s1 = fmaf(Ta[(b + groups) * R + r], __ldg(F + (b + groups) * R + r), s1);
+        s2 = fmaf(Ta[(b + 2 * groups) * R + r], __ldg(F + (b + 2 * groups) * R + r), s2);
+        s3 = fmaf(Ta[(b + 3 * groups) * R + r], __ldg(F + (b + 3 * groups) * R + r), s3);
+      }
+      for (; b < Ib; b += groups) s0 = fmaf(Ta[b * R + r], __ldg(F + b * R + r), s0);
     }
-    red[tid] = s;
+    red[tid] = (s0 + s1) + (s2 + s3);
     __syncthreads();
     if (tid < R) {
       float acc = 0.0f;
@@ -82,9 +116,16 @@ __global__ void k_post_slow(const float* __restrict__ T, int64_t Ia, int64_t Ib,
   const int r = tid % R;
   if (b >= Ib) return;
   const int64_t a_beg = Ia * split / splits, a_end = Ia * (split + 1) / splits;
-  float s = 0.0f;
-  for (int64_t a = a_beg; a < a_end; ++a) s = fmaf(T[(a * Ib + b) * R + r], __ldg(F + a * R + r), s);
-  out[(static_cast<int64_t>(split) * Ib + b) * R + r] = s;
+  float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+  int64_t a = a_beg;
+  for (; a + 3 < a_end; a += 4) {
+    s0 = fmaf(T[(a * Ib + b) * R + r], __ldg(F + a * R + r), s0);
+    s1 = fmaf(T[((a + 1) * Ib + b) * R + r], __ldg(F + (a + 1) * R + r), s1);
+    s2 = fmaf(T[((a + 2) * Ib + b) * R + r], __ldg(F + (a + 2) * R + r), s2);
+    s3 = fmaf(T[((a + 3) * Ib + b) * R + r], __ldg(F + (a + 3) * R + r), s3);
+  }
+  for (; a < a_end; ++a) s0 = fmaf(T[(a * Ib + b) * R + r], __ldg(F + a * R + r), s0);
+  out[(static_cast<int64_t>(split) * Ib + b) * R + r] = (s0 + s1) + (s2 + s3);
 }
 
 // ||X||^2 with FP64 accumulation; per-block partials then one block sums them in order.
@@ -124,61 +165,71 @@ __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restric
 }  // namespace
 
 // ------------------------------------------------------------------------- plans
-GemmPlan plan_gemm_n(int64_t P, int64_t Q, int R, int dtype, const void* X, int num_sms) {
-  GemmPlan pl{};
-  const int esize = dtype == NTF_BF16 ? 2 : 4;
-  pl.vec16 = (Q * esize) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0;
-  const int64_t max_rows = 512;
-  const int64_t nblk = (P + max_rows - 1) / max_rows;
-  pl.rows_per_blk = static_cast<int>((P + nblk - 1) / nblk);
-  pl.blocks = static_cast<int>(nblk);
-  const int per16 = 16 / esize;
-  const int64_t ntiles = (Q + 2 * per16 - 1) / (2 * per16);
-  const int64_t target = static_cast<int64_t>(num_sms) * 2;
-  int64_t splits = (target + nblk - 1) / nblk;
-  splits = std::max<int64_t>(1, std::min<int64_t>(splits, ntiles));
-  if (!pl.vec16) splits = std::max<int64_t>(1, std::min<int64_t>(Q / 64, 64));
-  pl.splits = static_cast<int>(splits);
-  return pl;
-}
+namespace {
 
-GemmPlan plan_gemm_t(int64_t P, int64_t Q, int R, int dtype, const void* X, int num_sms) {
+// Tiles of 64 rows (GEMM-N) or 64 columns (GEMM-T).  The contraction range is split across
+// CTAs only when there are too few tiles to fill the GPU several times over; a split range is
+// a multiple of 64 long.
+GemmPlan make_plan(int64_t tiles_extent, int64_t K, int dtype, const void* X, int64_t row_len,
+                   int num_sms) {
   GemmPlan pl{};
   const int esize = dtype == NTF_BF16 ? 2 : 4;
-  pl.vec16 = (Q * esize) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0;
-  const int cols = round_rp(R) <= 32 ? 512 : 256;
-  const int64_t nblk = (Q + cols - 1) / cols;
-  pl.blocks = static_cast<int>(nblk);
-  pl.rows_per_blk = 0;
-  const int64_t target = static_cast<int64_t>(num_sms) * 2;
-  int64_t splits = nblk >= target ? 1 : (target + nblk - 1) / nblk;
-  const int64_t tp = 8192 / (cols * esize);
-  splits = std::max<int64_t>(1, std::min<int64_t>(splits, (P + tp - 1) / tp));
+  pl.vec16 = (row_len * esize) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0;
+  const int64_t tiles = (tiles_extent + 63) / 64;
+  pl.tiles = static_cast<int>(tiles);
+  const int64_t want = static_cast<int64_t>(num_sms) * 8;
+  int64_t chunks = tiles >= want ? 1 : (want + tiles - 1) / tiles;
+  chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (K + 1023) / 1024));
+  int64_t len = (K + chunks - 1) / chunks;
+  len = ((len + 63) / 64) * 64;
+  chunks = (K + len - 1) / len;
   if (!pl.vec16) {
-    pl.blocks = 0;
-    splits = std::max<int64_t>(1, std::min<int64_t>(P / 64, 64));
+    chunks = 1;
+    len = K;
   }
-  pl.splits = static_cast<int>(splits);
+  pl.chunks = static_cast<int>(chunks);
+  pl.chunk_len = len;
   return pl;
 }
 
-cudaError_t launch_gemm_n(const void* X, int dtype, int64_t P, int64_t Q, int R, const Group& g,
-                          const GemmPlan& plan, float* out, cudaStream_t st) {
-  if (dtype == NTF_BF16)
-    return gemm_n_typed(static_cast<const __nv_bfloat16*>(X), P, Q, R, g, plan, out, st);
-  return gemm_n_typed(static_cast<const float*>(X), P, Q, R, g, plan, out, st);
+}  // namespace
+
+int round_rp(int R) { return detail::round_rp(R); }
+int64_t kr_rows_padded(int64_t K) { return ((K + 63) / 64) * 64; }
+
+GemmPlan plan_gemm_n(int64_t P, int64_t Q, int dtype, const void* X, int num_sms) {
+  return make_plan(P, Q, dtype, X, Q, num_sms);
 }
 
-cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R, const Group& g,
+GemmPlan plan_gemm_t(int64_t P, int64_t Q, int dtype, const void* X, int num_sms) {
+  return make_plan(Q, P, dtype, X, Q, num_sms);
+}
+
+cudaError_t launch_kr_table(const Group& g, int64_t K, int R, float* W, cudaStream_t st) {
+  const int RP = detail::round_rp(R);
+  const int64_t n = kr_rows_padded(K) * RP;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 4096));
+  k_kr_table<<<blocks, 256, 0, st>>>(g, K, R, RP, n, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_n(const void* X, int dtype, int64_t P, int64_t Q, int R, const float* W,
                           const GemmPlan& plan, float* out, cudaStream_t st) {
   if (dtype == NTF_BF16)
-    return gemm_t_typed(static_cast<const __nv_bfloat16*>(X), P, Q, R, g, plan, out, st);
-  return gemm_t_typed(static_cast<const float*>(X), P, Q, R, g, plan, out, st);
+    return detail::gemm_n_typed(static_cast<const __nv_bfloat16*>(X), P, Q, R, W, plan, out, st);
+  return detail::gemm_n_typed(static_cast<const float*>(X), P, Q, R, W, plan, out, st);
+}
+
+cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R, const float* W,
+                          const GemmPlan& plan, float* out, cudaStream_t st) {
+  if (dtype == NTF_BF16)
+    return detail::gemm_t_typed(static_cast<const __nv_bfloat16*>(X), P, Q, R, W, plan, out, st);
+  return detail::gemm_t_typed(static_cast<const float*>(X), P, Q, R, W, plan, out, st);
 }
 
 cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float* out,
                               cudaStream_t st) {
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 2048);
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
   k_sum_splits<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, st>>>(partial, splits, n, out);
   return cudaGetLastError();
 }

@@ -50,31 +50,44 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
     if (dims[m] < 1 || dims[m] > (int64_t{1} << 30)) return NTF_ERR_INVALID_ARG;
     if (m != mode && !d_factors[m]) return NTF_ERR_INVALID_ARG;
   }
-  const int s = order / 2;
-  int64_t P = 1, Q = 1;
-  for (int m = 0; m < order; ++m) (m < s ? P : Q) *= dims[m];
-  if (P >= (int64_t{1} << 31) || Q >= (int64_t{1} << 31)) return NTF_ERR_UNSUPPORTED;
+  // The same two contractions as the context path: the leading factors' modes come from
+  // X[P_R, Q_R] * KR(trailing factors), the others from X[P_L, Q_L]^T * KR(leading factors).
+  const int s_R = 2, s_L = order == 3 ? 1 : 2;
+  int64_t numel = 1, P_R = 1, P_L = 1;
+  for (int m = 0; m < order; ++m) {
+    numel *= dims[m];
+    if (m < s_R) P_R *= dims[m];
+    if (m < s_L) P_L *= dims[m];
+  }
+  const int64_t Q_R = numel / P_R, Q_L = numel / P_L;
+  if (P_R >= (int64_t{1} << 31) || Q_R >= (int64_t{1} << 31) || P_L >= (int64_t{1} << 31) ||
+      Q_L >= (int64_t{1} << 31))
+    return NTF_ERR_UNSUPPORTED;
   const int R = rank;
-  const bool left = mode < s;
-  const int first = left ? 0 : s;
-  const int count = left ? s : order - s;
-  const int64_t rows = left ? P : Q;  // rows of the contraction output T
+  const bool left = mode < s_R;
+  const int first = left ? 0 : s_L;
+  const int count = left ? s_R : order - s_L;
+  const int64_t rows = left ? P_R : Q_L;   // rows of the contraction output T
+  const int64_t K = left ? Q_R : P_L;      // contraction length
+  const int64_t w_floats = ntf::kr_rows_padded(K) * ntf::round_rp(R);
   // The contraction output goes straight to d_M when the mode's group has one mode;
-  // otherwise it is an intermediate in scratch.
+  // otherwise it is an intermediate in scratch, after the Khatri-Rao table.
   const int64_t t_floats = count == 1 ? 0 : rows * R;
+  const int64_t room = kScratchFloats - w_floats - t_floats;
+  if (room < 0) return NTF_ERR_INVALID_ARG;
 
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return NTF_ERR_CUDA;
-  ntf::GemmPlan plan = left ? ntf::plan_gemm_n(P, Q, R, dtype, d_tensor, sms)
-                            : ntf::plan_gemm_t(P, Q, R, dtype, d_tensor, sms);
-  // The intermediate must fit in the scratch array; split-K partial sums use what is left
-  // (fewer splits when the full plan would not fit).
-  const int64_t room = kScratchFloats - t_floats;
-  if (room < 0) return NTF_ERR_INVALID_ARG;
-  if (plan.splits > 1 && plan.splits * rows * R > room)
-    plan.splits = static_cast<int>(std::max<int64_t>(1, room / (rows * R)));
+  ntf::GemmPlan plan = left ? ntf::plan_gemm_n(P_R, Q_R, dtype, d_tensor, sms)
+                            : ntf::plan_gemm_t(P_L, Q_L, dtype, d_tensor, sms);
+  // Partial sums of a split contraction range use what is left of the scratch; when they do
+  // not fit, the range is not split.
+  if (plan.chunks > 1 && plan.chunks * rows * R > room) {
+    plan.chunks = 1;
+    plan.chunk_len = K;
+  }
   int post_splits = 1;
   if (count == 2 && mode != first) {
     post_splits = ntf::post_slow_splits(dims[first], dims[first + 1], R, sms);
@@ -86,12 +99,13 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
   float* scratch = nullptr;
   ntf_status st = scratch_on_current_device(&scratch);
   if (st != NTF_OK) return st;
-  float* T = count == 1 ? d_M : scratch;
-  float* part = scratch + t_floats;
+  float* W = scratch;
+  float* T = count == 1 ? d_M : scratch + w_floats;
+  float* part = scratch + w_floats + t_floats;
 
   ntf::Group g{};
-  const int gfirst = left ? s : 0;
-  const int gcount = left ? order - s : s;
+  const int gfirst = left ? s_R : 0;
+  const int gcount = left ? order - s_R : s_L;
   g.n = gcount;
   for (int j = 0; j < gcount; ++j) {
     g.F[j] = d_factors[gfirst + j];
@@ -99,11 +113,13 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
   }
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   (void)cudaGetLastError();
-  float* out = plan.splits > 1 ? part : T;
-  e = left ? ntf::launch_gemm_n(d_tensor, dtype, P, Q, R, g, plan, out, cs)
-           : ntf::launch_gemm_t(d_tensor, dtype, P, Q, R, g, plan, out, cs);
-  if (e == cudaSuccess && plan.splits > 1)
-    e = ntf::launch_sum_splits(part, plan.splits, rows * R, T, cs);
+  e = ntf::launch_kr_table(g, K, R, W, cs);
+  float* out = plan.chunks > 1 ? part : T;
+  if (e == cudaSuccess)
+    e = left ? ntf::launch_gemm_n(d_tensor, dtype, P_R, Q_R, R, W, plan, out, cs)
+             : ntf::launch_gemm_t(d_tensor, dtype, P_L, Q_L, R, W, plan, out, cs);
+  if (e == cudaSuccess && plan.chunks > 1)
+    e = ntf::launch_sum_splits(part, plan.chunks, rows * R, T, cs);
   if (e == cudaSuccess && count == 2) {
     const int64_t Ia = dims[first], Ib = dims[first + 1];
     if (mode == first)

@@ -38,25 +38,29 @@ struct Ctrl {
   int status;                     // kSt* bits
   int bad[kMaxOrder];             // 1 if the last system of factor n was not SPD
   int pad[3];
+  unsigned long long ws_rows[2];  // warm start: rows considered, rows that took the prediction
 };
 
 // ------------------------------------------------------------------ kernel launchers
 // mttkrp.cu
 struct GemmPlan {
-  int splits;       // split-K factor
-  int blocks;       // row blocks (GEMM-N) or column blocks (GEMM-T)
-  int rows_per_blk; // GEMM-N rows per block
-  bool vec16;       // 16-byte cp.async staging possible
+  int tiles;          // CTAs along the output rows (64 per tile)
+  int chunks;         // CTAs along the contraction range (> 1: partial sums)
+  int64_t chunk_len;  // contraction elements per chunk
+  bool vec16;         // 16-byte cp.async staging possible
 };
 
-GemmPlan plan_gemm_n(int64_t P, int64_t Q, int R, int dtype, const void* X, int num_sms);
-GemmPlan plan_gemm_t(int64_t P, int64_t Q, int R, int dtype, const void* X, int num_sms);
-
-// out (or partial[splits] if plan.splits > 1) [P, R] = X[P, Q] * KR(g)[Q, R]
-cudaError_t launch_gemm_n(const void* X, int dtype, int64_t P, int64_t Q, int R, const Group& g,
+int round_rp(int R);
+int64_t kr_rows_padded(int64_t K);
+GemmPlan plan_gemm_n(int64_t P, int64_t Q, int dtype, const void* X, int num_sms);
+GemmPlan plan_gemm_t(int64_t P, int64_t Q, int dtype, const void* X, int num_sms);
+// W[K_pad, RP] = Khatri-Rao rows of the group (zero padding)
+cudaError_t launch_kr_table(const Group& g, int64_t K, int R, float* W, cudaStream_t st);
+// out (or partial[chunks]) [P, R] = X[P, Q] * W[Q, R]
+cudaError_t launch_gemm_n(const void* X, int dtype, int64_t P, int64_t Q, int R, const float* W,
                           const GemmPlan& plan, float* out_or_partial, cudaStream_t st);
-// out (or partial) [Q, R] = X[P, Q]^T * KR(g)[P, R]
-cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R, const Group& g,
+// out (or partial[chunks]) [Q, R] = X[P, Q]^T * W[P, R]
+cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R, const float* W,
                           const GemmPlan& plan, float* out_or_partial, cudaStream_t st);
 // out[n] = sum_s partial[s * n + i]
 cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float* out,
@@ -75,15 +79,70 @@ cudaError_t launch_to_bf16(const float* in, uint16_t* out, int64_t n, cudaStream
 cudaError_t launch_gram(const float* F, int64_t I, int R, double* G, cudaStream_t st);
 cudaError_t launch_system(const double* grams, int N, int mode, int R, int rho_policy,
                           Ctrl* ctrl, double* H, double* L, cudaStream_t st);
-int admm_row_blocks(int64_t I);
-cudaError_t launch_admm_rows(const float* M, float* A, float* At, float* Y, const double* L,
-                             int64_t I, int R, int inner, int mode, Ctrl* ctrl,
-                             double* norm_part, cudaStream_t st);
-cudaError_t launch_update_finalize(const double* norm_part, int nblocks, int mode,
-                                   int rho_policy, double mu, double tau_incr,
-                                   double tau_decr, Ctrl* ctrl, cudaStream_t st);
 int fit_blocks(int64_t I, int R);
 cudaError_t launch_fit(const float* M, const float* F, int64_t I, int R, const double* grams,
                        int N, double* partial, Ctrl* ctrl, cudaStream_t st);
+
+// update.cu: one factor update in three launches -- system (FP64 coefficient matrix, its
+// Cholesky factor and inverse), rows (the inner iterations), reduce (Gram, residuals, fit).
+struct UpdateCall {
+  const double* grams;
+  double* sys;
+  const float* M;
+  float* A;
+  float* At;
+  float* Y;
+  Ctrl* ctrl;
+  double* gram_part;
+  double* scal_part;
+  double* gram_out;
+  int64_t I;
+  int N, mode, R, inner, rho_policy;
+  bool kr_aux, want_fit;
+  double mu, tau_incr, tau_decr;
+};
+int update_blocks(int64_t I);
+int update_scalars();
+size_t update_sys_bytes(int N, int R);
+cudaError_t launch_update_system(const UpdateCall& u, cudaStream_t st);
+cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st);
+cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st);
+cudaError_t launch_update(const UpdateCall& u, cudaStream_t st);
+
+// mlp.cu: warm-start network (parameter layout, forward, backward, Adam) and its use
+struct MlpShape {
+  int R, H, Din, Dout;
+  int64_t oW1, ob1, oW2, ob2, oW3, ob3, count;  // offsets into the flat parameter array
+};
+MlpShape mlp_shape(int R, int H);
+cudaError_t mlp_group_terms(const MlpShape& s, const __nv_bfloat16* pb, const float* Gn,
+                            int groups, float* hG, cudaStream_t st);
+cudaError_t mlp_forward_rows(const MlpShape& s, const float* p, const __nv_bfloat16* pb,
+                             const float* hG, const int* row_group, const float* mrows, int rows,
+                             float* z1, float* h1, float* z2, float* h2, float* out,
+                             cudaStream_t st);
+cudaError_t mlp_backward(const MlpShape& s, const __nv_bfloat16* pb, const float* Gn,
+                         const int* offs, int groups, const int* all_offs, const float* mrows,
+                         int rows, const float* T, const float* z1, const float* h1,
+                         const float* z2, const float* h2, const float* out, float* d_out,
+                         float* d_h2, float* d_h1, float* gsum, float* grad, double* loss_part,
+                         double* loss, cudaStream_t st);
+cudaError_t mlp_adam(const MlpShape& s, float* p, const float* grad, float* m, float* v,
+                     __nv_bfloat16* pb, float lr, int step, cudaStream_t st);
+cudaError_t mlp_row_groups(const int* offs, int groups, int* row_group, cudaStream_t st);
+cudaError_t mlp_refresh_bf16(const MlpShape& s, const float* p, __nv_bfloat16* pb, cudaStream_t st);
+cudaError_t ws_prepare(const float* G, const float* M, int R, int64_t I, float* Gn, float* mrows,
+                       float* s_out, cudaStream_t st);
+cudaError_t ws_judge(const float* out, const float* G, const float* M, const float* s_ptr,
+                     float* At, float* Y, int64_t I, int R, unsigned long long* counters,
+                     cudaStream_t st);
+// update.cu: FP32 coefficient matrix (no rho) of factor `mode` in its system slot
+const float* update_sys_h32(const double* sys, int mode, int R);
+
+// mlp_api.cu: warm start of a factor update by an attached network
+cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float* M, float* At,
+                           float* Y, int64_t I, unsigned long long* counters, cudaStream_t st);
+int mlp_rank(const ntf_mlp* n);
+int mlp_max_rows(const ntf_mlp* n);
 
 }  // namespace ntf

@@ -56,7 +56,8 @@ class RunStats(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("contractions", ctypes.c_int64 * 2), ("contraction_ms", ctypes.c_double * 2),
-                ("contraction_bytes", ctypes.c_double * 2)]
+                ("contraction_bytes", ctypes.c_double * 2),
+                ("ws_rows_considered", ctypes.c_int64), ("ws_rows_accepted", ctypes.c_int64)]
 
 
 _lib = None
@@ -85,6 +86,17 @@ _SIGS = {
     "ntf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ntf_profile_get": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "ntf_to_bf16": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "ntf_mlp_param_count": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int]),
+    "ntf_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, _P,
+                                      ctypes.c_int, ctypes.c_int, _P]),
+    "ntf_mlp_destroy": (ctypes.c_int, [_P]),
+    "ntf_mlp_get_params": (ctypes.c_int, [_P, _P]),
+    "ntf_mlp_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "ntf_mlp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int,
+                                          ctypes.c_float, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_double), _P]),
+    "ntf_mlp_last_error": (ctypes.c_char_p, []),
+    "ntf_attach_warmstart": (ctypes.c_int, [_P, _P]),
     "ntf_mttkrp_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.c_int,
                                           ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P), _P,
                                           _P]),
@@ -321,7 +333,69 @@ class Context:
         _check(lib().ntf_profile_get(self._h, ctypes.byref(p)))
         return {"sweeps": p.sweeps, "kernel_launches": p.kernel_launches,
                 "contractions": list(p.contractions), "contraction_ms": list(p.contraction_ms),
-                "contraction_bytes": list(p.contraction_bytes)}
+                "contraction_bytes": list(p.contraction_bytes),
+                "ws_rows_considered": p.ws_rows_considered,
+                "ws_rows_accepted": p.ws_rows_accepted}
+
+    def attach_warmstart(self, net: Optional["Mlp"]) -> None:
+        _check(lib().ntf_attach_warmstart(self._h, net._h if net is not None else None))
+        self._ws = net  # keep the network alive while attached
+
+
+def _mcheck(status: int) -> None:
+    if status != 0:
+        raise NTFError(status, lib().ntf_mlp_last_error().decode())
+
+
+class Mlp:
+    """Warm-start network (wraps ``ntf_mlp``); parameters in the flat layout of the ABI."""
+
+    def __init__(self, rank: int, hidden: int, params: torch.Tensor, max_rows: int,
+                 max_groups: int, stream: Optional[torch.cuda.Stream] = None):
+        n = int(lib().ntf_mlp_param_count(int(rank), int(hidden)))
+        if n < 0:
+            raise ValueError("bad rank or hidden width")
+        p = params.detach().to("cpu", torch.float32).contiguous()
+        if p.numel() != n:
+            raise ValueError(f"expected {n} parameters, got {p.numel()}")
+        self.R, self.H, self.count = int(rank), int(hidden), n
+        self.stream = stream
+        self._h = _P()
+        _mcheck(lib().ntf_mlp_create(ctypes.byref(self._h), self.R, self.H, _ptr(p),
+                                     int(max_rows), int(max_groups), _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if self._h:
+            lib().ntf_mlp_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> torch.Tensor:
+        out = torch.empty(self.count, dtype=torch.float32)
+        _mcheck(lib().ntf_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def forward(self, Gn: torch.Tensor, offsets: torch.Tensor, mrows: torch.Tensor) -> torch.Tensor:
+        groups, rows = int(offsets.numel()) - 1, int(mrows.shape[0])
+        out = torch.empty(rows, 2 * self.R, device=mrows.device)
+        _mcheck(lib().ntf_mlp_forward(self._h, _ptr(Gn), _ptr(offsets), groups, _ptr(mrows),
+                                      rows, _ptr(out)))
+        return out
+
+    def train_step(self, Gn, offsets, mrows, targets, lr: float, apply: bool = True,
+                   want_loss: bool = True, grad_out: Optional[torch.Tensor] = None):
+        groups, rows = int(offsets.numel()) - 1, int(mrows.shape[0])
+        loss = ctypes.c_double()
+        _mcheck(lib().ntf_mlp_train_step(self._h, _ptr(Gn), _ptr(offsets), groups, _ptr(mrows),
+                                         _ptr(targets), rows, float(lr), 1 if apply else 0,
+                                         ctypes.byref(loss) if want_loss else None,
+                                         _ptr(grad_out)))
+        return loss.value if want_loss else None
 
 
 def zeros_state(dims: Sequence[int], R: int, device="cuda") -> List[torch.Tensor]:
@@ -329,6 +403,6 @@ def zeros_state(dims: Sequence[int], R: int, device="cuda") -> List[torch.Tensor
 
 
 __all__ = ["Context", "Params", "NTFError", "default_params", "to_bf16", "lib", "zeros_state",
-           "mttkrp_noalloc",
+           "mttkrp_noalloc", "Mlp",
            "NTF_F32", "NTF_BF16", "NTF_KR_PRIMAL", "NTF_KR_AUX", "NTF_RHO_ADAPTIVE",
            "NTF_RHO_TRACE", "NTF_RHO_FIXED", "LIB_PATH"]

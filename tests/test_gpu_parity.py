@@ -341,7 +341,7 @@ def test_profiling_under_graph_replay(ntf):
             assert prof["contractions"] == [10, 10]
             assert all(ms > 0 for ms in prof["contraction_ms"])
             assert prof["contraction_bytes"] == [X.size * 4.0] * 2
-            assert prof["kernel_launches"] >= 10 * 14
+            assert prof["kernel_launches"] >= 10 * 10
             ctx.profile_enable(False)
             ctx.run(A, At, Y, 2)                      # back to a graph without events
             M = ctx.mttkrp(0, At)
