@@ -1,0 +1,123 @@
+"""Learned warm start for the factor updates: harvest training rows from the plain method,
+train the network with the library's kernels, attach it to a factorization.
+
+Everything that computes runs in ``libntf.so``; this module only orchestrates calls and
+holds the training rows in device memory.
+
+Training rows: during outer iterations of the plain method on synthetic tensors, every
+factor update contributes its coefficient matrix G (without rho) and its MTTKRP rows m_i;
+the target of a row is the non-negative least-squares solution reached by running the same
+row iteration to convergence (``conv_iters`` inner iterations, fixed rho = trace(G)/R) from
+the carried-over state, paired with its dual: [x* ; y*/s], s = trace(G)/R.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import ntf
+
+
+def init_params(R: int, H: int, seed: int) -> torch.Tensor:
+    """Glorot-uniform weights, zero biases, in the flat parameter layout of the ABI."""
+    g = np.random.default_rng(seed)
+    Din, Dout = R * R + R, 2 * R
+
+    def glorot(fo, fi):
+        a = math.sqrt(6.0 / (fi + fo))
+        return g.uniform(-a, a, (fo, fi))
+
+    parts = [glorot(H, Din), np.zeros(H), glorot(H, H), np.zeros(H), glorot(Dout, H),
+             np.zeros(Dout)]
+    return torch.as_tensor(np.concatenate([p.reshape(-1) for p in parts]), dtype=torch.float32)
+
+
+@dataclass
+class RowSet:
+    """Training rows grouped by coefficient matrix (device tensors)."""
+    R: int
+    Gn: List[torch.Tensor] = field(default_factory=list)       # [R*R] each
+    mrows: List[torch.Tensor] = field(default_factory=list)    # [rows, R] each
+    targets: List[torch.Tensor] = field(default_factory=list)  # [rows, 2R] each
+
+    @property
+    def rows(self) -> int:
+        return sum(int(m.shape[0]) for m in self.mrows)
+
+    def batch(self, idx: Sequence[int]):
+        Gn = torch.stack([self.Gn[i] for i in idx])
+        mr = torch.cat([self.mrows[i] for i in idx])
+        tg = torch.cat([self.targets[i] for i in idx])
+        offs = [0]
+        for i in idx:
+            offs.append(offs[-1] + int(self.mrows[i].shape[0]))
+        return Gn, torch.tensor(offs, dtype=torch.int32, device=mr.device), mr, tg
+
+
+def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
+            rows: RowSet, conv_iters: int = 300, params: Optional[ntf.Params] = None,
+            every: int = 1) -> RowSet:
+    """Run ``outer`` outer iterations of the plain method (Gauss-Seidel over the factors,
+    exactly the updates of ``Context.run``) and add the rows of every ``every``-th sweep's
+    factor updates to ``rows``."""
+    p = params or ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    pc = ntf.default_params(paper_mode=False, inner_iters=conv_iters,
+                            rho_policy=ntf.NTF_RHO_TRACE, eps_abs=0.0, eps_rel=0.0)
+    dims = tuple(int(d) for d in X.shape)
+    A = [f.clone() for f in init]
+    At = [f.clone() for f in init]
+    Y = [torch.zeros_like(f) for f in init]
+    H = torch.empty(R, R, dtype=torch.float64, device=X.device)
+    with ntf.Context(X, R, p) as ctx, ntf.Context(X, R, pc) as conv:
+        for m in range(len(dims)):
+            ctx.gram(m, At[m])
+            conv.gram(m, At[m])
+        for k in range(outer):
+            for n in range(len(dims)):
+                M = ctx.mttkrp(n, At)
+                if k % every == 0:
+                    rho = ctx.system(n, H)
+                    G = (H - rho * torch.eye(R, dtype=torch.float64, device=X.device))
+                    s = float(torch.trace(G)) / R
+                    Ac, Tc, Yc = A[n].clone(), At[n].clone(), Y[n].clone()
+                    conv.admm_update(n, M, Ac, Tc, Yc, stats=False)
+                    rows.Gn.append((G / s).float().reshape(-1).contiguous())
+                    rows.mrows.append((M / s).contiguous())
+                    rows.targets.append(torch.cat([Tc, Yc / s], dim=1).contiguous())
+                    conv.gram(n, At[n])  # restore: the converged update refreshed its Gram
+                ctx.admm_update(n, M, A[n], At[n], Y[n], stats=False)
+                conv.gram(n, At[n])
+    torch.cuda.synchronize()
+    return rows
+
+
+def train(net: ntf.Mlp, rows: RowSet, steps: int, groups_per_batch: int, lr: float,
+          seed: int = 0, log_every: int = 0) -> List[float]:
+    """Adam on random batches of whole groups; returns the loss of every logged step."""
+    g = np.random.default_rng(seed)
+    n = len(rows.Gn)
+    losses = []
+    for t in range(steps):
+        idx = g.choice(n, size=min(groups_per_batch, n), replace=False)
+        Gn, offs, mr, tg = rows.batch(sorted(idx.tolist()))
+        want = bool(log_every) and (t % log_every == 0 or t == steps - 1)
+        loss = net.train_step(Gn, offs, mr, tg, lr, apply=True, want_loss=want)
+        if want:
+            losses.append(loss)
+    return losses
+
+
+def eval_loss(net: ntf.Mlp, rows: RowSet, groups_per_batch: int) -> float:
+    """Mean loss over all rows (no update)."""
+    tot, cnt = 0.0, 0
+    for i in range(0, len(rows.Gn), groups_per_batch):
+        idx = list(range(i, min(i + groups_per_batch, len(rows.Gn))))
+        Gn, offs, mr, tg = rows.batch(idx)
+        loss = net.train_step(Gn, offs, mr, tg, 0.0, apply=False, want_loss=True)
+        tot += loss * tg.numel()
+        cnt += tg.numel()
+    return tot / max(cnt, 1)
