@@ -268,6 +268,7 @@ def run_ntf(args):
         h2d = Xh.numel() * 4 + 2 * sum(f.numel() * 4 for f in init_h)
         d2h = sum(f.numel() * 4 for f in out_h)
         ctx.close()
+        variants = None if args.no_variants else run_variants(args, Xd, init_d, target)
 
     value_s = ms / 1000.0
     if world > 1:
@@ -318,13 +319,15 @@ def run_ntf(args):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(prof["kernel_launches"]),
         "clocks": clk.summary(),
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
 
 
 def run_kernel_case(args):
     """Standalone MTTKRP calls on a small-but-larger-than-L2 tensor (for ncu captures):
-    mode 0 runs the X * KR_right contraction, the last mode the X^T * KR_left one."""
+    mode 0 runs the X * KR_right contraction, the last mode the X^T * KR_left one.  Prints
+    the CUDA-event time of each (contraction plus its small second-level reduction)."""
     import torch
     from paper_1409_2383_gb300 import ntf
     dims = tuple(int(d) for d in args.dims.split("x"))
@@ -333,13 +336,67 @@ def run_kernel_case(args):
     if args.storage == "bf16":
         X = ntf.to_bf16(X)
     F = [torch.as_tensor(rng.random((d, args.rank), dtype=np.float32)).cuda() for d in dims]
-    with ntf.Context(X, args.rank) as ctx:
-        for _ in range(args.steps):
+    engine = {"auto": ntf.NTF_CONTRACT_AUTO, "tensor": ntf.NTF_CONTRACT_TENSOR,
+              "simt": ntf.NTF_CONTRACT_SIMT}[args.engine]
+    times = {0: [], len(dims) - 1: []}
+    with ntf.Context(X, args.rank, ntf.default_params(contraction=engine)) as ctx:
+        for it in range(args.warmup + args.steps):
             for n in (0, len(dims) - 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
                 ctx.mttkrp(n, F)
-        torch.cuda.synchronize()
+                e1.record()
+                e1.synchronize()
+                if it >= args.warmup:
+                    times[n].append(e0.elapsed_time(e1) * 1e3)
+    nbytes = X.numel() * X.element_size()
+    us = {f"mode{n}_us": statistics.median(v) for n, v in times.items()}
+    gbs = {f"mode{n}_gbs": nbytes / (statistics.median(v) * 1e-6) / 1e9 for n, v in times.items()}
     print(json.dumps({"kernel_case": args.dims, "rank": args.rank, "storage": args.storage,
-                      "calls": 2 * args.steps}))
+                      "engine": args.engine, "calls": 2 * (args.warmup + args.steps), **us,
+                      **gbs}))
+
+
+def run_variants(args, Xd, init_d, target):
+    """Time to the same fit target for BF16 tensor storage and for BF16 storage plus the
+    learned warm start (network trained on rows harvested from tensors of the same generator
+    with other seeds, 200^3, by the library's own kernels; training time reported apart)."""
+    import torch
+    import synth
+    from paper_1409_2383_gb300 import ntf, warmstart
+    out = {}
+    fp32 = warmstart.time_to_fit(Xd, RANK, init_d, target, MAX_OUTER, repeats=3)
+    out["fp32"] = fp32
+    Xb = ntf.to_bf16(Xd)
+    out["bf16"] = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, repeats=3)
+    t0 = time.perf_counter()
+    rows = warmstart.RowSet(RANK)
+    hdims, seeds = (200, 200, 200), args.train_tensors
+    sweeps = max(1, int(math.ceil(args.train_rows / (sum(hdims) * seeds))))
+    for sd in range(1, seeds + 1):
+        Xt, _, it = synth.workload(hdims, RANK, seed=sd, snr_db=SNR_DB)
+        warmstart.harvest(torch.as_tensor(Xt).cuda(), RANK,
+                          [torch.as_tensor(f, dtype=torch.float32).cuda() for f in it],
+                          outer=sweeps, rows=rows, conv_iters=300)
+    t1 = time.perf_counter()
+    H = 256
+    net = ntf.Mlp(RANK, H, warmstart.init_params(RANK, H, seed=0), max_rows=4096, max_groups=16)
+    loss0 = warmstart.eval_loss(net, rows, 16)
+    steps = max(1, int(args.train_epochs * len(rows.Gn) / 16))
+    warmstart.train(net, rows, steps=steps, groups_per_batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    loss1 = warmstart.eval_loss(net, rows, 16)
+    learned = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, net=net, repeats=3)
+    out["bf16_learned"] = learned
+    out["training"] = {"rows": rows.rows, "groups": len(rows.Gn), "tensors": seeds,
+                       "tensor_dims": list(hdims), "sweeps_per_tensor": sweeps,
+                       "harvest_s": t1 - t0, "train_s": t2 - t1, "steps": steps,
+                       "loss_before": loss0, "loss_after": loss1, "hidden": H}
+    out["speedup_bf16_learned_vs_fp32"] = fp32["seconds"] / learned["seconds"]
+    out["speedup_bf16_vs_fp32"] = fp32["seconds"] / out["bf16"]["seconds"]
+    net.close()
+    return out
 
 
 def main():
@@ -349,11 +406,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ntf", choices=["ntf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the BF16 and BF16 + learned warm-start comparison")
+    ap.add_argument("--train-rows", type=int, default=1_000_000)
+    ap.add_argument("--train-tensors", type=int, default=20)
+    ap.add_argument("--train-epochs", type=float, default=3.0)
     ap.add_argument("--kernel-case", action="store_true",
                     help="standalone MTTKRP calls only (profiling case)")
     ap.add_argument("--dims", default="384x384x384")
     ap.add_argument("--rank", type=int, default=RANK)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "tensor", "simt"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.kernel_case:

@@ -70,6 +70,13 @@ typedef enum { NTF_KR_PRIMAL = 0, NTF_KR_AUX = 1 } ntf_kr_source;
  * FIXED:    rho stays at the value set by ntf_set_rho (default rho0). */
 typedef enum { NTF_RHO_ADAPTIVE = 0, NTF_RHO_TRACE = 1, NTF_RHO_FIXED = 2 } ntf_rho_policy;
 
+/* Engine of the two MTTKRP contractions.  TENSOR: tcgen05 tensor cores fed by TMA (needs
+ * R <= 64 and 16-byte aligned tensor rows, else ntf_create fails with NTF_ERR_UNSUPPORTED);
+ * SIMT: FP32 FMA kernels (any shape); AUTO: TENSOR where it applies, else SIMT.  Both keep
+ * FP32 accuracy: the tensor-core path multiplies BF16 tensor entries by a 3-part BF16 split
+ * of the Khatri-Rao operand, or FP32 entries as TF32 hi/lo pairs (three MMAs per step). */
+typedef enum { NTF_CONTRACT_AUTO = 0, NTF_CONTRACT_TENSOR = 1, NTF_CONTRACT_SIMT = 2 } ntf_contraction;
+
 typedef struct {
   int inner_iters;   /* L >= 1: update/projection/dual repetitions per factor (paper: 1) */
   int kr_source;     /* ntf_kr_source                                                    */
@@ -80,6 +87,7 @@ typedef struct {
   double tau_decr;
   double eps_abs;    /* stopping tolerances of Sec. III-C (paper: 1e-4, 1e-4)            */
   double eps_rel;
+  int contraction;   /* ntf_contraction (default AUTO)                                   */
 } ntf_params;
 
 /* Per-factor residuals of one update (Sec. III-C), all Frobenius norms. */

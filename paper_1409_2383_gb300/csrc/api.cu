@@ -32,6 +32,7 @@ struct ntf_ctx {
   cudaStream_t st = nullptr;
   ntf_params prm{};
   GemmPlan pn{}, pt{};
+  ntf::UmmaPlan un{}, ut{};      // tensor-core plans of the two contractions (on: used)
   int post_split_left = 1, post_split_right = 1;
   // workspace
   float* partial = nullptr;      // partial sums of the first contraction and of the posts
@@ -40,6 +41,8 @@ struct ntf_ctx {
   float* TL = nullptr;           // [Q_L, R]
   float* W = nullptr;            // Khatri-Rao table of the first contraction [K_pad, RP]
   float* W_b = nullptr;          // Khatri-Rao table of the second contraction
+  void* Wu = nullptr;            // split Khatri-Rao tables of the tensor-core contractions
+  void* Wu_b = nullptr;
   // side streams of a sweep: B runs the second contraction, C the coefficient systems
   cudaStream_t sB = nullptr, sC = nullptr;
   cudaEvent_t ev_start = nullptr, ev_tl = nullptr, ev_b = nullptr, ev_c = nullptr;
@@ -119,6 +122,8 @@ ntf_status check_params(const ntf_params* p) {
     return fail(NTF_ERR_INVALID_ARG, "penalty rule needs mu, tau_incr, tau_decr > 1");
   if (p->eps_abs < 0.0 || p->eps_rel < 0.0)
     return fail(NTF_ERR_INVALID_ARG, "negative stopping tolerance");
+  if (p->contraction < NTF_CONTRACT_AUTO || p->contraction > NTF_CONTRACT_SIMT)
+    return fail(NTF_ERR_INVALID_ARG, "unknown contraction engine %d", p->contraction);
   return NTF_OK;
 }
 
@@ -168,6 +173,20 @@ ntf_status prof_mark(ntf_ctx* c, int k, int which, cudaStream_t st) {
 // T_R[P_R, R] = X[P_R, Q_R] * KR(factors s_R..N-1), on stream st
 ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st) {
   const Group g = make_group(c, c->s_R, c->N - c->s_R, F);
+  if (c->un.on) {
+    NTF_CUDA(ntf::launch_kr_split(g, c->un, c->R, c->Wu, st));
+    const int chunks = c->un.args.chunks;
+    float* out = chunks > 1 ? c->partial : dst;
+    NTF_TRY(prof_mark(c, 0, 0, st));
+    NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, st));
+    NTF_TRY(prof_mark(c, 0, 1, st));
+    c->launches += 2;
+    if (chunks > 1) {
+      NTF_CUDA(ntf::launch_sum_splits(c->partial, chunks, c->P_R * c->R, dst, st));
+      c->launches += 1;
+    }
+    return NTF_OK;
+  }
   NTF_CUDA(ntf::launch_kr_table(g, c->Q_R, c->R, c->W, st));
   float* out = c->pn.chunks > 1 ? c->partial : dst;
   NTF_TRY(prof_mark(c, 0, 0, st));
@@ -184,6 +203,20 @@ ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStr
 // T_L[Q_L, R] = X[P_L, Q_L]^T * KR(factors 0..s_L-1), on stream st
 ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st) {
   const Group g = make_group(c, 0, c->s_L, F);
+  if (c->ut.on) {
+    NTF_CUDA(ntf::launch_kr_split(g, c->ut, c->R, c->Wu_b, st));
+    const int chunks = c->ut.args.chunks;
+    float* out = chunks > 1 ? c->partial_b : dst;
+    NTF_TRY(prof_mark(c, 1, 0, st));
+    NTF_CUDA(ntf::launch_umma(c->ut, out, &c->d_ctrl->status, st));
+    NTF_TRY(prof_mark(c, 1, 1, st));
+    c->launches += 2;
+    if (chunks > 1) {
+      NTF_CUDA(ntf::launch_sum_splits(c->partial_b, chunks, c->Q_L * c->R, dst, st));
+      c->launches += 1;
+    }
+    return NTF_OK;
+  }
   NTF_CUDA(ntf::launch_kr_table(g, c->P_L, c->R, c->W_b, st));
   float* out = c->pt.chunks > 1 ? c->partial_b : dst;
   NTF_TRY(prof_mark(c, 1, 0, st));
@@ -348,6 +381,8 @@ void free_ctx(ntf_ctx* c) {
   cudaFree(c->TL);
   cudaFree(c->W);
   cudaFree(c->W_b);
+  cudaFree(c->Wu);
+  cudaFree(c->Wu_b);
   cudaFree(c->partial_b);
   cudaFree(c->Mbuf);
   cudaFree(c->grams);
@@ -378,6 +413,7 @@ void ntf_default_params(ntf_params* p, int paper_mode) {
   p->tau_decr = 2.0;
   p->eps_abs = 1e-4;
   p->eps_rel = 1e-4;
+  p->contraction = NTF_CONTRACT_AUTO;
 }
 
 const char* ntf_status_string(ntf_status s) {
@@ -466,11 +502,31 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
   };
   e = cudaSuccess;
-  if (e == cudaSuccess) e = alloc((void**)&c->partial, part * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->TR, c->P_R * R * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->TL, c->Q_L * R * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->W, w_rows * ntf::round_rp(R) * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->W_b, w_rows_b * ntf::round_rp(R) * sizeof(float));
+  // tensor-core plans: the split tables must exist before the tensor maps are encoded
+  if (e == cudaSuccess && p->contraction != NTF_CONTRACT_SIMT) {
+    e = alloc(&c->Wu, ntf::umma_wsplit_bytes(c->Q_R, R, dtype));
+    if (e == cudaSuccess) e = alloc(&c->Wu_b, ntf::umma_wsplit_bytes(c->P_L, R, dtype));
+    if (e == cudaSuccess) {
+      const bool okn = ntf::umma_plan(&c->un, false, dtype, d_tensor, c->P_R, c->Q_R, R, c->Wu,
+                                      c->num_sms);
+      const bool okt = ntf::umma_plan(&c->ut, true, dtype, d_tensor, c->P_L, c->Q_L, R, c->Wu_b,
+                                      c->num_sms);
+      if (p->contraction == NTF_CONTRACT_TENSOR && !(okn && okt)) {
+        free_ctx(c);
+        return fail(NTF_ERR_UNSUPPORTED,
+                    "tensor-core contraction needs rank <= 64 and 16-byte aligned tensor rows");
+      }
+      if (c->un.on && c->un.args.chunks > 1)
+        part = std::max<int64_t>(part, c->un.args.chunks * c->P_R * R);
+      if (c->ut.on && c->ut.args.chunks > 1)
+        part_b = std::max<int64_t>(part_b, c->ut.args.chunks * c->Q_L * R);
+    }
+  }
+  if (e == cudaSuccess) e = alloc((void**)&c->partial, part * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->partial_b, part_b * sizeof(float));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sC, cudaStreamNonBlocking);

@@ -61,6 +61,36 @@ __global__ void k_kr_table(Group g, int64_t K, int R, int RP, int64_t n, float* 
   }
 }
 
+// Split Khatri-Rao table of the tensor-core contractions: [splits * N rows][K_pad], K
+// contiguous; row s * N + r holds part s of column r.  BF16: W = w1 + w2 + w3 with
+// w1 = bf16(W), w2 = bf16(W - w1), w3 = bf16(W - w1 - w2) (each remainder is exact in FP32).
+// FP32: W = wh + wl, wh = W truncated to TF32, wl = W - wh (exact).
+template <bool kBF16>
+__global__ void k_kr_split(Group g, int64_t K, int R, int N, int64_t K_pad, void* __restrict__ W) {
+  const int64_t n = static_cast<int64_t>(N) * K_pad;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < n;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(idx / K_pad);
+    const int64_t q = idx % K_pad;
+    const float w = (q < K && r < R) ? kr_entry(g, q, r, R) : 0.0f;
+    if constexpr (kBF16) {
+      __nv_bfloat16* o = static_cast<__nv_bfloat16*>(W);
+      const __nv_bfloat16 b1 = __float2bfloat16_rn(w);
+      const float r1 = w - __bfloat162float(b1);
+      const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(b2);
+      o[idx] = b1;
+      o[n + idx] = b2;
+      o[2 * n + idx] = __float2bfloat16_rn(r2);
+    } else {
+      float* o = static_cast<float*>(W);
+      const float hi = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+      o[idx] = hi;
+      o[n + idx] = w - hi;
+    }
+  }
+}
+
 // --------------------------------------------------------------------- reductions
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, int64_t n,
                              float* __restrict__ out) {
@@ -210,6 +240,17 @@ cudaError_t launch_kr_table(const Group& g, int64_t K, int R, float* W, cudaStre
   const int64_t n = kr_rows_padded(K) * RP;
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 4096));
   k_kr_table<<<blocks, 256, 0, st>>>(g, K, R, RP, n, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* Wsplit,
+                            cudaStream_t st) {
+  const int64_t n = static_cast<int64_t>(plan.N) * plan.K_pad;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 4096));
+  if (plan.f32)
+    k_kr_split<false><<<blocks, 256, 0, st>>>(g, plan.args.K, R, plan.N, plan.K_pad, Wsplit);
+  else
+    k_kr_split<true><<<blocks, 256, 0, st>>>(g, plan.args.K, R, plan.N, plan.K_pad, Wsplit);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // helpers.  Not part of the ABI (include/ntf.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -74,6 +75,41 @@ cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, cons
 cudaError_t launch_norm2(const void* X, int dtype, int64_t n, double* partial, int blocks,
                          double* out, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* in, uint16_t* out, int64_t n, cudaStream_t st);
+
+// umma_host.cu / umma_{bf16,f32}.cu: tensor-core contractions (tcgen05 + TMA).
+namespace umma {
+struct Args {
+  int64_t M;          // output rows
+  int64_t K;          // contraction length
+  int64_t chunk_len;  // contraction elements per K-chunk (a multiple of 64)
+  int R;              // output columns written (R <= N)
+  int tiles;          // ceil(M / 128)
+  int chunks;         // K-chunks (> 1: out holds chunk partial sums [chunks][M][R])
+  float* out;
+  int* err;           // device status word: kStTimeout is or-ed in on a timeout
+};
+}  // namespace umma
+
+struct UmmaPlan {
+  bool on = false;
+  bool transposed = false;  // GEMM-T (X^T W) rather than GEMM-N (X W)
+  bool f32 = false;         // FP32 storage (TF32 split) rather than BF16
+  int N = 0;                // MMA N: R rounded up to a multiple of 16
+  int splits = 0;           // parts of the W table (3 BF16 or 2 TF32)
+  int grid = 0;             // persistent CTAs
+  int64_t K_pad = 0;        // W table row length (multiple of 64)
+  umma::Args args{};        // out and err are set at launch
+  CUtensorMap tx{}, tw{};
+};
+// Plans the contraction of X viewed as [P, Q] (GEMM-T when transposed) with the split W table
+// at Wsplit (umma_wsplit_bytes bytes).  Returns false (plan.on = false) when the shape or
+// alignment does not admit the tensor-core path.
+bool umma_plan(UmmaPlan* plan, bool transposed, int dtype, const void* X, int64_t P, int64_t Q,
+               int R, void* Wsplit, int num_sms);
+size_t umma_wsplit_bytes(int64_t K, int R, int dtype);
+cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* Wsplit,
+                            cudaStream_t st);
+cudaError_t launch_umma(const UmmaPlan& plan, float* out, int* err, cudaStream_t st);
 
 // admm.cu
 cudaError_t launch_gram(const float* F, int64_t I, int R, double* G, cudaStream_t st);

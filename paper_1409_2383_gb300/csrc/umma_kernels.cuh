@@ -1,0 +1,523 @@
+// Tensor-core MTTKRP contractions (tcgen05 + TMA).  Included by umma_{bf16,f32}.cu.
+//
+// The two skinny contractions of the sweep (mttkrp.cu)
+//
+//   GEMM-N:  out[p, r] = sum_q X[p, q] W[q, r]        (A = X tile, K-major)
+//   GEMM-T:  out[q, r] = sum_p X[p, q] W[p, r]        (A = X^T tile, M-contiguous)
+//
+// run as D[128 x N] += A[128 x K] * B[K x N] on the 5th-generation tensor cores, with the
+// output rows (M = 128 per tile) on the TMEM lanes and the padded rank N on TMEM columns.
+//
+// Precision.  The tensor cores multiply 16-bit or TF32 operands exactly into FP32 sums, so
+// the FP32 contract is kept by splitting operands into sums of narrower parts:
+//   BF16 storage: X is exact in BF16; W = w1 + w2 + w3 with w1 = bf16(W),
+//                 w2 = bf16(W - w1), w3 = bf16(W - w1 - w2) (24 significant bits), and
+//                 X W = X w1 + X w2 + X w3 (one kind::f16 MMA per K step with the three
+//                 parts side by side in N, summed by the epilogue).
+//   FP32 storage: X = xh + xl and W = wh + wl with xh, wh = the value truncated to TF32
+//                 (10 stored mantissa bits) and xl, wl = the exact remainders; X W is formed
+//                 as xh wh + xh wl + xl wh (two kind::tf32 MMAs), dropping xl wl
+//                 (relative size 2^-22).  The split of X happens in shared memory between
+//                 the TMA load and the MMA (converter warps).
+//
+// CTA roles (persistent: one CTA per SM walks the (tile, K-chunk) work items):
+//   warps 0-3  epilogue: TMEM -> registers -> global, warp w owns TMEM lanes 32w..32w+31
+//   warp 4     TMA producer (one thread): X tile + all W split rows of the stage
+//   warp 5     MMA issuer (one thread): tcgen05.mma into a double-buffered accumulator; a
+//              tile's contraction range is accumulated in segments of 8 stages, each in a
+//              fresh accumulator that the epilogue adds into FP32 registers
+//   warps 6-9  (FP32 only) converters: split X into hi/lo operand tiles
+// Stages form a ring guarded by mbarriers (full: TMA bytes landed; ready: converted; empty:
+// the MMAs reading the stage completed).  Every wait is bounded: on timeout the kernel sets
+// the timeout bit in *err, every role leaves its loop, outstanding copies and MMAs are
+// drained (bounded), and the TMEM is freed before the CTA exits.
+#pragma once
+#include <cuda.h>
+
+#include "ntf_internal.cuh"
+
+namespace ntf {
+namespace umma {
+
+constexpr int kTileM = 128;
+constexpr int kSmemBudget = 200 * 1024;
+constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
+
+template <bool kT, bool kF32, int kN>
+struct Cfg {
+  static constexpr int kStageK = kF32 ? 32 : 64;   // K per stage: 128 bytes of one row
+  static constexpr int kSplits = kF32 ? 2 : 3;     // W parts
+  static constexpr int kABytes = kTileM * 128;     // operand tile (hi part for FP32)
+  static constexpr int kLoBytes = kF32 ? kTileM * 128 : 0;
+  static constexpr int kRawBytes = (kF32 && kT) ? kTileM * 128 : 0;  // untransposed X rows
+  static constexpr int kWBytes = kSplits * kN * 128;
+  static constexpr int kStageBytes = kABytes + kLoBytes + kRawBytes + kWBytes;
+  static constexpr int kStagesRaw = kSmemBudget / kStageBytes;
+  static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
+  static constexpr int kTxBytes = ((kF32 && kT) ? kRawBytes : kABytes) + kWBytes;
+  static constexpr int kWarps = kF32 ? 10 : 6;
+  static constexpr int kThreads = kWarps * 32;
+  // Accumulator of one segment: one N-column block per W part (x w1 | x w2 | x w3 for BF16,
+  // xh wh | xh wl + xl wh for FP32); two of them alternate between MMA and epilogue.
+  static constexpr int kAccCols = kSplits * kN;
+  static constexpr int kAccStride = kAccCols <= 32 ? 32 : kAccCols <= 64 ? 64 : kAccCols <= 128 ? 128 : 256;
+  static constexpr int kTmemCols = 2 * kAccStride;
+  // Stages accumulated in TMEM before the epilogue takes the partial sum into FP32 registers.
+  // The tensor-core accumulation does not round to nearest (each MMA adds a small one-sided
+  // error, ~2^-24 of the sum); capping the number of MMAs per accumulator caps that bias
+  // at 32 main-block additions (~2e-6 relative), and the register sums round to nearest.
+  static constexpr int kSegStages = 8;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+  static_assert(kStages >= 2, "stage does not fit");
+  static_assert(kStageBytes % 1024 == 0, "stage pieces must stay 1024-byte aligned");
+  static_assert(kN % 16 == 0 && kN >= 16 && kN <= 64, "N must be 16..64 in steps of 16");
+  static_assert(kTmemCols <= 512, "accumulators exceed the tensor memory");
+};
+
+// Args (the work-item description shared with the host) is declared in ntf_internal.cuh.
+
+// ----------------------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(b)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase of parity `parity` to complete; false on timeout or, when
+// abort_flag is given, once another role has given up.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
+                                         volatile int* abort_flag) {
+  uint64_t t0 = 0;
+  for (uint32_t n = 0;; ++n) {
+    if (bar_try(b, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if ((n & 255u) == 0) {
+      const uint64_t t = now_ns();
+      if (n == 0) t0 = t;
+      else if (t - t0 > kWaitNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                       uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading / stride byte offsets,
+// the fixed version bits 46-48 = 0b001, 128-byte swizzle (mode 2 in bits 61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, operand formats (f16 kind: 1 = BF16; tf32 kind:
+// 2 = TF32), A major-ness (0 = K-major, 1 = M-contiguous), N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t a_mn, int n, int m) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (a_mn << 15) |
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+template <bool kF32>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t acc) {
+  if constexpr (kF32)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          saddr(b))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes (one row per lane).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// TF32 split: hi keeps sign, exponent and the 10 leading mantissa bits; lo = x - hi exactly.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// ---------------------------------------------------------------------------- kernel
+template <bool kT, bool kF32, int kN>
+__global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
+    k_umma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw,
+           Args a) {
+  using C = Cfg<kT, kF32, kN>;
+  constexpr int S = C::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full[S], ready[S], empty[S], tfull[2], tempty[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base_s = (saddr(smem_raw) + 1023u) & ~1023u;
+  uint8_t* base = smem_raw + (base_s - saddr(smem_raw));
+  const int items = a.tiles * a.chunks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&ready[s], 4);
+      bar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&tfull[b], 1);
+      bar_init(&tempty[b], 4);
+    }
+    bar_init(&drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     saddr(&tmem_base)),
+                 "r"(C::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  volatile int* abrt = &abort_flag;
+  auto give_up = [&]() {
+    if (!*abrt) {
+      *abrt = 1;
+      atomicOr(a.err, kStTimeout);
+    }
+  };
+
+  auto stage_ptr = [&](int slot) { return base + slot * C::kStageBytes; };
+  // piece offsets within a stage
+  constexpr int kOffA = 0, kOffLo = C::kABytes, kOffRaw = kOffLo + C::kLoBytes,
+                kOffW = kOffRaw + C::kRawBytes;
+
+  if (warp == 4) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tx)) : "memory");
+      asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tw)) : "memory");
+      uint32_t g = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int tile = it % a.tiles, ch = it / a.tiles;
+        const int64_t k0 = ch * a.chunk_len;
+        const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
+        const int nks = static_cast<int>((k1 - k0 + C::kStageK - 1) / C::kStageK);
+        for (int ks = 0; ks < nks; ++ks, ++g) {
+          const int slot = g % S;
+          if (!bar_wait(&empty[slot], ((g / S) & 1) ^ 1, abrt)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          uint8_t* st = stage_ptr(slot);
+          bar_arrive_tx(&full[slot], C::kTxBytes);
+          const int kx = static_cast<int>(k0 + ks * C::kStageK);
+          const int m0 = tile * kTileM;
+          if constexpr (!kT) {
+            tma_2d(st + kOffA, &tx, kx, m0, &full[slot]);
+          } else if constexpr (!kF32) {
+            tma_2d(st + kOffA, &tx, m0, kx, &full[slot]);
+            tma_2d(st + kOffA + kTileM * 64, &tx, m0 + 64, kx, &full[slot]);
+          } else {
+            tma_2d(st + kOffRaw, &tx, m0, kx, &full[slot]);
+          }
+          tma_2d(st + kOffW, &tw, kx, 0, &full[slot]);
+        }
+      }
+      // copies still in flight (only possible after a timeout) land before the CTA exits:
+      // the last use of every slot has completed its phase
+      if (!ok)
+        for (uint32_t h = g > S ? g - S : 0; h < g; ++h) bar_wait(&full[h % S], (h / S) & 1, nullptr);
+    }
+  } else if (warp == 5) {
+    // ------------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      // BF16: one MMA per K step, B = [w1 | w2 | w3] (N' = 3N) -> the three column blocks.
+      // FP32: xh [wh | wl] (N' = 2N) -> blocks 0 and 1, then xl wh -> block 1.
+      constexpr uint32_t kIdWide =
+          idesc(kF32 ? 2u : 1u, (kT && !kF32) ? 1u : 0u, C::kAccCols, kTileM);
+      constexpr uint32_t kIdLo = idesc(2u, 0u, kN, kTileM);
+      uint32_t g = 0, u = 0;
+      bool ok = true, issued = false;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int ch = it / a.tiles;
+        const int64_t k0 = ch * a.chunk_len;
+        const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
+        const int nks = static_cast<int>((k1 - k0 + C::kStageK - 1) / C::kStageK);
+        for (int s0 = 0; s0 < nks && ok; s0 += C::kSegStages, ++u) {
+          const int s1 = nks < s0 + C::kSegStages ? nks : s0 + C::kSegStages;
+          const uint32_t b = u & 1;
+          if (!bar_wait(&tempty[b], ((u >> 1) & 1) ^ 1, abrt)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t d = tmem + b * C::kAccStride;
+          for (int ks = s0; ks < s1; ++ks, ++g) {
+            const int slot = g % S;
+            if (!bar_wait(kF32 ? &ready[slot] : &full[slot], (g / S) & 1, abrt)) {
+              give_up();
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t st = base_s + slot * C::kStageBytes;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t acc = (ks != s0 || k != 0);
+              const uint64_t w = sdesc(st + kOffW + k * 32, 16, 1024);
+              if constexpr (kF32) {
+                const uint64_t ah = sdesc(st + kOffA + k * 32, 16, 1024);
+                const uint64_t al = sdesc(st + kOffLo + k * 32, 16, 1024);
+                mma<true>(d, ah, w, kIdWide, acc);
+                mma<true>(d + kN, al, w, kIdLo, 1);
+              } else {
+                // K-major A: 32 bytes per K step inside the swizzled row; M-contiguous A:
+                // 16 K rows of 128 bytes per step, the two 64-column halves 8 KB apart.
+                const uint64_t aa = kT ? sdesc(st + kOffA + k * 2048, kTileM * 64, 1024)
+                                       : sdesc(st + kOffA + k * 32, 16, 1024);
+                mma<false>(d, aa, w, kIdWide, acc);
+              }
+            }
+            issued = true;
+            mma_commit(&empty[slot]);
+          }
+          if (!ok) break;
+          mma_commit(&tfull[b]);
+        }
+      }
+      if (!ok && issued) {  // let every issued MMA finish before the TMEM is released
+        mma_commit(&drain);
+        bar_wait(&drain, 0, nullptr);
+      }
+    }
+  } else if (warp < 4) {
+    // --------------------------------------------------------------------- epilogue
+    uint32_t u = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      const int tile = it % a.tiles, ch = it / a.tiles;
+      const int64_t k0 = ch * a.chunk_len;
+      const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
+      const int nks = static_cast<int>((k1 - k0 + C::kStageK - 1) / C::kStageK);
+      float v[kN];
+#pragma unroll
+      for (int c = 0; c < kN; ++c) v[c] = 0.0f;
+      for (int s0 = 0; s0 < nks; s0 += C::kSegStages, ++u) {
+        const uint32_t b = u & 1;
+        ok = __all_sync(0xffffffffu, bar_wait(&tfull[b], (u >> 1) & 1, abrt));
+        if (!ok) {
+          if (lane == 0) give_up();
+          break;
+        }
+        fence_after();
+        const uint32_t taddr =
+            tmem + (static_cast<uint32_t>(warp * 32) << 16) + b * C::kAccStride;
+#pragma unroll
+        for (int c = 0; c < kN; c += 16) {
+          float p0[16], p1[16], p2[16];
+          tmem_ld16(taddr + c, p0);
+          tmem_ld16(taddr + kN + c, p1);
+          if constexpr (C::kSplits == 3) tmem_ld16(taddr + 2 * kN + c, p2);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float corr = C::kSplits == 3 ? p1[i] + p2[i] : p1[i];
+            v[c + i] += p0[i] + corr;
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&tempty[b]);
+      }
+      if (!ok) break;
+      const int64_t row = static_cast<int64_t>(tile) * kTileM + warp * 32 + lane;
+      if (row < a.M) {
+        float* o = a.out + (static_cast<int64_t>(ch) * a.M + row) * a.R;
+        if ((a.R & 3) == 0) {
+#pragma unroll
+          for (int c = 0; c < kN; c += 4)
+            if (c < a.R)
+              *reinterpret_cast<float4*>(o + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < kN; ++c)
+            if (c < a.R) o[c] = v[c];
+        }
+      }
+    }
+  } else if constexpr (kF32) {
+    // ------------------------------------------------------------------- converters
+    const int t = threadIdx.x - 6 * 32;  // 0..127
+    uint32_t g = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      const int ch = it / a.tiles;
+      const int64_t k0 = ch * a.chunk_len;
+      const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
+      const int nks = static_cast<int>((k1 - k0 + C::kStageK - 1) / C::kStageK);
+      for (int ks = 0; ks < nks; ++ks, ++g) {
+        const int slot = g % S;
+        ok = __all_sync(0xffffffffu, bar_wait(&full[slot], (g / S) & 1, abrt));
+        if (!ok) {
+          if (lane == 0) give_up();
+          break;
+        }
+        uint8_t* st = stage_ptr(slot);
+        if constexpr (!kT) {
+          // in place: the hi part overwrites X, the lo part goes to the same offset of the
+          // lo tile, so both keep the swizzled layout the TMA wrote
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int off = (t + 128 * i) * 16;
+            const float4 x = *reinterpret_cast<const float4*>(st + kOffA + off);
+            float4 h, l;
+            split_tf32(x.x, h.x, l.x);
+            split_tf32(x.y, h.y, l.y);
+            split_tf32(x.z, h.z, l.z);
+            split_tf32(x.w, h.w, l.w);
+            *reinterpret_cast<float4*>(st + kOffA + off) = h;
+            *reinterpret_cast<float4*>(st + kOffLo + off) = l;
+          }
+        } else {
+          // transpose: raw rows [32 K][128 M] (plain layout) -> K-major rows of the
+          // operand tiles, 128 bytes (32 K values) per M row, 16-byte chunk c stored at
+          // chunk position c ^ (m & 7) (the 128-byte swizzle)
+          const float* raw = reinterpret_cast<const float*>(st + kOffRaw);
+          const int m = t;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            float4 h, l;
+            split_tf32(raw[(4 * c + 0) * kTileM + m], h.x, l.x);
+            split_tf32(raw[(4 * c + 1) * kTileM + m], h.y, l.y);
+            split_tf32(raw[(4 * c + 2) * kTileM + m], h.z, l.z);
+            split_tf32(raw[(4 * c + 3) * kTileM + m], h.w, l.w);
+            const int off = m * 128 + ((c ^ (m & 7)) << 4);
+            *reinterpret_cast<float4*>(st + kOffA + off) = h;
+            *reinterpret_cast<float4*>(st + kOffLo + off) = l;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) bar_arrive(&ready[slot]);
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(C::kTmemCols));
+  }
+}
+
+}  // namespace umma
+}  // namespace ntf
+
+namespace ntf {
+namespace umma {
+
+template <bool kT, bool kF32, int kN>
+cudaError_t run(const UmmaPlan& p, const Args& a, cudaStream_t st) {
+  using C = Cfg<kT, kF32, kN>;
+  auto kern = k_umma<kT, kF32, kN>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<p.grid, C::kThreads, C::kSmemBytes, st>>>(p.tx, p.tw, a);
+  return cudaGetLastError();
+}
+
+template <bool kF32>
+cudaError_t dispatch(const UmmaPlan& p, const Args& a, cudaStream_t st) {
+  switch (p.N * 2 + (p.transposed ? 1 : 0)) {
+    case 32: return run<false, kF32, 16>(p, a, st);
+    case 33: return run<true, kF32, 16>(p, a, st);
+    case 64: return run<false, kF32, 32>(p, a, st);
+    case 65: return run<true, kF32, 32>(p, a, st);
+    case 96: return run<false, kF32, 48>(p, a, st);
+    case 97: return run<true, kF32, 48>(p, a, st);
+    case 128: return run<false, kF32, 64>(p, a, st);
+    case 129: return run<true, kF32, 64>(p, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace umma
+}  // namespace ntf

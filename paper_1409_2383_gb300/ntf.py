@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libntf.so")
 NTF_F32, NTF_BF16 = 0, 1
 NTF_KR_PRIMAL, NTF_KR_AUX = 0, 1
 NTF_RHO_ADAPTIVE, NTF_RHO_TRACE, NTF_RHO_FIXED = 0, 1, 2
+NTF_CONTRACT_AUTO, NTF_CONTRACT_TENSOR, NTF_CONTRACT_SIMT = 0, 1, 2
 
 STATUS = {
     0: "NTF_OK", 1: "NTF_ERR_INVALID_ARG", 2: "NTF_ERR_CUDA", 3: "NTF_ERR_OOM",
@@ -38,7 +39,7 @@ class Params(ctypes.Structure):
                 ("rho_policy", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("mu", ctypes.c_double), ("tau_incr", ctypes.c_double),
                 ("tau_decr", ctypes.c_double), ("eps_abs", ctypes.c_double),
-                ("eps_rel", ctypes.c_double)]
+                ("eps_rel", ctypes.c_double), ("contraction", ctypes.c_int)]
 
 
 class UpdateStats(ctypes.Structure):
@@ -405,4 +406,5 @@ def zeros_state(dims: Sequence[int], R: int, device="cuda") -> List[torch.Tensor
 __all__ = ["Context", "Params", "NTFError", "default_params", "to_bf16", "lib", "zeros_state",
            "mttkrp_noalloc", "Mlp",
            "NTF_F32", "NTF_BF16", "NTF_KR_PRIMAL", "NTF_KR_AUX", "NTF_RHO_ADAPTIVE",
-           "NTF_RHO_TRACE", "NTF_RHO_FIXED", "LIB_PATH"]
+           "NTF_RHO_TRACE", "NTF_RHO_FIXED", "NTF_CONTRACT_AUTO", "NTF_CONTRACT_TENSOR",
+           "NTF_CONTRACT_SIMT", "LIB_PATH"]

@@ -121,3 +121,41 @@ def eval_loss(net: ntf.Mlp, rows: RowSet, groups_per_batch: int) -> float:
         tot += loss * tg.numel()
         cnt += tg.numel()
     return tot / max(cnt, 1)
+
+
+def time_to_fit(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], target: float,
+                max_outer: int, net: Optional[ntf.Mlp] = None, repeats: int = 1,
+                params: Optional[ntf.Params] = None):
+    """Time (CUDA events) of factorizations from `init` until rel_err <= target, on a fresh
+    non-default stream (so the sweep is replayed as a CUDA graph).  Returns a dict with the
+    median seconds, iterations, final error and the warm-start row counts."""
+    p = params or ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    stream = torch.cuda.Stream()
+    times, res = [], None
+    with torch.cuda.stream(stream):
+        A = [f.clone() for f in init]
+        At = [f.clone() for f in init]
+        Y = [torch.zeros_like(f) for f in init]
+        with ntf.Context(X, R, p, stream=stream) as ctx:
+            if net is not None:
+                ctx.attach_warmstart(net)
+            ctx.profile_enable(True)             # recorded in the graph from the first run
+            prof0 = prof = ctx.profile_get()
+            for rep in range(repeats + 1):      # the first run records the graph
+                for a, t, y, f in zip(A, At, Y, init):
+                    a.copy_(f)
+                    t.copy_(f)
+                    y.zero_()
+                prof0 = ctx.profile_get()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = ctx.run(A, At, Y, max_outer, target_rfe=target)
+                e1.record(stream)
+                e1.synchronize()
+                prof = ctx.profile_get()
+                if rep > 0 or repeats == 0:
+                    times.append(e0.elapsed_time(e1) / 1000.0)
+    return {"seconds": float(np.median(times)), "iters": res["iters"],
+            "rel_err": res["rel_err"], "reached": bool(res["reached_target"]),
+            "ws_considered": prof["ws_rows_considered"] - prof0["ws_rows_considered"],
+            "ws_accepted": prof["ws_rows_accepted"] - prof0["ws_rows_accepted"]}

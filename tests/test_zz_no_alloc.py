@@ -4,8 +4,9 @@ Some callers of this library cannot allocate device memory on their call path (s
 reserve all device memory at start-up and treat later allocations as failures).
 ``ntf_mttkrp_noalloc`` serves them: it needs no context and keeps its scratch in a static
 device array.  Here it is called through the C ABI twice in a row for every mode of several
-tensors and compared with ``ntf_mttkrp`` of a context, within the tolerance of the other
-parity tests (relative Frobenius error 1e-5)."""
+tensors and compared with ``ntf_mttkrp`` of a context that uses the same FP32 FMA
+contraction kernels, within the tolerance of the other parity tests (relative Frobenius
+error 1e-5)."""
 import ctypes
 
 import numpy as np
@@ -43,7 +44,7 @@ def test_noalloc_matches_context_mttkrp_on_two_calls(ntf, dims, R, dtype):
     g = torch.Generator().manual_seed(sum(dims) + R)
     X = (torch.rand(dims, generator=g) - 0.3).to(dtype).cuda()
     F = [torch.rand(d, R, generator=g).cuda() for d in dims]
-    with ntf.Context(X, R) as ctx:
+    with ntf.Context(X, R, ntf.default_params(contraction=ntf.NTF_CONTRACT_SIMT)) as ctx:
         want = [ctx.mttkrp(n, F).clone() for n in range(len(dims))]
     outs = [torch.empty(d, R, device="cuda") for d in dims]
     for call in range(2):
