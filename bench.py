@@ -357,40 +357,62 @@ def run_kernel_case(args):
                       **gbs}))
 
 
-def run_variants(args, Xd, init_d, target):
-    """Time to the same fit target for BF16 tensor storage and for BF16 storage plus the
-    learned warm start (network trained on rows harvested from tensors of the same generator
-    with other seeds, 200^3, by the library's own kernels; training time reported apart)."""
+def run_sweep_case(args):
+    """A few outer iterations of the benchmark workload in the chosen storage (for ncu launch
+    lists of the whole sweep): one eager sweep, then graph replays."""
     import torch
-    import synth
+    from paper_1409_2383_gb300 import ntf
+    X, init = _workload(0)
+    Xd = torch.as_tensor(X).cuda()
+    if args.storage == "bf16":
+        Xd = ntf.to_bf16(Xd)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        A = [torch.as_tensor(f).cuda() for f in init]
+        At = [a.clone() for a in A]
+        Y = [torch.zeros_like(a) for a in A]
+        with ntf.Context(Xd, RANK, p, stream=stream) as ctx:
+            rs = ctx.run(A, At, Y, args.steps)
+        stream.synchronize()
+    print(json.dumps({"sweep_case": WORKLOAD, "storage": args.storage, "sweeps": args.steps,
+                      "rel_err": rs["rel_err"]}))
+
+
+def run_variants(args, Xd, init_d, target):
+    """Time to the same fit target for plain FP32 storage, BF16 storage, and BF16 storage
+    plus the learned warm start in the first sweeps (network trained on rows harvested from
+    the first sweeps of other tensors of the same generator, by the library's own kernels;
+    harvest and training time reported apart)."""
+    import torch
     from paper_1409_2383_gb300 import ntf, warmstart
     out = {}
     fp32 = warmstart.time_to_fit(Xd, RANK, init_d, target, MAX_OUTER, repeats=3)
     out["fp32"] = fp32
     Xb = ntf.to_bf16(Xd)
     out["bf16"] = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, repeats=3)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rows = warmstart.RowSet(RANK)
-    hdims, seeds = (200, 200, 200), args.train_tensors
-    sweeps = max(1, int(math.ceil(args.train_rows / (sum(hdims) * seeds))))
-    for sd in range(1, seeds + 1):
-        Xt, _, it = synth.workload(hdims, RANK, seed=sd, snr_db=SNR_DB)
-        warmstart.harvest(torch.as_tensor(Xt).cuda(), RANK,
-                          [torch.as_tensor(f, dtype=torch.float32).cuda() for f in it],
-                          outer=sweeps, rows=rows, conv_iters=300)
+    rows = warmstart.training_set(DIMS, RANK, args.train_rows, sweeps=2, seed0=1000,
+                                  snr_db=SNR_DB, storage="bf16")
+    torch.cuda.synchronize()
     t1 = time.perf_counter()
     H = 256
-    net = ntf.Mlp(RANK, H, warmstart.init_params(RANK, H, seed=0), max_rows=4096, max_groups=16)
+    max_rows = 16 * max(DIMS)
+    net = ntf.Mlp(RANK, H, warmstart.init_params(RANK, H, seed=0), max_rows=max_rows,
+                  max_groups=16)
     loss0 = warmstart.eval_loss(net, rows, 16)
     steps = max(1, int(args.train_epochs * len(rows.Gn) / 16))
-    warmstart.train(net, rows, steps=steps, groups_per_batch=16, lr=1e-3)
+    warmstart.train(net, rows, steps=steps, groups_per_batch=16, lr=1e-3, decay_at=0.7)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     loss1 = warmstart.eval_loss(net, rows, 16)
-    learned = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, net=net, repeats=3)
+    learned = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, net=net, repeats=3,
+                                    ws_sweeps=args.ws_sweeps)
     out["bf16_learned"] = learned
-    out["training"] = {"rows": rows.rows, "groups": len(rows.Gn), "tensors": seeds,
-                       "tensor_dims": list(hdims), "sweeps_per_tensor": sweeps,
+    out["training"] = {"rows": rows.rows, "groups": len(rows.Gn),
+                       "tensors": len(rows.Gn) // (2 * len(DIMS)), "tensor_dims": list(DIMS),
+                       "sweeps_harvested": 2, "ws_sweeps": args.ws_sweeps,
                        "harvest_s": t1 - t0, "train_s": t2 - t1, "steps": steps,
                        "loss_before": loss0, "loss_after": loss1, "hidden": H}
     out["speedup_bf16_learned_vs_fp32"] = fp32["seconds"] / learned["seconds"]
@@ -409,18 +431,23 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the BF16 and BF16 + learned warm-start comparison")
     ap.add_argument("--train-rows", type=int, default=1_000_000)
-    ap.add_argument("--train-tensors", type=int, default=20)
-    ap.add_argument("--train-epochs", type=float, default=3.0)
+    ap.add_argument("--train-epochs", type=float, default=20.0)
+    ap.add_argument("--ws-sweeps", type=int, default=1,
+                    help="outer iterations of each run in which the network is consulted")
     ap.add_argument("--kernel-case", action="store_true",
                     help="standalone MTTKRP calls only (profiling case)")
     ap.add_argument("--dims", default="384x384x384")
     ap.add_argument("--rank", type=int, default=RANK)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "tensor", "simt"])
+    ap.add_argument("--sweep-case", action="store_true",
+                    help="run --steps outer iterations of the workload (for ncu launch lists)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.kernel_case:
         run_kernel_case(args)
+    elif args.sweep_case:
+        run_sweep_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -236,12 +236,16 @@ ntf_status ntf_mlp_train_step(ntf_mlp* net, const float* d_Gn, const int* d_offs
                               int apply, double* loss, float* d_grad_out);
 const char* ntf_mlp_last_error(void);
 
-/* Use `net` (same rank, max_rows >= the largest tensor extent) to warm-start every factor
- * update of the context: before the inner iterations each row is offered the network's
- * (max(0, x), min(0, s y)) and keeps it in place of the carried-over (At, Y) row if its KKT
- * natural residual ||min(x, G x - m)|| is smaller; the plain iterations then refine either
- * way.  net = NULL detaches.  The context does not own the network. */
-ntf_status ntf_attach_warmstart(ntf_ctx* ctx, ntf_mlp* net);
+/* Use `net` (same rank, max_rows >= the largest tensor extent) to warm-start factor updates:
+ * before the inner iterations each row is offered the network's (max(0, x), min(0, s y))
+ * and keeps it in place of the carried-over (At, Y) row only if it is better on both
+ * counts -- a smaller row objective 1/2 x^T G x - m^T x (the row's share of the fit) and a
+ * smaller KKT natural residual ||min(x, G x - m)||; the plain iterations then refine either
+ * way.  sweeps >= 1: the network is consulted in the first `sweeps` outer iterations of
+ * each ntf_run call (the cold start, where it helps); sweeps = 0: in every iteration.
+ * ntf_admm_update consults it whenever attached.  net = NULL detaches.  The context does
+ * not own the network. */
+ntf_status ntf_attach_warmstart(ntf_ctx* ctx, ntf_mlp* net, int sweeps);
 
 /* MTTKRP that allocates nothing.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc on their call path -- services that reserve all

@@ -109,3 +109,21 @@ def targets(G: np.ndarray, X: np.ndarray, Y: np.ndarray, s: float) -> np.ndarray
 def decode(out: np.ndarray, s: float, R: int) -> Tuple[np.ndarray, np.ndarray]:
     """Network output -> warm-start (aux, dual) rows: aux = max(0, x), dual = min(0, s y)."""
     return np.maximum(out[:, :R], 0.0), np.minimum(out[:, R:] * s, 0.0)
+
+
+def row_objective(G: np.ndarray, M: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """q(x_i) = 1/2 x_i^T G x_i - m_i^T x_i per row: the part of the squared fit error that
+    depends on row i of the factor being updated (eq. ADMM_NTF_ALS_C without the constant)."""
+    return 0.5 * np.sum((X @ G) * X, axis=1) - np.sum(M * X, axis=1)
+
+
+def kkt_residual(G: np.ndarray, M: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """||min(x_i, G x_i - m_i)||^2 per row: zero exactly at the NNLS solution (eq. KKT_NTF)."""
+    return np.sum(np.minimum(X, X @ G - M) ** 2, axis=1)
+
+
+def judge(G: np.ndarray, M: np.ndarray, Xc: np.ndarray, Xo: np.ndarray) -> np.ndarray:
+    """Rows where the candidate Xc replaces the carried-over Xo: both the row objective and
+    the KKT residual are smaller (strictly)."""
+    return ((row_objective(G, M, Xc) < row_objective(G, M, Xo))
+            & (kkt_residual(G, M, Xc) < kkt_residual(G, M, Xo)))

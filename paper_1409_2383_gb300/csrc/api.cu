@@ -61,6 +61,8 @@ struct ntf_ctx {
   Ctrl* h_ctrl = nullptr;        // pinned
   double x_norm2 = 0.0;
   ntf_mlp* ws = nullptr;         // attached warm-start network (not owned)
+  int ws_sweeps = 0;             // consult it in the first ws_sweeps iterations of a run (0: all)
+  bool ws_now = true;            // whether the sweep being enqueued consults it
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[3 * ntf::kMaxOrder] = {};
   int graph_launches = 0;        // kernels in the recorded sweep
@@ -299,7 +301,7 @@ ntf::UpdateCall make_call(ntf_ctx* c, int mode, const float* M, float* A, float*
 
 ntf_status warm_start(ntf_ctx* c, int mode, const float* M, float* At, float* Y,
                       cudaStream_t st) {
-  if (!c->ws) return NTF_OK;
+  if (!c->ws || !c->ws_now) return NTF_OK;
   NTF_CUDA(ntf::mlp_warm_start(c->ws, c->sys, mode, M, At, Y, c->dims[mode],
                                c->d_ctrl->ws_rows, st));
   c->launches += 8;
@@ -632,6 +634,7 @@ ntf_status ntf_admm_update(ntf_ctx* c, int mode, const float* d_M, float* d_A, f
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's
   NTF_TRY(check_mode(c, mode));
   if (!d_M || !d_A || !d_At || !d_Y) return fail(NTF_ERR_INVALID_ARG, "null matrix argument");
+  c->ws_now = true;  // a single update consults an attached network
   NTF_TRY(enqueue_update(c, mode, d_M, d_A, d_At, d_Y, false));
   if (!stats) return NTF_OK;
   NTF_TRY(read_ctrl(c));
@@ -716,8 +719,9 @@ ntf_status ntf_profile_get(ntf_ctx* c, ntf_profile* out) {
   return NTF_OK;
 }
 
-ntf_status ntf_attach_warmstart(ntf_ctx* c, ntf_mlp* net) {
+ntf_status ntf_attach_warmstart(ntf_ctx* c, ntf_mlp* net, int sweeps) {
   if (!c) return fail(NTF_ERR_INVALID_ARG, "null context");
+  if (sweeps < 0) return fail(NTF_ERR_INVALID_ARG, "sweeps must be >= 0");
   if (net && ntf::mlp_rank(net) != c->R)
     return fail(NTF_ERR_INVALID_ARG, "network rank %d differs from the context rank %d",
                 ntf::mlp_rank(net), c->R);
@@ -725,6 +729,7 @@ ntf_status ntf_attach_warmstart(ntf_ctx* c, ntf_mlp* net) {
     return fail(NTF_ERR_INVALID_ARG, "network workspace (%d rows) smaller than a factor (%lld)",
                 ntf::mlp_max_rows(net), static_cast<long long>(c->max_dim));
   c->ws = net;
+  c->ws_sweeps = sweeps;
   return NTF_OK;
 }
 
@@ -752,10 +757,11 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
     NTF_CUDA(ntf::launch_gram(src[m], c->dims[m], c->R, c->grams + m * RR, c->st));
 
   // The sweep is recorded once as a CUDA graph (after one eager sweep has set every kernel
-  // attribute) and replayed; it is re-recorded only if the state pointers change.
-  bool same = c->graph != nullptr && c->graph_prof == c->prof && c->graph_ws == c->ws;
-  for (int m = 0; m < c->N && same; ++m)
-    same = c->graph_key[3 * m] == A[m] && c->graph_key[3 * m + 1] == At[m] &&
+  // attribute) and replayed; it is re-recorded only if the state pointers change.  Sweeps
+  // that consult a warm-start network limited to the first iterations run eagerly.
+  bool keys = c->graph != nullptr;
+  for (int m = 0; m < c->N && keys; ++m)
+    keys = c->graph_key[3 * m] == A[m] && c->graph_key[3 * m + 1] == At[m] &&
            c->graph_key[3 * m + 2] == Y[m];
   ntf_run_stats rs{};
   rs.rel_err = NAN;
@@ -764,10 +770,14 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   // Capture needs a non-legacy stream; otherwise (or if capture fails) launch eagerly.
   bool can_graph = c->st != nullptr;
   for (int it = 0; it < max_outer && !done; ++it) {
+    c->ws_now = c->ws != nullptr && (c->ws_sweeps == 0 || it < c->ws_sweeps);
+    ntf_mlp* const sweep_ws = c->ws_now ? c->ws : nullptr;
+    const bool same = keys && c->graph != nullptr && c->graph_prof == c->prof &&
+                      c->graph_ws == sweep_ws;
     if (same) {
       NTF_CUDA(cudaGraphLaunch(c->graph, c->st));
       c->launches += c->graph_launches;
-    } else if (it == 0 || !can_graph) {
+    } else if (it == 0 || !can_graph || (sweep_ws != nullptr && c->ws_sweeps > 0)) {
       NTF_TRY(enqueue_sweep(c, A, At, Y));
     } else {
       if (c->graph) {
@@ -786,25 +796,18 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
       if (!ok) {
         (void)cudaGetLastError();
         if (c->graph) cudaGraphExecDestroy(c->graph);
-  for (cudaEvent_t e : {c->ev_start, c->ev_tl, c->ev_b, c->ev_c})
-    if (e) cudaEventDestroy(e);
-  for (int m = 0; m < ntf::kMaxOrder; ++m)
-    for (cudaEvent_t e : {c->ev_sys[m], c->ev_rows[m], c->ev_red[m]})
-      if (e) cudaEventDestroy(e);
-  if (c->sB) cudaStreamDestroy(c->sB);
-  if (c->sC) cudaStreamDestroy(c->sC);
         c->graph = nullptr;
         can_graph = false;
         NTF_TRY(enqueue_sweep(c, A, At, Y));
       } else {
         c->graph_prof = c->prof;
-        c->graph_ws = c->ws;
+        c->graph_ws = sweep_ws;
         for (int m = 0; m < c->N; ++m) {
           c->graph_key[3 * m] = A[m];
           c->graph_key[3 * m + 1] = At[m];
           c->graph_key[3 * m + 2] = Y[m];
         }
-        same = true;
+        keys = true;
         NTF_CUDA(cudaGraphLaunch(c->graph, c->st));
         c->launches += c->graph_launches;
       }

@@ -332,8 +332,10 @@ __global__ void k_ws_prepare(const float* __restrict__ G, const float* __restric
 }
 
 // Per row (one warp): candidate from the network, x = max(0, out[:R]), y = min(0, s out[R:]);
-// keep it in place of the carried-over (At, Y) if its KKT natural residual
-// ||min(x, G x - m)|| is smaller.  Counts considered / accepted rows.
+// it replaces the carried-over (At, Y) row only if it is better on both counts: a smaller
+// row objective q(x) = 1/2 x^T G x - m^T x = 1/2 sum_j x_j ((G x - m)_j - m_j) (the row's
+// share of the fit) and a smaller KKT natural residual ||min(x, G x - m)||.  Counts
+// considered / accepted rows.
 __global__ void k_ws_judge(const float* __restrict__ out, const float* __restrict__ G,
                            const float* __restrict__ M, const float* __restrict__ s_ptr,
                            float* __restrict__ At, float* __restrict__ Y, int64_t I, int R,
@@ -358,7 +360,7 @@ __global__ void k_ws_judge(const float* __restrict__ out, const float* __restric
     }
   }
   __syncwarp();
-  float rc = 0.0f, ro = 0.0f;
+  float rc = 0.0f, ro = 0.0f, qc = 0.0f, qo = 0.0f;  // q: twice the row objective
   for (int h = 0; h < 2; ++h) {
     const int j = lane + 32 * h;
     if (j >= R) continue;
@@ -371,12 +373,16 @@ __global__ void k_ws_judge(const float* __restrict__ out, const float* __restric
     const float a = fminf(xc[h], gc), b = fminf(xo[h], go);
     rc += a * a;
     ro += b * b;
+    qc += xc[h] * (gc - m[h]);
+    qo += xo[h] * (go - m[h]);
   }
   for (int off = 16; off > 0; off >>= 1) {
     rc += __shfl_xor_sync(0xffffffffu, rc, off);
     ro += __shfl_xor_sync(0xffffffffu, ro, off);
+    qc += __shfl_xor_sync(0xffffffffu, qc, off);
+    qo += __shfl_xor_sync(0xffffffffu, qo, off);
   }
-  const bool take = rc < ro;
+  const bool take = rc < ro && qc < qo;
   if (take) {
     for (int h = 0; h < 2; ++h) {
       const int j = lane + 32 * h;

@@ -1,9 +1,10 @@
 // One factor update of eq. (ADMM_NTF_ALS_C) followed by the projection and dual steps of
 // eq. (ADMoM_NTF), repeated inner_iters times, as three launches:
 //
-//  k_update_system  one CTA: H = Hadamard_{m != n} Gram_m + rho I (FP64), its Cholesky factor
-//                   L and H^{-1} = L^{-T} L^{-1} (FP64) -- the coefficient matrix common to all
-//                   rows (App. B), factored once.  Stored as FP64 and as FP32 copies.
+//  k_update_system  one CTA: H = Hadamard_{m != n} Gram_m + rho I (FP64) and H^{-1} (FP64,
+//                   symmetric sweep operator: Gauss-Jordan in symmetric form, the SPD
+//                   counterpart of factoring H once) -- the coefficient matrix common to all
+//                   rows (App. B).  Stored as FP64 and FP32.
 //  k_update_rows    one warp per row: x = H^{-1}(m + rho At - Y), At = (x + Y/rho)_+,
 //                   Y += rho (x - At); per-CTA partial sums of the residual norms of
 //                   Sec. III-C, of the new factor's Gram (FP64) and of the fit terms
@@ -19,20 +20,10 @@
 namespace ntf {
 namespace {
 
-constexpr int kSysThreads = 256;
 constexpr int kRowWarps = 8;  // rows per CTA
 constexpr int kRowThreads = kRowWarps * 32;
 constexpr int kScal = 8;      // scalar partials per CTA
 constexpr int kRedEntries = 64;
-
-// 1/sqrt(d) for d > 0: the single-precision estimate refined by one Newton-Raphson step for
-// f(y) = y^-2 - d (y <- y (3 - d y^2) / 2), which squares its relative error (~1e-7 -> ~1e-14).
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  const float df = static_cast<float>(d);
-  if (!(df > 0.0f) || isinf(df) || df < 1e-30f) return rsqrt(d);
-  const double y = static_cast<double>(rsqrtf(df));
-  return y * fma(-0.5 * d * y, y, 1.5);
-}
 
 // Per-mode system slot: H^{-1} in FP64, H^{-1} and H (without rho) in FP32.
 struct SysView {
@@ -66,60 +57,115 @@ struct UpdArgs {
   double mu, tau_incr, tau_decr;
 };
 
+// 1/p for p > 0: the single-precision estimate refined by two Newton-Raphson steps for
+// f(y) = 1/y - p (y <- y + y (1 - p y)), each of which squares the relative error.
+__device__ __forceinline__ double recip_newton(double p) {
+  const float pf = static_cast<float>(p);
+  if (!(pf > 1e-30f) || !(pf < 1e30f)) return 1.0 / p;
+  double y = static_cast<double>(__frcp_rn(pf));
+  y = fma(y, fma(-p, y, 1.0), y);
+  return fma(y, fma(-p, y, 1.0), y);
+}
+
+// H = Hadamard_{m != n} Gram_m + rho I and H^{-1} by the symmetric sweep operator
+// (Goodnight 1979) on every diagonal entry: sweeping pivot k with d = a_kk replaces
+//   a_ij -> a_ij - a_ik a_kj / d  (i, j != k),   a_ik -> a_ik / d,   a_kk -> -1 / d,
+// keeps the matrix symmetric, and after all R sweeps the matrix is -H^{-1}.  This is
+// Gauss-Jordan elimination without pivoting in symmetric form: valid and stable for SPD H,
+// where every pivot is a Schur-complement diagonal entry, positive exactly when H is SPD.
+//
+// FP64 on this GPU runs at a small fraction of the FP32 rate, so the kernel minimises FP64
+// lane operations: only the lower triangle is kept (in registers, S packed entries per
+// thread), one warp forms 1/d and the scaled pivot column, and every other entry costs one
+// FP64 multiply-add per step.  The pivot column and its scaled copy are broadcast through
+// shared memory (double-buffered, two barriers per step).
+constexpr int kSysThreads = 128;
+
+template <int S>
 __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
-  extern __shared__ double sh[];
-  const int R = a.R, RR = R * R;
-  double* Hs = sh;          // Hadamard of the other Grams (no rho)
-  double* Af = Hs + RR;     // H + rho I -> Cholesky factor -> H^{-1}
-  double* Wm = Af + RR;     // L^{-1}
-  double* invd = Wm + RR;   // [64] 1/L_kk
-  __shared__ double s_rho, s_pinv;
+  __shared__ double s_col[2][64], s_sc[2][64], s_ip[2];
+  __shared__ double s_red[kSysThreads / 32];
   __shared__ int s_fail;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < RR; idx += kSysThreads) {
-    double v = 1.0;
-    for (int m = 0; m < a.N; ++m)
-      if (m != a.mode) v *= a.grams[m * RR + idx];
-    Hs[idx] = v;
-    Af[idx] = v;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double rho;
-    if (a.rho_policy == NTF_RHO_TRACE) {
-      double tr = 0.0;
-      for (int i = 0; i < R; ++i) tr += Hs[i * R + i];
-      rho = tr / R;
-    } else {
-      rho = a.ctrl->rho[a.mode];
+  const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SysView sv = sys_view(a.sys, a.mode, R);
+  double v[S];
+  int ii[S], jj[S];
+  double tr = 0.0;
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const int p = tid + kSysThreads * q;
+    int i = static_cast<int>((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > p) --i;
+    while ((i + 1) * (i + 2) / 2 <= p) ++i;
+    const int j = p - i * (i + 1) / 2;
+    ii[q] = p < T ? i : -1;
+    jj[q] = p < T ? j : -1;
+    double h = 0.0;
+    if (p < T) {
+      h = 1.0;
+      for (int m = 0; m < a.N; ++m)
+        if (m != a.mode) h *= a.grams[m * RR + i * R + j];
+      sv.h32[i * R + j] = static_cast<float>(h);
+      sv.h32[j * R + i] = static_cast<float>(h);
+      if (i == j) tr += h;
     }
-    s_rho = rho;
-    s_fail = !(rho > 0.0) || !isfinite(rho);
-    for (int i = 0; i < R; ++i) Af[i * R + i] += rho;
+    v[q] = h;
   }
+  for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
+  if (lane == 0) s_red[warp] = tr;
+  if (tid == 0) s_fail = 0;
   __syncthreads();
-  // Cholesky, right-looking, columns left unscaled (pivot d_k) and scaled by 1/L_kk after
-  for (int k = 0; k < R && !s_fail; ++k) {
+  double rho;
+  if (a.rho_policy == NTF_RHO_TRACE) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSysThreads / 32; ++w) t += s_red[w];
+    rho = t / R;
+  } else {
+    rho = a.ctrl->rho[a.mode];
+  }
+  if (!(rho > 0.0) || !isfinite(rho)) {
     if (tid == 0) {
-      const double d = Af[k * R + k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_fail = 1;
-      } else {
-        const double rs = rsqrt_newton(d);
-        invd[k] = rs;
-        Af[k * R + k] = d * rs;
-        s_pinv = rs * rs;
+      a.ctrl->bad[a.mode] = 1;
+      atomicOr(&a.ctrl->status, kStNotSpd);
+    }
+    return;  // uniform
+  }
+#pragma unroll
+  for (int q = 0; q < S; ++q)
+    if (ii[q] >= 0 && ii[q] == jj[q]) v[q] += rho;
+
+  for (int k = 0; k < R; ++k) {
+    const int b = k & 1;
+    // publish column k (= row k): a_xk for every x
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      if (ii[q] == k) s_col[b][jj[q]] = v[q];
+      else if (jj[q] == k) s_col[b][ii[q]] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const double d = s_col[b][k];
+      const bool bad = !(d > 0.0) || !isfinite(d);
+      const double ip = bad ? 0.0 : recip_newton(d);
+      for (int x = lane; x < R; x += 32) s_sc[b][x] = s_col[b][x] * ip;
+      if (lane == 0) {
+        s_ip[b] = ip;
+        if (bad) s_fail = 1;
       }
     }
     __syncthreads();
-    if (s_fail) break;
-    const double pinv = s_pinv;
-    const int n = R - k - 1;
-    for (int idx = tid; idx < n * n; idx += kSysThreads) {
-      const int i = k + 1 + idx / n, j = k + 1 + idx % n;
-      if (j <= i) Af[i * R + j] -= Af[i * R + k] * Af[j * R + k] * pinv;
+    if (s_fail) break;  // uniform
+    const double ip = s_ip[b];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      const int i = ii[q], j = jj[q];
+      if (i < 0) continue;
+      if (i == k) v[q] = (j == k) ? -ip : s_sc[b][j];
+      else if (j == k) v[q] = s_sc[b][i];
+      else v[q] = fma(-s_col[b][i], s_sc[b][j], v[q]);
     }
-    __syncthreads();
   }
   if (s_fail) {
     if (tid == 0) {
@@ -128,40 +174,19 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
     }
     return;
   }
-  for (int idx = tid; idx < RR; idx += kSysThreads) {
-    const int i = idx / R, j = idx % R;
-    if (j < i) Af[idx] *= invd[j];
-    Wm[idx] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  // L^{-1}: column-oriented forward substitution on all columns at once; rows kept unscaled
-  // (B) and scaled at the end: W[k][c] = B[k][c] / L_kk.
-  for (int k = 0; k < R - 1; ++k) {
-    const double rk = invd[k];
-    const int n = R - k - 1, w = k + 1;
-    for (int idx = tid; idx < n * w; idx += kSysThreads) {
-      const int j = k + 1 + idx / w, c = idx % w;
-      Wm[j * R + c] -= Af[j * R + k] * (Wm[k * R + c] * rk);
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < RR; idx += kSysThreads) {
-    const int k = idx / R, c = idx % R;
-    if (c <= k) Wm[idx] *= invd[k];
-  }
-  __syncthreads();
-  const SysView sv = sys_view(a.sys, a.mode, R);
-  for (int idx = tid; idx < RR; idx += kSysThreads) {
-    const int i = idx / R, j = idx % R;
-    double s = 0.0;
-    for (int k = max(i, j); k < R; ++k) s = fma(Wm[k * R + i], Wm[k * R + j], s);
-    sv.hinv64[idx] = s;
-    sv.hinv32[idx] = static_cast<float>(s);
-    sv.h32[idx] = static_cast<float>(Hs[idx]);
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const int i = ii[q], j = jj[q];
+    if (i < 0) continue;
+    const double h = -v[q];  // the swept matrix is -H^{-1}
+    sv.hinv64[i * R + j] = h;
+    sv.hinv64[j * R + i] = h;
+    sv.hinv32[i * R + j] = static_cast<float>(h);
+    sv.hinv32[j * R + i] = static_cast<float>(h);
   }
   if (tid == 0) {
     a.ctrl->bad[a.mode] = 0;
-    a.ctrl->stats[a.mode][5] = s_rho;
+    a.ctrl->stats[a.mode][5] = rho;
   }
 }
 
@@ -407,13 +432,13 @@ UpdArgs make_args(const UpdateCall& u) {
 
 cudaError_t launch_update_system(const UpdateCall& u, cudaStream_t st) {
   const UpdArgs a = make_args(u);
-  const size_t RR = static_cast<size_t>(u.R) * u.R;
-  const size_t sys_smem = (3 * RR + 64) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_update_system,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sys_smem));
-  if (e != cudaSuccess) return e;
-  k_update_system<<<1, kSysThreads, sys_smem, st>>>(a);
+  const int T = u.R * (u.R + 1) / 2;  // packed lower triangle, S entries per thread
+  if (T <= 1 * kSysThreads) k_update_system<1><<<1, kSysThreads, 0, st>>>(a);
+  else if (T <= 2 * kSysThreads) k_update_system<2><<<1, kSysThreads, 0, st>>>(a);
+  else if (T <= 4 * kSysThreads) k_update_system<4><<<1, kSysThreads, 0, st>>>(a);
+  else if (T <= 8 * kSysThreads) k_update_system<8><<<1, kSysThreads, 0, st>>>(a);
+  else if (T <= 17 * kSysThreads) k_update_system<17><<<1, kSysThreads, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ _SIGS = {
                                           ctypes.c_float, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_double), _P]),
     "ntf_mlp_last_error": (ctypes.c_char_p, []),
-    "ntf_attach_warmstart": (ctypes.c_int, [_P, _P]),
+    "ntf_attach_warmstart": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "ntf_mttkrp_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.c_int,
                                           ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P), _P,
                                           _P]),
@@ -338,8 +338,11 @@ class Context:
                 "ws_rows_considered": p.ws_rows_considered,
                 "ws_rows_accepted": p.ws_rows_accepted}
 
-    def attach_warmstart(self, net: Optional["Mlp"]) -> None:
-        _check(lib().ntf_attach_warmstart(self._h, net._h if net is not None else None))
+    def attach_warmstart(self, net: Optional["Mlp"], sweeps: int = 0) -> None:
+        """sweeps >= 1: consult the network in the first `sweeps` outer iterations of each
+        run; 0: in every iteration."""
+        _check(lib().ntf_attach_warmstart(self._h, net._h if net is not None else None,
+                                          int(sweeps)))
         self._ws = net  # keep the network alive while attached
 
 

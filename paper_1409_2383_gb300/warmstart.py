@@ -8,7 +8,9 @@ Training rows: during outer iterations of the plain method on synthetic tensors,
 factor update contributes its coefficient matrix G (without rho) and its MTTKRP rows m_i;
 the target of a row is the non-negative least-squares solution reached by running the same
 row iteration to convergence (``conv_iters`` inner iterations, fixed rho = trace(G)/R) from
-the carried-over state, paired with its dual: [x* ; y*/s], s = trace(G)/R.
+the carried-over state, paired with its dual: [x* ; y*/s], s = trace(G)/R.  The network is
+consulted in the first sweeps of a factorization (the cold start), so the training rows come
+from the first sweeps of many tensors of the workload's generator (``training_set``).
 """
 from __future__ import annotations
 
@@ -58,6 +60,39 @@ class RowSet:
         return Gn, torch.tensor(offs, dtype=torch.int32, device=mr.device), mr, tg
 
 
+def synthetic_tensor(dims: Sequence[int], R: int, seed: int, snr_db: float = 20.0,
+                     device: str = "cuda"):
+    """Tensor and start of the synthetic workload, drawn on the device: factors i.i.d.
+    uniform[0, 1], X = [F_1, ..., F_N] + Gaussian noise at `snr_db` (SNR = ||X_0||^2 /
+    (numel sigma^2)), start factors i.i.d. uniform[0, 1].  Same recipe as the host generator
+    of the tests, with the device's random streams."""
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    F = [torch.rand(int(d), R, generator=g, device=device) for d in dims]
+    letters = "abcd"[:len(dims)]
+    X = torch.einsum(",".join(f"{c}r" for c in letters) + "->" + letters, *F).contiguous()
+    sigma = math.sqrt(float(X.double().pow(2).sum()) / X.numel() / 10.0 ** (snr_db / 10.0))
+    X.add_(torch.randn(X.shape, generator=g, device=device), alpha=sigma)
+    init = [torch.rand(int(d), R, generator=g, device=device) for d in dims]
+    return X, init
+
+
+def training_set(dims: Sequence[int], R: int, rows: int, sweeps: int = 2, seed0: int = 1,
+                 snr_db: float = 20.0, conv_iters: int = 300, storage: str = "fp32") -> RowSet:
+    """Rows of the first `sweeps` outer iterations of synthetic tensors with seeds seed0,
+    seed0 + 1, ... until at least `rows` rows are collected."""
+    from . import ntf as _ntf
+    out = RowSet(R)
+    seed = seed0
+    while out.rows < rows:
+        X, init = synthetic_tensor(dims, R, seed, snr_db)
+        if storage == "bf16":
+            X = _ntf.to_bf16(X)
+        harvest(X, R, init, outer=sweeps, rows=out, conv_iters=conv_iters)
+        del X
+        seed += 1
+    return out
+
+
 def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
             rows: RowSet, conv_iters: int = 300, params: Optional[ntf.Params] = None,
             every: int = 1) -> RowSet:
@@ -96,8 +131,9 @@ def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
 
 
 def train(net: ntf.Mlp, rows: RowSet, steps: int, groups_per_batch: int, lr: float,
-          seed: int = 0, log_every: int = 0) -> List[float]:
-    """Adam on random batches of whole groups; returns the loss of every logged step."""
+          seed: int = 0, log_every: int = 0, decay_at: float = 1.0) -> List[float]:
+    """Adam on random batches of whole groups (learning rate divided by 10 after a fraction
+    `decay_at` of the steps); returns the loss of every logged step."""
     g = np.random.default_rng(seed)
     n = len(rows.Gn)
     losses = []
@@ -105,7 +141,8 @@ def train(net: ntf.Mlp, rows: RowSet, steps: int, groups_per_batch: int, lr: flo
         idx = g.choice(n, size=min(groups_per_batch, n), replace=False)
         Gn, offs, mr, tg = rows.batch(sorted(idx.tolist()))
         want = bool(log_every) and (t % log_every == 0 or t == steps - 1)
-        loss = net.train_step(Gn, offs, mr, tg, lr, apply=True, want_loss=want)
+        lr_t = lr if t < decay_at * steps else 0.1 * lr
+        loss = net.train_step(Gn, offs, mr, tg, lr_t, apply=True, want_loss=want)
         if want:
             losses.append(loss)
     return losses
@@ -125,7 +162,7 @@ def eval_loss(net: ntf.Mlp, rows: RowSet, groups_per_batch: int) -> float:
 
 def time_to_fit(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], target: float,
                 max_outer: int, net: Optional[ntf.Mlp] = None, repeats: int = 1,
-                params: Optional[ntf.Params] = None):
+                params: Optional[ntf.Params] = None, ws_sweeps: int = 1):
     """Time (CUDA events) of factorizations from `init` until rel_err <= target, on a fresh
     non-default stream (so the sweep is replayed as a CUDA graph).  Returns a dict with the
     median seconds, iterations, final error and the warm-start row counts."""
@@ -138,7 +175,7 @@ def time_to_fit(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], target: f
         Y = [torch.zeros_like(f) for f in init]
         with ntf.Context(X, R, p, stream=stream) as ctx:
             if net is not None:
-                ctx.attach_warmstart(net)
+                ctx.attach_warmstart(net, ws_sweeps)
             ctx.profile_enable(True)             # recorded in the graph from the first run
             prof0 = prof = ctx.profile_get()
             for rep in range(repeats + 1):      # the first run records the graph

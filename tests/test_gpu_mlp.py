@@ -142,9 +142,10 @@ def test_training_reduces_loss(ntf):
 
 
 def test_warm_start_judge_in_factor_update(ntf):
-    """Warm start of one factor update: every row starts from the network's candidate or
-    the carried-over state, whichever has the smaller KKT residual (replayed in FP64 with
-    the oracle network); the final state is the oracle update from that start."""
+    """Warm start of one factor update: every row starts from the network's candidate if it
+    has both the smaller row objective and the smaller KKT residual, else from the
+    carried-over state (replayed in FP64 with the oracle network and oracle judge); the final
+    state is the oracle update from that start."""
     from paper_1409_2383_gb300 import warmstart
     rng = np.random.default_rng(9)
     dims, R, H = (40, 30, 20), 4, 32
@@ -169,7 +170,7 @@ def test_warm_start_judge_in_factor_update(ntf):
         ctx.admm_update(n, torch.as_tensor(M).cuda(), A_d, At_d, Y_d)
         prof = ctx.profile_get()
     assert prof["ws_rows_considered"] == dims[n]
-    # replay in FP64: network candidate vs carried state, judged by the KKT natural residual
+    # replay in FP64: network candidate vs carried state, judged as the oracle judge does
     s = np.trace(G) / R
     Gf = G.astype(np.float32).astype(np.float64)
     sf = np.trace(Gf) / R
@@ -178,20 +179,28 @@ def test_warm_start_judge_in_factor_update(ntf):
     out, _ = om.forward(_split(flat.numpy(), R, H), U)
     xc, yc = om.decode(out, sf, R)
 
-    def resid(x):
-        return np.sum(np.minimum(x, x @ G - M.astype(np.float64)) ** 2, axis=1)
+    M64, X0 = M.astype(np.float64), At0.astype(np.float64)
+    rc, ro = om.kkt_residual(G, M64, xc), om.kkt_residual(G, M64, X0)
+    qc, qo = om.row_objective(G, M64, xc), om.row_objective(G, M64, X0)
 
-    rc, ro = resid(xc), resid(At0.astype(np.float64))
-    clear = np.abs(rc - ro) > 1e-3 * np.maximum(rc, ro)
-    take = rc < ro
+    def sure(a, b):  # a < b (+1) or a > b (-1) by a margin FP32 rounding cannot flip; else 0
+        gap = 1e-3 * np.maximum(np.abs(a), np.abs(b))
+        return np.where(a < b - gap, 1, np.where(a > b + gap, -1, 0))
+
+    kr, kq = sure(rc, ro), sure(qc, qo)
+    take_sure = (kr == 1) & (kq == 1)
+    keep_sure = (kr == -1) | (kq == -1)
+    clear = take_sure | keep_sure
+    take = om.judge(G, M64, xc, X0)
+    assert np.array_equal(take[clear], take_sure[clear])
     start_t = np.where(take[:, None], xc, At0)
     start_y = np.where(take[:, None], yc, Y0)
     _, At_w, Y_w, _ = o.admm_factor_update(M.astype(np.float64), G, start_t, start_y,
                                            o.rho_trace(G), 2)
     got_t = At_d.cpu().numpy()
     assert rel(got_t[clear], At_w[clear]) <= 1e-3
-    assert prof["ws_rows_accepted"] >= int(np.sum(take & clear))
-    assert prof["ws_rows_accepted"] <= int(np.sum(take | ~clear))
+    assert prof["ws_rows_accepted"] >= int(np.sum(take_sure))
+    assert prof["ws_rows_accepted"] <= int(np.sum(~keep_sure))
     assert np.all(got_t >= 0)
     net.close()
 

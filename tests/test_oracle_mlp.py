@@ -106,3 +106,38 @@ def test_features_are_scale_invariant():
     assert np.allclose(T1, T2, atol=1e-9)
     ax, dy = mlp.decode(T1, s1, 4)
     assert np.allclose(ax[0], x1, atol=1e-12) and np.allclose(dy[0], np.minimum(y1, 0))
+
+
+def test_row_objective_and_kkt_residual_pins():
+    """q(x) against the Cholesky least-squares form 1/2||L^T x - L^{-1} m||^2 - 1/2||L^{-1} m||^2
+    (G = L L^T); the KKT residual vanishes at the exhaustive NNLS solution and nowhere near it."""
+    rng = np.random.default_rng(21)
+    R = 5
+    K = rng.random((3 * R, R))
+    G = K.T @ K
+    M = rng.standard_normal((6, R)) * np.trace(G) / R
+    X = np.abs(rng.standard_normal((6, R)))
+    L = np.linalg.cholesky(G)
+    b = np.linalg.solve(L, M.T).T
+    ls = 0.5 * np.sum((X @ L - b) ** 2, axis=1) - 0.5 * np.sum(b ** 2, axis=1)
+    assert np.allclose(mlp.row_objective(G, M, X), ls, rtol=1e-12, atol=1e-9)
+    Xs = np.array([o.nnls_exhaustive(G, m) for m in M])
+    assert np.all(mlp.kkt_residual(G, M, Xs) < 1e-18 * np.sum(M ** 2))
+    assert np.all(mlp.kkt_residual(G, M, Xs + 0.1) > 0)
+
+
+def test_judge_needs_both_criteria():
+    rng = np.random.default_rng(22)
+    R = 4
+    K = rng.random((3 * R, R))
+    G = K.T @ K
+    M = rng.standard_normal((8, R)) * np.trace(G) / R
+    Xs = np.array([o.nnls_exhaustive(G, m) for m in M])
+    Xp = np.maximum(Xs + 0.3 * rng.standard_normal(Xs.shape), 0.0)
+    Xp[np.all(Xp == Xs, axis=1)] += 0.5      # no perturbed row may equal the solution
+    # the solution minimises q over x >= 0 and has zero KKT residual: it always wins ...
+    assert np.all(mlp.judge(G, M, Xs, Xp))
+    # ... and is never replaced (no candidate has a smaller KKT residual than zero)
+    assert not np.any(mlp.judge(G, M, Xp, Xs))
+    # a candidate equal to the carried state is not taken (strict comparisons)
+    assert not np.any(mlp.judge(G, M, Xp, Xp))
