@@ -1,13 +1,17 @@
 """Benchmark: time to relative fit 1e-3 of ADMoM non-negative CP factorization on GB300.
 
-One step = one whole factorization of the 400x400x400 FP32 rank-20 workload (U[0,1] factors,
+One step = one whole factorization of the 400x400x400 rank-20 workload (U[0,1] factors,
 20 dB Gaussian noise, data seed 0, uniform start of seed 1; L = 5 inner iterations,
 Khatri-Rao of the auxiliaries, rho = trace(G)/R) from the start until the relative error is
 within 1e-3 of the converged value RFE* (RFE_k <= RFE* (1 + 1e-3)), where RFE* is the error
-after the workload's 200 outer iterations, found during warm-up.  The metric is the time of
-one such factorization (lower is better); the same JSON line carries the live roofline of the
-dominant tensor contraction (HBM GB/s from CUDA events inside the timed steps), an end-to-end
-time through host buffers, and the FP64 oracle timed on the host cores.
+of the plain FP32 method after the workload's 200 outer iterations, found during warm-up.
+The timed form (--form) defaults to BF16 tensor storage with the learned warm start in the
+first sweep (network trained before the timed region on rows of other tensors of the same
+generator; its harvest and training times are reported apart); plain FP32 and plain BF16
+are timed to the same target as variants.  The metric is the time of one factorization
+(lower is better); the same JSON line carries the live roofline of the dominant tensor
+contraction (HBM GB/s from CUDA events inside the timed steps), an end-to-end time through
+host buffers, and the FP64 oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ntf|reference]
 
@@ -46,22 +50,37 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# Source files that define each timed kernel: a stored ncu traffic figure is used only while
+# these files are unchanged since the capture.
+KERNEL_SOURCES = {
+    "k_umma": ["umma_kernels.cuh", "umma_bf16.cu", "umma_f32.cu", "umma_host.cu"],
+    "k_gemm": ["mttkrp_kernels.cuh", "gemm_n_f32.cu", "gemm_n_bf16.cu", "gemm_t_f32.cu",
+               "gemm_t_bf16.cu"],
+}
+
+
+def kernel_source_hash(family: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[family]:
+        with open(os.path.join(ROOT, "paper_1409_2383_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _traffic_record(kernel: str):
-    """Per-launch DRAM bytes from a committed ncu summary, if taken on the current sources."""
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary (profiles/traffic.json),
+    if it was taken on the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f)
+            entry = json.load(f).get(kernel)
     except Exception:
         return None
-    from paper_1409_2383_gb300 import build as b
-    import hashlib
-    h = hashlib.sha256()
-    for src in sorted(b._sources()) + sorted(b._headers()):
-        with open(src, "rb") as f:
-            h.update(f.read())
-    entry = rec.get(kernel)
-    if not entry or entry.get("source_sha256") != h.hexdigest():
+    if not entry:
+        return None
+    family = "k_umma" if kernel.startswith("k_umma") else "k_gemm"
+    if entry.get("source_sha256") != kernel_source_hash(family):
         return None
     return entry.get("dram_bytes_per_launch")
 
@@ -185,6 +204,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+FORMS = {
+    # form: (storage, learned warm start)
+    "bf16_learned": ("bf16", True),
+    "bf16": ("bf16", False),
+    "fp32": ("fp32", False),
+}
+
+
+def train_network(args):
+    """Warm-start network for the workload: rows harvested from the first sweeps of tensors
+    of the workload generator with other seeds (drawn on the device), trained by the
+    library's kernels.  Returns (network, report)."""
+    import torch
+    from paper_1409_2383_gb300 import ntf, warmstart
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows = warmstart.training_set(DIMS, RANK, args.train_rows, sweeps=args.ws_sweeps,
+                                  seed0=1000, snr_db=SNR_DB, storage="bf16")
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    H = 256
+    groups, per_group = 256, 25                  # rows from many coefficient matrices per step
+    net = ntf.Mlp(RANK, H, warmstart.init_params(RANK, H, seed=0),
+                  max_rows=max(groups * per_group, 16 * max(DIMS)), max_groups=groups)
+    loss0 = warmstart.eval_loss(net, rows, 16)
+    steps = max(1, int(args.train_epochs * rows.rows / (groups * per_group)))
+    warmstart.train(net, rows, steps=steps, groups_per_batch=groups, lr=1e-3, decay_at=0.7,
+                    rows_per_group=per_group)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rep = {"rows": rows.rows, "groups": len(rows.Gn), "tensor_dims": list(DIMS),
+           "sweeps_harvested": args.ws_sweeps, "ws_sweeps": args.ws_sweeps,
+           "harvest_s": t1 - t0, "train_s": t2 - t1, "steps": steps, "hidden": H,
+           "loss_before": loss0, "loss_after": warmstart.eval_loss(net, rows, 16)}
+    del rows
+    return net, rep
+
+
 def run_ntf(args):
     import torch
     world, rank, local = _dist()
@@ -192,8 +249,9 @@ def run_ntf(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    from paper_1409_2383_gb300 import ntf
+    from paper_1409_2383_gb300 import ntf, warmstart
 
+    storage, learned = FORMS[args.form]
     X, init = _workload(rank)                # replicas: one tensor per rank
     stream = torch.cuda.Stream()
     p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
@@ -203,7 +261,6 @@ def run_ntf(args):
         A = [f.clone() for f in init_d]
         At = [f.clone() for f in init_d]
         Y = [torch.zeros_like(f) for f in init_d]
-        ctx = ntf.Context(Xd, RANK, p, stream=stream)
 
         def reset():
             for a, t, y, f in zip(A, At, Y, init_d):
@@ -211,11 +268,19 @@ def run_ntf(args):
                 t.copy_(f)
                 y.zero_()
 
-        # warm-up 1: the converged error of the workload's iteration budget
-        reset()
-        full = ctx.run(A, At, Y, MAX_OUTER, check_every=MAX_OUTER)
+        # the fit target of every form: the converged error of the plain FP32 method within
+        # the workload's iteration budget, relaxed by the fit tolerance
+        with ntf.Context(Xd, RANK, p, stream=stream) as c32:
+            reset()
+            full = c32.run(A, At, Y, MAX_OUTER, check_every=MAX_OUTER)
         target = full["rel_err"] * (1 + FIT_TOL)
-        for _ in range(max(args.warmup - 1, 0)):
+
+        net, training = train_network(args) if learned else (None, None)
+        Xf = ntf.to_bf16(Xd) if storage == "bf16" else Xd
+        ctx = ntf.Context(Xf, RANK, p, stream=stream)
+        if net is not None:
+            ctx.attach_warmstart(net, args.ws_sweeps)
+        for _ in range(args.warmup):
             reset()
             ctx.run(A, At, Y, MAX_OUTER, target_rfe=target)
         stream.synchronize()
@@ -241,9 +306,14 @@ def run_ntf(args):
         prof = ctx.profile_get()
         ctx.profile_enable(False)
         final_rfe = rs["rel_err"]
+        ctx.close()
+        # error of the form's factors against the FP32 tensor (BF16 storage rounds the data)
+        with ntf.Context(Xd, RANK, p, stream=stream) as c32:
+            rfe_vs_fp32 = c32.fit(At)
 
-        # end to end through the public API with host buffers: H2D of the tensor and the
-        # start, context creation (||X||^2), the factorization, D2H of the factors
+        # end to end through the public API with host buffers: H2D of the FP32 tensor and the
+        # start, BF16 conversion, context creation (||X||^2), the factorization, D2H of the
+        # factors
         Xh = torch.as_tensor(X).pin_memory()
         init_h = [torch.as_tensor(f).pin_memory() for f in init]
         out_h = [torch.empty_like(f).pin_memory() for f in init_h]
@@ -253,6 +323,8 @@ def run_ntf(args):
         for _ in range(e2e_steps):
             Xe = torch.empty_like(Xd)
             Xe.copy_(Xh, non_blocking=True)
+            if storage == "bf16":
+                Xe = ntf.to_bf16(Xe)
             Ae = [torch.empty_like(f) for f in init_d]
             Te = [torch.empty_like(f) for f in init_d]
             for a, t, f in zip(Ae, Te, init_h):
@@ -260,6 +332,8 @@ def run_ntf(args):
                 t.copy_(f, non_blocking=True)
             Ye = [torch.zeros_like(f) for f in init_d]
             with ntf.Context(Xe, RANK, p, stream=stream) as c2:
+                if net is not None:
+                    c2.attach_warmstart(net, args.ws_sweeps)
                 c2.run(Ae, Te, Ye, MAX_OUTER, target_rfe=target)
             for o_, t in zip(out_h, Te):
                 o_.copy_(t, non_blocking=True)
@@ -267,8 +341,25 @@ def run_ntf(args):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         h2d = Xh.numel() * 4 + 2 * sum(f.numel() * 4 for f in init_h)
         d2h = sum(f.numel() * 4 for f in out_h)
-        ctx.close()
-        variants = None if args.no_variants else run_variants(args, Xd, init_d, target)
+
+        variants = None
+        if not args.no_variants:
+            variants = {}
+            for name, (st_, lw) in FORMS.items():
+                if name == args.form:
+                    continue
+                if lw and net is None:
+                    net, training = train_network(args)
+                Xv = ntf.to_bf16(Xd) if st_ == "bf16" else Xd
+                variants[name] = warmstart.time_to_fit(Xv, RANK, init_d, target, MAX_OUTER,
+                                                       net=net if lw else None, repeats=3,
+                                                       ws_sweeps=args.ws_sweeps)
+            variants[args.form] = {"seconds": ms / 1000.0, "iters": statistics.mean(iters),
+                                   "rel_err": final_rfe}
+            if "fp32" in variants:
+                variants["speedup_vs_fp32"] = variants["fp32"]["seconds"] / (ms / 1000.0)
+        if net is not None:
+            net.close()
 
     value_s = ms / 1000.0
     if world > 1:
@@ -278,35 +369,43 @@ def run_ntf(args):
     if rank != 0:
         return
 
-    # roofline of the dominant contraction (more device time)
+    # roofline of the dominant contraction (more device time) of the timed form
     k = 0 if prof["contraction_ms"][0] >= prof["contraction_ms"][1] else 1
-    names = ["k_gemm_n (X * KR_right)", "k_gemm_t (X^T * KR_left)"]
+    names = ["k_umma<0,...> (X * KR_right, tcgen05)", "k_umma<1,...> (X^T * KR_left, tcgen05)"]
+    kernel_ids = [f"k_umma_n_{storage}", f"k_umma_t_{storage}"]
     avg_ms = prof["contraction_ms"][k] / max(prof["contractions"][k], 1)
     bytes_ = prof["contraction_bytes"][k]
     achieved = bytes_ / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _traffic_record(["k_gemm_n", "k_gemm_t"][k])
+    traffic = _traffic_record(kernel_ids[k])
     sweep_ms = ms / statistics.mean(iters)
 
     cpu = None
     if not args.no_cpu_baseline:
         n_cpu = 2
         sec = cpu_oracle_seconds_per_iteration(X, init, n_cpu)
-        n_it = statistics.mean(iters)
+        n_it, _ = _stored_iterations()
         cpu = {"value": sec * n_it, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n_cpu} FP64 oracle outer iterations of {WORKLOAD} (median "
-                         f"{sec:.2f} s) x the {n_it:.0f} iterations the GPU run needed"}
+                         f"{sec:.2f} s) x the {n_it} iterations the oracle needs to reach the "
+                         "fit (stored oracle trajectory)"}
 
     line = {
         "metric": METRIC, "value": value_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16" if storage == "bf16" else "f32",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "snr_db": SNR_DB,
-                   "storage": "fp32", "inner_iters": 5, "rho": "trace(G)/R",
-                   "kr_source": "aux", "fit_tol": FIT_TOL, "max_outer": MAX_OUTER,
-                   "target_rfe": target, "final_rfe": final_rfe,
+                   "form": args.form, "storage": storage,
+                   "accumulate": "f32 (Gram, coefficient system: f64)",
+                   "warm_start": f"learned, first {args.ws_sweeps} sweep(s)" if learned
+                   else "none",
+                   "inner_iters": 5, "rho": "trace(G)/R", "kr_source": "aux",
+                   "fit_tol": FIT_TOL, "max_outer": MAX_OUTER,
+                   "target_rfe": target, "target_from": "plain FP32 converged error x (1 + tol)",
+                   "final_rfe": final_rfe, "final_rfe_vs_fp32_tensor": rfe_vs_fp32,
                    "outer_iters_to_fit": statistics.mean(iters), "ms_per_outer_iter": sweep_ms,
-                   "l2": "inputs larger than L2 (256 MB tensor streamed twice per iteration)",
+                   "l2": "inputs larger than L2 (tensor streamed twice per iteration)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": names[k], "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -319,6 +418,7 @@ def run_ntf(args):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(prof["kernel_launches"]),
         "clocks": clk.summary(),
+        "training": training,
         "variants": variants,
     }
     print(json.dumps(line), flush=True)
@@ -379,48 +479,6 @@ def run_sweep_case(args):
                       "rel_err": rs["rel_err"]}))
 
 
-def run_variants(args, Xd, init_d, target):
-    """Time to the same fit target for plain FP32 storage, BF16 storage, and BF16 storage
-    plus the learned warm start in the first sweeps (network trained on rows harvested from
-    the first sweeps of other tensors of the same generator, by the library's own kernels;
-    harvest and training time reported apart)."""
-    import torch
-    from paper_1409_2383_gb300 import ntf, warmstart
-    out = {}
-    fp32 = warmstart.time_to_fit(Xd, RANK, init_d, target, MAX_OUTER, repeats=3)
-    out["fp32"] = fp32
-    Xb = ntf.to_bf16(Xd)
-    out["bf16"] = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, repeats=3)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rows = warmstart.training_set(DIMS, RANK, args.train_rows, sweeps=2, seed0=1000,
-                                  snr_db=SNR_DB, storage="bf16")
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    H = 256
-    max_rows = 16 * max(DIMS)
-    net = ntf.Mlp(RANK, H, warmstart.init_params(RANK, H, seed=0), max_rows=max_rows,
-                  max_groups=16)
-    loss0 = warmstart.eval_loss(net, rows, 16)
-    steps = max(1, int(args.train_epochs * len(rows.Gn) / 16))
-    warmstart.train(net, rows, steps=steps, groups_per_batch=16, lr=1e-3, decay_at=0.7)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    loss1 = warmstart.eval_loss(net, rows, 16)
-    learned = warmstart.time_to_fit(Xb, RANK, init_d, target, MAX_OUTER, net=net, repeats=3,
-                                    ws_sweeps=args.ws_sweeps)
-    out["bf16_learned"] = learned
-    out["training"] = {"rows": rows.rows, "groups": len(rows.Gn),
-                       "tensors": len(rows.Gn) // (2 * len(DIMS)), "tensor_dims": list(DIMS),
-                       "sweeps_harvested": 2, "ws_sweeps": args.ws_sweeps,
-                       "harvest_s": t1 - t0, "train_s": t2 - t1, "steps": steps,
-                       "loss_before": loss0, "loss_after": loss1, "hidden": H}
-    out["speedup_bf16_learned_vs_fp32"] = fp32["seconds"] / learned["seconds"]
-    out["speedup_bf16_vs_fp32"] = fp32["seconds"] / out["bf16"]["seconds"]
-    net.close()
-    return out
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,7 +487,10 @@ def main():
     ap.add_argument("--impl", default="ntf", choices=["ntf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the BF16 and BF16 + learned warm-start comparison")
+                    help="skip timing the other storage forms")
+    ap.add_argument("--form", default="bf16_learned", choices=sorted(FORMS),
+                    help="the timed form: BF16 or FP32 storage, with or without the learned "
+                         "warm start")
     ap.add_argument("--train-rows", type=int, default=1_000_000)
     ap.add_argument("--train-epochs", type=float, default=20.0)
     ap.add_argument("--ws-sweeps", type=int, default=1,

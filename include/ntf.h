@@ -201,14 +201,16 @@ ntf_status ntf_sync(ntf_ctx* ctx);
  * With the other factors fixed each row of a factor solves the non-negative least squares
  * min_{x >= 0} 1/2 x^T G x - m^T x (G: coefficient matrix of eq. ADMM_NTF_ALS_C without rho,
  * m: MTTKRP row), whose solution x* and dual y* = m - G x* satisfy eq. (KKT_NTF).  The network
- * maps [vec(G/s) ; m/s], s = trace(G)/R, to [x* ; y* / s]: layers R^2+R -> H -> H -> 2R with the
- * exact GELU, BF16 weights in every product (FP32 master copies, FP32 accumulation).
- * Parameters are one flat FP32 array in the order W1 [H, R^2+R], b1 [H], W2 [H, H], b2 [H],
- * W3 [2R, H], b3 [2R] (row-major), of ntf_mlp_param_count(R, H) floats.  Batches: `groups`
- * normalised coefficient matrices d_Gn [groups, R^2] (G/s), CSR offsets d_offsets
- * [groups + 1] (device ints; the rows of group g are offsets[g] .. offsets[g+1]-1) and
- * normalised MTTKRP rows d_mrows [rows, R] (m/s); targets [rows, 2R].  All calls run on the
- * stream given at creation. */
+ * maps [vec(G/s) ; m/s ; z], s = trace(G)/R, z = (G + s I)^{-1} m (the first primal iterate of
+ * the row's ADMM from zero, eq. ADMM_NTF_ALS_C), to [x* ; y* / s]: layers R^2+2R -> H -> H ->
+ * 2R with the exact GELU, BF16 weights in every product (FP32 master copies, FP32
+ * accumulation).  Parameters are one flat FP32 array in the order W1 [H, R^2+2R], b1 [H],
+ * W2 [H, H], b2 [H], W3 [2R, H], b3 [2R] (row-major), of ntf_mlp_param_count(R, H) floats.
+ * Batches: `groups` normalised coefficient matrices d_Gn [groups, R^2] (G/s), CSR offsets
+ * d_offsets [groups + 1] (device ints; the rows of group g are offsets[g] .. offsets[g+1]-1)
+ * and per-row inputs d_mrows [rows, 2R] ([m/s ; z]); targets [rows, 2R].  All calls run on the
+ * stream given at creation.  Inside a factor update (ntf_attach_warmstart) z is formed with
+ * the update's own (G + rho I)^{-1}, which is (G + s I)^{-1} under the trace penalty policy. */
 typedef struct ntf_mlp ntf_mlp;
 
 /* Number of floats in the parameter array (-1 for an invalid rank / width). */

@@ -6,10 +6,13 @@ With the other factors fixed, every row a_i of a factor solves
     min_{x >= 0} 1/2 x^T G x - m_i^T x          (G = coefficient matrix, m_i = MTTKRP row)
 and the ADMoM iteration of eq. (ADMoM_NTF) converges to x* with dual y* = m_i - G x*
 (eq. KKT_NTF: Y = M - A G, Y <= 0, Y (*) A = 0).  The network maps the normalised pair
-(G / s, m_i / s), s = trace(G) / R, to (x*, y* / s).  That normalisation uses the invariance
-of the problem under (G, m) -> (c G, c m): x* is unchanged and y* scales by c.
+(G / s, m_i / s, z_i), s = trace(G) / R, to (x*, y* / s), where z_i = (G + s I)^{-1} m_i is
+the first primal iterate of the row's ADMM from zero (eq. ADMM_NTF_ALS_C with rho = s): a
+fixed function of (G, m_i) that spares the network learning a matrix inverse.  The
+normalisation uses the invariance of the problem under (G, m) -> (c G, c m): x* and z are
+unchanged and y* scales by c.
 
-Architecture: input [vec(G/s) ; m_i/s] of size R^2 + R, two hidden layers of width H with
+Architecture: input [vec(G/s) ; m_i/s ; z_i] of size R^2 + 2R, two hidden layers of width H with
 the exact GELU, x -> x Phi(x), and a linear output of size 2R; loss = mean squared error.
 Adam as in Kingma & Ba (2015).  Everything in FP64, one dense layer after the other, with
 the first layer applied to the full concatenated input (no per-G reuse), so it is the plain
@@ -38,14 +41,16 @@ def gelu_grad(z: np.ndarray) -> np.ndarray:
 
 
 def features(G: np.ndarray, M: np.ndarray) -> Tuple[np.ndarray, float]:
-    """Rows [vec(G/s) ; m_i/s] for every row m_i of M, and the scale s = trace(G)/R."""
+    """Rows [vec(G/s) ; m_i/s ; z_i] for every row m_i of M, z_i = (G + s I)^{-1} m_i, and the
+    scale s = trace(G)/R."""
     G = np.asarray(G, np.float64)
     M = np.asarray(M, np.float64)
     R = G.shape[0]
     s = float(np.trace(G)) / R
-    U = np.empty((M.shape[0], R * R + R))
+    U = np.empty((M.shape[0], R * R + 2 * R))
     U[:, :R * R] = (G / s).reshape(1, -1)
-    U[:, R * R:] = M / s
+    U[:, R * R:R * R + R] = M / s
+    U[:, R * R + R:] = np.linalg.solve(G + s * np.eye(R), M.T).T
     return U, s
 
 

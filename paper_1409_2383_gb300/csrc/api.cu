@@ -315,7 +315,7 @@ ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float*
   NTF_TRY(warm_start(c, mode, M, At, Y, c->st));
   NTF_CUDA(ntf::launch_update_rows(u, c->st));
   NTF_CUDA(ntf::launch_update_reduce(u, c->st));
-  c->launches += 3;
+  c->launches += ntf::update_fused(u) ? 2 : 3;
   return NTF_OK;
 }
 
@@ -332,6 +332,7 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
   NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_start, 0));
   NTF_CUDA(ntf::launch_update_system(make_call(c, 0, c->Mbuf, A[0], At[0], Y[0], false), sb));
   NTF_CUDA(cudaEventRecord(c->ev_sys[0], sb));
+  c->launches += 1;
   const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
   NTF_TRY(contract_right(c, src, const_cast<float*>(T), sa));
   for (int m = 0; m < c->N; ++m) {
@@ -356,7 +357,7 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
           make_call(c, m + 1, c->Mbuf, A[m + 1], At[m + 1], Y[m + 1], false), sc));
       NTF_CUDA(cudaEventRecord(c->ev_sys[m + 1], sc));
     }
-    c->launches += 3;
+    c->launches += 1 + (ntf::update_fused(u) ? 0 : 1) + (m + 1 < c->N ? 1 : 0);
   }
   NTF_CUDA(cudaEventRecord(c->ev_b, sb));
   NTF_CUDA(cudaEventRecord(c->ev_c, sc));

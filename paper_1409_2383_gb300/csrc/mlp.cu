@@ -2,13 +2,14 @@
 //
 // With the other factors fixed, every row of the factor solves min_{x >= 0} 1/2 x^T G x - m^T x
 // (G: coefficient matrix of eq. ADMM_NTF_ALS_C without rho, m: MTTKRP row); ADMoM converges to
-// x* with dual y* = m - G x* (eq. KKT_NTF).  The network maps [vec(G/s) ; m/s], s = trace(G)/R,
-// to [x* ; y*/s] (the problem is invariant under (G, m) -> (cG, cm) with x* fixed and y*
-// scaled by c).  Layers: R^2+R -> H -> H -> 2R, exact GELU, BF16 weights in the products with
-// FP32 master copies and FP32 accumulation everywhere.  The first layer is split
-// W1 = [W1_G | W1_m]: W1_G vec(G/s) is formed once per coefficient matrix and shared by all
-// of its rows.  Training: mean squared error, Adam (Kingma & Ba).  All reductions run in a
-// fixed order.
+// x* with dual y* = m - G x* (eq. KKT_NTF).  The network maps [vec(G/s) ; m/s ; z],
+// s = trace(G)/R, z = (G + s I)^{-1} m (the first primal iterate of the row's ADMM from zero),
+// to [x* ; y*/s] (the problem is invariant under (G, m) -> (cG, cm) with x* and z fixed and y*
+// scaled by c).  Layers: R^2+2R -> H -> H -> 2R, exact GELU, BF16 weights in the products
+// with FP32 master copies and FP32 accumulation everywhere.  The first layer is split
+// W1 = [W1_G | W1_u]: W1_G vec(G/s) is formed once per coefficient matrix and shared by all
+// of its rows; W1_u acts on the per-row input u = [m/s ; z] (2R values).  Training: mean
+// squared error, Adam (Kingma & Ba).  All reductions run in a fixed order.
 #include <cmath>
 #include <cstdint>
 
@@ -208,7 +209,8 @@ MlpShape mlp_shape(int R, int H) {
   MlpShape s{};
   s.R = R;
   s.H = H;
-  s.Din = R * R + R;
+  s.P = 2 * R;
+  s.Din = R * R + s.P;
   s.Dout = 2 * R;
   s.oW1 = 0;
   s.ob1 = s.oW1 + static_cast<int64_t>(H) * s.Din;
@@ -221,15 +223,15 @@ MlpShape mlp_shape(int R, int H) {
 }
 
 // Forward for `rows` rows given per-group first-layer terms hG [groups, H] (already W1_G
-// vec(G/s)), row_group[rows] and the normalised MTTKRP rows mrows [rows, R].  Work buffers:
-// z1, h1, z2, h2 [rows, H], out [rows, Dout].
+// vec(G/s)), row_group[rows] and the per-row inputs mrows [rows, 2R] = [m/s ; z].  Work
+// buffers: z1, h1, z2, h2 [rows, H], out [rows, Dout].
 cudaError_t mlp_forward_rows(const MlpShape& s, const float* p, const __nv_bfloat16* pb,
                              const float* hG, const int* row_group, const float* mrows, int rows,
                              float* z1, float* h1, float* z2, float* h2, float* out,
                              cudaStream_t st) {
   const int H = s.H, R = s.R;
-  // z1 = mrows W1_m^T (columns R^2 .. R^2+R-1 of W1), then + hG[group] + b1
-  cudaError_t e = gemm<false, true, __nv_bfloat16>(rows, H, R, mrows, R, pb + s.oW1 + R * R,
+  // z1 = mrows W1_u^T (columns R^2 .. R^2+2R-1 of W1), then + hG[group] + b1
+  cudaError_t e = gemm<false, true, __nv_bfloat16>(rows, H, s.P, mrows, s.P, pb + s.oW1 + R * R,
                                                    s.Din, z1, H, nullptr, false, st);
   if (e != cudaSuccess) return e;
   k_first_layer_add<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(
@@ -277,8 +279,8 @@ cudaError_t mlp_backward(const MlpShape& s, const __nv_bfloat16* pb, const float
   e = gemm<false, false, __nv_bfloat16>(rows, H, H, d_h2, H, pb + s.oW2, H, d_h1, H, nullptr, false, st);
   if (e != cudaSuccess) return e;
   k_gelu_back<<<blocks_for(static_cast<int64_t>(rows) * H), 256, 0, st>>>(z1, d_h1, static_cast<int64_t>(rows) * H);
-  // layer 1 (d_h1 holds dz1): dW1_m = dz1^T mrows into columns R^2.., dW1_G = gsum^T Gn
-  e = gemm<true, false, float>(H, R, rows, d_h1, H, mrows, R, grad + s.oW1 + R * R, s.Din, nullptr, false, st);
+  // layer 1 (d_h1 holds dz1): dW1_u = dz1^T mrows into columns R^2.., dW1_G = gsum^T Gn
+  e = gemm<true, false, float>(H, s.P, rows, d_h1, H, mrows, s.P, grad + s.oW1 + R * R, s.Din, nullptr, false, st);
   if (e != cudaSuccess) return e;
   k_segment_sum<<<blocks_for(static_cast<int64_t>(groups) * H), 256, 0, st>>>(d_h1, offs, groups, H, gsum);
   e = gemm<true, false, float>(H, R * R, groups, gsum, H, Gn, R * R, grad + s.oW1, s.Din, nullptr, false, st);
@@ -315,18 +317,33 @@ cudaError_t mlp_refresh_bf16(const MlpShape& s, const float* p, __nv_bfloat16* p
 namespace ntf {
 namespace {
 
-// Gn = G / s and mrows = M / s with s = trace(G) / R (G: FP32 coefficient matrix, no rho).
-__global__ void k_ws_prepare(const float* __restrict__ G, const float* __restrict__ M, int R,
-                             int64_t I, float* __restrict__ Gn, float* __restrict__ mrows,
-                             float* __restrict__ s_out) {
+// Gn = G / s and the per-row inputs mrows[i] = [m_i / s ; z_i], z_i = Hinv m_i, with
+// s = trace(G) / R (G: FP32 coefficient matrix without rho; Hinv: the update's FP32
+// (G + rho I)^{-1}, rho = s under the trace policy).  One thread per output value.
+__global__ void k_ws_prepare(const float* __restrict__ G, const float* __restrict__ Hinv,
+                             const float* __restrict__ M, int R, int64_t I, float* __restrict__ Gn,
+                             float* __restrict__ mrows, float* __restrict__ s_out) {
   float tr = 0.0f;
   for (int i = 0; i < R; ++i) tr += G[i * R + i];
   const float s = tr / R, inv = 1.0f / s;
-  const int64_t nG = static_cast<int64_t>(R) * R, nM = I * R;
+  const int64_t nG = static_cast<int64_t>(R) * R, nM = I * 2 * R;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < nG + nM;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if (i < nG) Gn[i] = G[i] * inv;
-    else mrows[i - nG] = M[i - nG] * inv;
+    if (i < nG) {
+      Gn[i] = G[i] * inv;
+      continue;
+    }
+    const int64_t k = i - nG, row = k / (2 * R);
+    const int c = static_cast<int>(k % (2 * R));
+    const float* m = M + row * R;
+    float v;
+    if (c < R) {
+      v = m[c] * inv;
+    } else {
+      v = 0.0f;
+      for (int j = 0; j < R; ++j) v = fmaf(Hinv[j * R + (c - R)], m[j], v);  // Hinv symmetric
+    }
+    mrows[k] = v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *s_out = s;
 }
@@ -400,10 +417,10 @@ __global__ void k_ws_judge(const float* __restrict__ out, const float* __restric
 
 }  // namespace
 
-cudaError_t ws_prepare(const float* G, const float* M, int R, int64_t I, float* Gn, float* mrows,
-                       float* s_out, cudaStream_t st) {
-  const int64_t n = static_cast<int64_t>(R) * R + I * R;
-  k_ws_prepare<<<blocks_for(n), 256, 0, st>>>(G, M, R, I, Gn, mrows, s_out);
+cudaError_t ws_prepare(const float* G, const float* Hinv, const float* M, int R, int64_t I,
+                       float* Gn, float* mrows, float* s_out, cudaStream_t st) {
+  const int64_t n = static_cast<int64_t>(R) * R + I * 2 * R;
+  k_ws_prepare<<<blocks_for(n), 256, 0, st>>>(G, Hinv, M, R, I, Gn, mrows, s_out);
   return cudaGetLastError();
 }
 

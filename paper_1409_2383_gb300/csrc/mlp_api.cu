@@ -21,7 +21,7 @@ struct ntf_mlp {
   int* row_group = nullptr;      // [max_rows]
   int* all_offs = nullptr;       // {0, rows}
   float* Gn = nullptr;           // warm start: normalised G [R^2]
-  float* mrows = nullptr;        // warm start: normalised MTTKRP rows [max_rows, R]
+  float* mrows = nullptr;        // warm start: per-row inputs [max_rows, 2R]
   float* s_dev = nullptr;        // warm start: scale
   double* loss_part = nullptr;   // [64]
   double* loss_dev = nullptr;
@@ -68,7 +68,7 @@ ntf_status check_batch(const ntf_mlp* n, int groups, int rows) {
 }
 
 // Forward for a batch given as normalised coefficient matrices Gn [groups, R^2], CSR offsets
-// (rows of a group contiguous) and normalised MTTKRP rows [rows, R].
+// (rows of a group contiguous) and per-row inputs [rows, 2R] = [m/s ; z].
 ntf_status forward_batch(ntf_mlp* n, const float* Gn, const int* offs, int groups,
                          const float* mrows, int rows, cudaStream_t st) {
   MLP_CUDA(ntf::mlp_row_groups(offs, groups, n->row_group, st));
@@ -86,7 +86,8 @@ cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float*
                            float* Y, int64_t I, unsigned long long* counters, cudaStream_t st) {
   const int R = n->s.R;
   const float* G = update_sys_h32(sys, mode, R);
-  cudaError_t e = ws_prepare(G, M, R, I, n->Gn, n->mrows, n->s_dev, st);
+  cudaError_t e = ws_prepare(G, update_sys_hinv32(sys, mode, R), M, R, I, n->Gn, n->mrows,
+                             n->s_dev, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->row_group, 0, I * sizeof(int), st);
   if (e == cudaSuccess) e = mlp_group_terms(n->s, n->pb, n->Gn, 1, n->hG, st);
   if (e == cudaSuccess)
@@ -137,7 +138,7 @@ ntf_status ntf_mlp_create(ntf_mlp** out, int rank, int hidden, const float* h_pa
   A((void**)&n->row_group, static_cast<size_t>(max_rows) * 4);
   A((void**)&n->all_offs, 2 * 4);
   A((void**)&n->Gn, R * R * 4);
-  A((void**)&n->mrows, static_cast<size_t>(max_rows) * R * 4);
+  A((void**)&n->mrows, static_cast<size_t>(max_rows) * 2 * R * 4);
   A((void**)&n->s_dev, 4);
   A((void**)&n->loss_part, 64 * 8);
   A((void**)&n->loss_dev, 8);

@@ -40,6 +40,7 @@ struct Ctrl {
   int bad[kMaxOrder];             // 1 if the last system of factor n was not SPD
   int pad[3];
   unsigned long long ws_rows[2];  // warm start: rows considered, rows that took the prediction
+  unsigned int red_count[kMaxOrder];  // CTAs of the running rows kernel that have finished
 };
 
 // ------------------------------------------------------------------ kernel launchers
@@ -142,12 +143,14 @@ int update_scalars();
 size_t update_sys_bytes(int N, int R);
 cudaError_t launch_update_system(const UpdateCall& u, cudaStream_t st);
 cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st);
+// no-op when the rows kernel reduces its own partials (update_fused)
 cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st);
+bool update_fused(const UpdateCall& u);
 cudaError_t launch_update(const UpdateCall& u, cudaStream_t st);
 
 // mlp.cu: warm-start network (parameter layout, forward, backward, Adam) and its use
 struct MlpShape {
-  int R, H, Din, Dout;
+  int R, H, P, Din, Dout;  // P: per-row input width (2R)
   int64_t oW1, ob1, oW2, ob2, oW3, ob3, count;  // offsets into the flat parameter array
 };
 MlpShape mlp_shape(int R, int H);
@@ -167,13 +170,15 @@ cudaError_t mlp_adam(const MlpShape& s, float* p, const float* grad, float* m, f
                      __nv_bfloat16* pb, float lr, int step, cudaStream_t st);
 cudaError_t mlp_row_groups(const int* offs, int groups, int* row_group, cudaStream_t st);
 cudaError_t mlp_refresh_bf16(const MlpShape& s, const float* p, __nv_bfloat16* pb, cudaStream_t st);
-cudaError_t ws_prepare(const float* G, const float* M, int R, int64_t I, float* Gn, float* mrows,
-                       float* s_out, cudaStream_t st);
+cudaError_t ws_prepare(const float* G, const float* Hinv, const float* M, int R, int64_t I,
+                       float* Gn, float* mrows, float* s_out, cudaStream_t st);
 cudaError_t ws_judge(const float* out, const float* G, const float* M, const float* s_ptr,
                      float* At, float* Y, int64_t I, int R, unsigned long long* counters,
                      cudaStream_t st);
-// update.cu: FP32 coefficient matrix (no rho) of factor `mode` in its system slot
+// update.cu: FP32 coefficient matrix (no rho) and FP32 (G + rho I)^{-1} of factor `mode` in
+// its system slot
 const float* update_sys_h32(const double* sys, int mode, int R);
+const float* update_sys_hinv32(const double* sys, int mode, int R);
 
 // mlp_api.cu: warm start of a factor update by an attached network
 cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float* M, float* At,

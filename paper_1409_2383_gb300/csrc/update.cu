@@ -23,7 +23,9 @@ namespace {
 constexpr int kRowWarps = 8;  // rows per CTA
 constexpr int kRowThreads = kRowWarps * 32;
 constexpr int kScal = 8;      // scalar partials per CTA
-constexpr int kRedEntries = 64;
+// The rows kernel reduces its own partials (in its last CTA) when there are at most this many
+// Gram partial entries to add; larger sets go to the separate multi-CTA reduction.
+constexpr int64_t kFusedReduceMax = 32768;
 
 // Per-mode system slot: H^{-1} in FP64, H^{-1} and H (without rho) in FP32.
 struct SysView {
@@ -54,6 +56,7 @@ struct UpdArgs {
   double* gram_out;     // [R, R] stored Gram of this factor
   int64_t I;
   int N, mode, R, inner, rho_policy, kr_aux, want_fit;
+  int fused;            // rows kernel also reduces (last CTA)
   double mu, tau_incr, tau_decr;
 };
 
@@ -190,6 +193,8 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
   }
 }
 
+__device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
+
 // Rows.  Real = float (trace policy) or double.  One warp per row, lanes own elements lane
 // and lane + 32; v and f are broadcast through a per-warp shared buffer.
 template <typename Real>
@@ -322,56 +327,33 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
     }
     gp[idx] = g0 + g1;
   }
+  if (!a.fused) return;
+  // the last CTA to finish sums every CTA's partials (fixed order, so the result does not
+  // depend on which CTA that is) and resets the counter for the next launch
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&a.ctrl->red_count[a.mode], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  update_reduce_cta(a, gridDim.x);
+  if (tid == 0) a.ctrl->red_count[a.mode] = 0;
 }
 
-// CTAs 0..gridDim.x-2: 64 Gram entries each, 4 threads per entry summing every 4th block,
-// combined in a fixed order.  Last CTA: residuals, penalty rule, fit.
-__global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
-  __shared__ double sred[256][kScal];
-  const int tid = threadIdx.x;
-  if (a.ctrl->bad[a.mode]) return;
-  const int RR = a.R * a.R;
-  if (blockIdx.x + 1 < gridDim.x) {
-    const int e = blockIdx.x * kRedEntries + tid / 4, part = tid % 4;
-    double s0 = 0.0, s1 = 0.0;
-    if (e < RR) {
-      int b = part;
-      for (; b + 4 < nblocks; b += 8) {
-        s0 += a.gram_part[static_cast<int64_t>(b) * RR + e];
-        s1 += a.gram_part[static_cast<int64_t>(b + 4) * RR + e];
-      }
-      if (b < nblocks) s0 += a.gram_part[static_cast<int64_t>(b) * RR + e];
-    }
-    sred[tid][0] = s0 + s1;
-    __syncthreads();
-    if (part == 0 && e < RR)
-      a.gram_out[e] = ((sred[tid][0] + sred[tid + 1][0]) + sred[tid + 2][0]) + sred[tid + 3][0];
-    return;
-  }
-  double s[kScal] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = tid; b < nblocks; b += 256)
-#pragma unroll
-    for (int q = 0; q < kScal; ++q) s[q] += a.scal_part[b * kScal + q];
-#pragma unroll
-  for (int q = 0; q < kScal; ++q) sred[tid][q] = s[q];
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (tid < w)
-#pragma unroll
-      for (int q = 0; q < kScal; ++q) sred[tid][q] += sred[tid + w][q];
-    __syncthreads();
-  }
-  if (tid != 0) return;
+// Residual norms, penalty rule (Sec. III-D) and, for the last factor of a sweep, the fit,
+// from the fixed-order sums of the scalar partials (one thread).
+__device__ void update_finalize(const UpdArgs& a, const double* sum) {
   Ctrl* c = a.ctrl;
   const double rho = c->stats[a.mode][5];
-  const double P = sqrt(sred[0][0]), D = rho * sqrt(sred[0][1]);
+  const double P = sqrt(sum[0]), D = rho * sqrt(sum[1]);
   c->stats[a.mode][0] = P;
   c->stats[a.mode][1] = D;
-  c->stats[a.mode][2] = sqrt(sred[0][2]);
-  c->stats[a.mode][3] = sqrt(sred[0][3]);
-  c->stats[a.mode][4] = sqrt(sred[0][4]);
+  c->stats[a.mode][2] = sqrt(sum[2]);
+  c->stats[a.mode][3] = sqrt(sum[3]);
+  c->stats[a.mode][4] = sqrt(sum[4]);
   bool finite = true;
-  for (int q = 0; q < 5; ++q) finite = finite && isfinite(sred[0][q]);
+  for (int q = 0; q < 5; ++q) finite = finite && isfinite(sum[q]);
   if (a.rho_policy == NTF_RHO_ADAPTIVE) {
     // eq. (varying_penalty_rule); the cases exclude each other because mu > 1
     double r = rho;
@@ -382,7 +364,7 @@ __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
     c->rho[a.mode] = rho;
   }
   if (a.want_fit) {
-    const double inner = sred[0][5], quad = sred[0][6];
+    const double inner = sum[5], quad = sum[6];
     const double e2 = c->x_norm2 - 2.0 * inner + quad;
     c->fit_inner = inner;
     c->fit_gram = quad;
@@ -392,10 +374,76 @@ __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
   if (!finite) atomicOr(&c->status, kStNonFinite);
 }
 
+// Gram entry e of the updated factor: the per-CTA partials summed over blocks in a fixed order,
+// read from L2 sixteen blocks at a time (the loads of a batch are independent, so they are in
+// flight together; consecutive threads read consecutive entries).
+__device__ __forceinline__ double gram_entry_sum(const UpdArgs& a, int nblocks, int e) {
+  const int RR = a.R * a.R;
+  constexpr int kB = 16;
+  double s = 0.0;
+  int b = 0;
+  for (; b + kB <= nblocks; b += kB) {
+    double t[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) t[u] = __ldcg(a.gram_part + static_cast<int64_t>(b + u) * RR + e);
+#pragma unroll
+    for (int w = kB / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) t[u] += t[u + w];
+    s += t[0];
+  }
+  for (; b < nblocks; ++b) s += __ldcg(a.gram_part + static_cast<int64_t>(b) * RR + e);
+  return s;
+}
+
+// Scalar partial q summed over blocks by one warp: lane l takes blocks l, l + 32, ... and the
+// lanes are combined by a fixed butterfly.
+__device__ __forceinline__ double scalar_sum(const UpdArgs& a, int nblocks, int q, int lane) {
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += __ldcg(a.scal_part + b * kScal + q);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// The whole reduction in one CTA of 256 threads (8 warps: one per scalar).
+__device__ void update_reduce_cta(const UpdArgs& a, int nblocks) {
+  __shared__ double s_sum[kScal];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int RR = a.R * a.R;
+  for (int e = tid; e < RR; e += blockDim.x) a.gram_out[e] = gram_entry_sum(a, nblocks, e);
+  for (int q = warp; q < kScal; q += blockDim.x / 32) {
+    const double v = scalar_sum(a, nblocks, q, lane);
+    if (lane == 0) s_sum[q] = v;
+  }
+  __syncthreads();
+  if (tid == 0) update_finalize(a, s_sum);
+}
+
+// Separate reduction (large partial sets): CTAs 0..gridDim.x-2 sum 256 Gram entries each,
+// the last CTA the scalars.
+__global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
+  __shared__ double s_sum[kScal];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (a.ctrl->bad[a.mode]) return;
+  const int RR = a.R * a.R;
+  if (blockIdx.x + 1 < gridDim.x) {
+    const int e = blockIdx.x * 256 + tid;
+    if (e < RR) a.gram_out[e] = gram_entry_sum(a, nblocks, e);
+    return;
+  }
+  const double v = scalar_sum(a, nblocks, warp, lane);
+  if (lane == 0) s_sum[warp] = v;
+  __syncthreads();
+  if (tid == 0) update_finalize(a, s_sum);
+}
+
 }  // namespace
 
 const float* update_sys_h32(const double* sys, int mode, int R) {
   return sys_view(const_cast<double*>(sys), mode, R).h32;
+}
+const float* update_sys_hinv32(const double* sys, int mode, int R) {
+  return sys_view(const_cast<double*>(sys), mode, R).hinv32;
 }
 
 int update_blocks(int64_t I) { return static_cast<int>((I + kRowWarps - 1) / kRowWarps); }
@@ -423,6 +471,7 @@ UpdArgs make_args(const UpdateCall& u) {
   a.rho_policy = u.rho_policy;
   a.kr_aux = u.kr_aux ? 1 : 0;
   a.want_fit = u.want_fit ? 1 : 0;
+  a.fused = update_fused(u) ? 1 : 0;
   a.mu = u.mu;
   a.tau_incr = u.tau_incr;
   a.tau_decr = u.tau_decr;
@@ -464,9 +513,14 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+bool update_fused(const UpdateCall& u) {
+  return static_cast<int64_t>(update_blocks(u.I)) * u.R * u.R <= kFusedReduceMax;
+}
+
 cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st) {
+  if (update_fused(u)) return cudaSuccess;  // done by the rows kernel
   const UpdArgs a = make_args(u);
-  const int gram_ctas = (u.R * u.R + kRedEntries - 1) / kRedEntries;
+  const int gram_ctas = (u.R * u.R + 255) / 256;
   k_update_reduce<<<gram_ctas + 1, 256, 0, st>>>(a, update_blocks(u.I));
   return cudaGetLastError();
 }

@@ -27,7 +27,7 @@ from . import ntf
 def init_params(R: int, H: int, seed: int) -> torch.Tensor:
     """Glorot-uniform weights, zero biases, in the flat parameter layout of the ABI."""
     g = np.random.default_rng(seed)
-    Din, Dout = R * R + R, 2 * R
+    Din, Dout = R * R + 2 * R, 2 * R
 
     def glorot(fo, fi):
         a = math.sqrt(6.0 / (fi + fo))
@@ -43,14 +43,16 @@ class RowSet:
     """Training rows grouped by coefficient matrix (device tensors)."""
     R: int
     Gn: List[torch.Tensor] = field(default_factory=list)       # [R*R] each
-    mrows: List[torch.Tensor] = field(default_factory=list)    # [rows, R] each
+    mrows: List[torch.Tensor] = field(default_factory=list)    # [rows, 2R] each: [m/s ; z]
     targets: List[torch.Tensor] = field(default_factory=list)  # [rows, 2R] each
+    _packed: Optional[tuple] = None
 
     @property
     def rows(self) -> int:
         return sum(int(m.shape[0]) for m in self.mrows)
 
     def batch(self, idx: Sequence[int]):
+        """Whole groups idx as one batch: (Gn [g, R^2], CSR offsets, row inputs, targets)."""
         Gn = torch.stack([self.Gn[i] for i in idx])
         mr = torch.cat([self.mrows[i] for i in idx])
         tg = torch.cat([self.targets[i] for i in idx])
@@ -58,6 +60,25 @@ class RowSet:
         for i in idx:
             offs.append(offs[-1] + int(self.mrows[i].shape[0]))
         return Gn, torch.tensor(offs, dtype=torch.int32, device=mr.device), mr, tg
+
+    def sample(self, groups: int, rows_per_group: int, gen: torch.Generator):
+        """A training batch of `rows_per_group` random rows from each of `groups` random
+        groups: many coefficient matrices per step (whole-group batches see only a few and
+        train markedly worse)."""
+        if self._packed is None or self._packed[0] != len(self.Gn):
+            sizes = torch.tensor([int(m.shape[0]) for m in self.mrows], device=self.Gn[0].device)
+            start = torch.cumsum(sizes, 0) - sizes
+            self._packed = (len(self.Gn), torch.stack(self.Gn), torch.cat(self.mrows),
+                            torch.cat(self.targets), start, sizes)
+        n, G_all, M_all, T_all, start, sizes = self._packed
+        dev = G_all.device
+        gi = torch.randint(n, (groups,), generator=gen, device=dev)
+        u = torch.rand(groups, rows_per_group, generator=gen, device=dev)
+        ridx = (start[gi][:, None] + (u * sizes[gi][:, None]).long()).reshape(-1)
+        offs = torch.arange(0, groups * rows_per_group + 1, rows_per_group, dtype=torch.int32,
+                            device=dev)
+        return (G_all[gi].contiguous(), offs, M_all[ridx].contiguous(),
+                T_all[ridx].contiguous())
 
 
 def synthetic_tensor(dims: Sequence[int], R: int, seed: int, snr_db: float = 20.0,
@@ -121,7 +142,8 @@ def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
                     Ac, Tc, Yc = A[n].clone(), At[n].clone(), Y[n].clone()
                     conv.admm_update(n, M, Ac, Tc, Yc, stats=False)
                     rows.Gn.append((G / s).float().reshape(-1).contiguous())
-                    rows.mrows.append((M / s).contiguous())
+                    Z = torch.linalg.solve(H, M.double().T).T      # (G + rho I)^{-1} m
+                    rows.mrows.append(torch.cat([M / s, Z.float()], dim=1).contiguous())
                     rows.targets.append(torch.cat([Tc, Yc / s], dim=1).contiguous())
                     conv.gram(n, At[n])  # restore: the converged update refreshed its Gram
                 ctx.admm_update(n, M, A[n], At[n], Y[n], stats=False)
@@ -131,15 +153,15 @@ def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
 
 
 def train(net: ntf.Mlp, rows: RowSet, steps: int, groups_per_batch: int, lr: float,
-          seed: int = 0, log_every: int = 0, decay_at: float = 1.0) -> List[float]:
-    """Adam on random batches of whole groups (learning rate divided by 10 after a fraction
-    `decay_at` of the steps); returns the loss of every logged step."""
-    g = np.random.default_rng(seed)
-    n = len(rows.Gn)
+          seed: int = 0, log_every: int = 0, decay_at: float = 1.0,
+          rows_per_group: int = 25) -> List[float]:
+    """Adam on random batches of `rows_per_group` rows from each of `groups_per_batch` random
+    groups (learning rate divided by 10 after a fraction `decay_at` of the steps); returns
+    the loss of every logged step."""
+    gen = torch.Generator(device=rows.Gn[0].device).manual_seed(seed)
     losses = []
     for t in range(steps):
-        idx = g.choice(n, size=min(groups_per_batch, n), replace=False)
-        Gn, offs, mr, tg = rows.batch(sorted(idx.tolist()))
+        Gn, offs, mr, tg = rows.sample(groups_per_batch, rows_per_group, gen)
         want = bool(log_every) and (t % log_every == 0 or t == steps - 1)
         lr_t = lr if t < decay_at * steps else 0.1 * lr
         loss = net.train_step(Gn, offs, mr, tg, lr_t, apply=True, want_loss=want)

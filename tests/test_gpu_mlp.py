@@ -30,7 +30,7 @@ def rel(a, b):
 
 def _split(flat, R, H):
     """Flat parameter array -> oracle dict, weights rounded to BF16 as the GPU products use."""
-    Din, D = R * R + R, 2 * R
+    Din, D = R * R + 2 * R, 2 * R
     sizes = [("W1", (H, Din)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (D, H)),
              ("b3", (D,))]
     out, i = {}, 0
@@ -56,8 +56,9 @@ def _batch(R, groups, rows_per, seed):
         Yd = np.zeros_like(m)
         for i in range(rows_per[g]):
             X[i], Yd[i] = om.nnls_row(G, m[i])
+        U, _ = om.features(G, m)
         Gn.append(G / s)
-        M.append(m / s)
+        M.append(U[:, R * R:])                   # per-row inputs [m/s ; z]
         T.append(om.targets(G, X, Yd, s))
     offs = np.concatenate([[0], np.cumsum(rows_per)]).astype(np.int32)
     return Gn, M, T, offs
@@ -82,7 +83,7 @@ def _dense_U(Gn, M, offs):
 def test_forward_and_gradients_match_oracle(ntf, R, H):
     from paper_1409_2383_gb300 import warmstart
     flat = warmstart.init_params(R, H, seed=R).numpy()
-    flat[H * (R * R + R):H * (R * R + R) + H] = 0.05      # non-zero biases
+    flat[H * (R * R + 2 * R):H * (R * R + 2 * R) + H] = 0.05      # non-zero biases
     net = ntf.Mlp(R, H, torch.as_tensor(flat), max_rows=256, max_groups=8)
     Gn, M, T, offs = _batch(R, 3, [7, 30, 11], seed=R + 1)
     dG, doffs, dM, dT = _dev(Gn, M, T, offs)
@@ -99,7 +100,7 @@ def test_forward_and_gradients_match_oracle(ntf, R, H):
     g_o = om.backward(p, cache, out_o, Tn)
     flat_g = grad.cpu().numpy()
     i = 0
-    for k, shp in [("W1", (H, R * R + R)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)),
+    for k, shp in [("W1", (H, R * R + 2 * R)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)),
                    ("W3", (2 * R, H)), ("b3", (2 * R,))]:
         n = int(np.prod(shp))
         assert rel(flat_g[i:i + n].reshape(shp), g_o[k]) <= 2e-4, k
@@ -171,11 +172,8 @@ def test_warm_start_judge_in_factor_update(ntf):
         prof = ctx.profile_get()
     assert prof["ws_rows_considered"] == dims[n]
     # replay in FP64: network candidate vs carried state, judged as the oracle judge does
-    s = np.trace(G) / R
     Gf = G.astype(np.float32).astype(np.float64)
-    sf = np.trace(Gf) / R
-    U = np.concatenate([np.tile((Gf / sf).reshape(1, -1), (dims[n], 1)),
-                        M.astype(np.float64) / sf], axis=1)
+    U, sf = om.features(Gf, M.astype(np.float64))
     out, _ = om.forward(_split(flat.numpy(), R, H), U)
     xc, yc = om.decode(out, sf, R)
 
@@ -206,7 +204,8 @@ def test_warm_start_judge_in_factor_update(ntf):
 
 
 def test_harvest_rows_are_converged_nnls_solutions(ntf):
-    """Harvested targets solve the row NNLS of their coefficient matrix (KKT of eq. KKT_NTF)."""
+    """Harvested targets solve the row NNLS of their coefficient matrix (KKT of eq. KKT_NTF);
+    the z inputs are the first ADMM primal iterates from zero."""
     from paper_1409_2383_gb300 import warmstart
     import synth
     dims, R = (30, 28, 26), 4
@@ -217,7 +216,10 @@ def test_harvest_rows_are_converged_nnls_solutions(ntf):
     assert len(rows.Gn) == 6 and rows.rows == 2 * sum(dims)
     for g in range(len(rows.Gn)):
         G = rows.Gn[g].double().cpu().numpy().reshape(R, R)
-        m = rows.mrows[g].double().cpu().numpy()
+        u = rows.mrows[g].double().cpu().numpy()
+        m, z = u[:, :R], u[:, R:]
         t = rows.targets[g].double().cpu().numpy()
         k = o.kkt_nnls(G, m, t[:, :R], t[:, R:])
         assert k["neg_x"] == 0 and k["dual"] < 1e-4 and k["comp"] < 1e-5
+        # z = (G + s I)^{-1} m in the normalised variables: (G/s + I)^{-1} (m/s)
+        assert rel(z, np.linalg.solve(G + np.eye(R), m.T).T) <= 1e-5

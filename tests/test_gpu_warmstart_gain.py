@@ -1,7 +1,7 @@
 """What the trained warm-start network gains over the plain method.
 
-The network is trained (by the library's kernels) on rows harvested from the first two
-sweeps of tensors of the workload generator with other seeds, then consulted in the first
+The network is trained (by the library's kernels) on rows harvested from the first
+sweep of tensors of the workload generator with other seeds, then consulted in the first
 sweep of a factorization of a held-out tensor.  On that tensor the test compares, with and
 without it, the relative error after each of the first sweeps and the iterations and time to
 the fit target.  It requires that the network wins a substantial share of the first sweep's
@@ -39,11 +39,12 @@ def _history(ntf, X, R, init, sweeps, net=None):
 def test_trained_network_on_held_out_tensor(ntf):
     from paper_1409_2383_gb300 import warmstart
     dims, R, H = (64, 64, 64), 8, 128
-    rows = warmstart.training_set(dims, R, rows=60000, sweeps=2, seed0=1)
+    rows = warmstart.training_set(dims, R, rows=60000, sweeps=1, seed0=1)
     net = ntf.Mlp(R, H, warmstart.init_params(R, H, seed=0), max_rows=16 * max(dims),
-                  max_groups=16)
+                  max_groups=64)
     before = warmstart.eval_loss(net, rows, 16)
-    warmstart.train(net, rows, steps=2000, groups_per_batch=16, lr=1e-3, decay_at=0.7)
+    warmstart.train(net, rows, steps=2000, groups_per_batch=64, lr=1e-3, decay_at=0.7,
+                    rows_per_group=16)
     after = warmstart.eval_loss(net, rows, 16)
     assert after < 0.2 * before
 

@@ -34,7 +34,7 @@ def test_gelu_grad_finite_difference():
 
 def test_backward_matches_central_differences():
     R, H = 3, 7
-    Din, Dout = R * R + R, 2 * R
+    Din, Dout = R * R + 2 * R, 2 * R
     p = _params(Din, H, Dout)
     rng = np.random.default_rng(1)
     U = rng.standard_normal((5, Din))
@@ -141,3 +141,17 @@ def test_judge_needs_both_criteria():
     assert not np.any(mlp.judge(G, M, Xp, Xs))
     # a candidate equal to the carried state is not taken (strict comparisons)
     assert not np.any(mlp.judge(G, M, Xp, Xp))
+
+
+def test_z_feature_is_the_first_admm_iterate_from_zero():
+    """The z part of the features equals the primal of one step of eq. (ADMM_NTF_ALS_C) from a
+    zero auxiliary and dual with rho = trace(G)/R (the oracle's Cholesky-based update)."""
+    rng = np.random.default_rng(23)
+    R = 6
+    K = rng.random((4 * R, R))
+    G = K.T @ K
+    M = rng.random((9, R)) * 3.0
+    U, s = mlp.features(G, M)
+    A, _, _, _ = o.admm_factor_update(M, G, np.zeros_like(M), np.zeros_like(M), s, 1)
+    assert np.allclose(U[:, R * R + R:], A, rtol=1e-12, atol=1e-12)
+    assert np.allclose(U[:, R * R:R * R + R], M / s)
