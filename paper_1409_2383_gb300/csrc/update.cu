@@ -25,7 +25,8 @@ constexpr int kRowThreads = kRowWarps * 32;
 constexpr int kScal = 8;      // scalar partials per CTA
 // The rows kernel reduces its own partials (in its last CTA) when there are at most this many
 // Gram partial entries to add; larger sets go to the separate multi-CTA reduction.
-constexpr int64_t kFusedReduceMax = 32768;
+constexpr int64_t kFusedReduceMax = 2048;
+constexpr int kRedEntries = 64;  // Gram entries per CTA of the separate reduction
 
 // Per-mode system slot: H^{-1} in FP64, H^{-1} and H (without rho) in FP32.
 struct SysView {
@@ -77,18 +78,33 @@ __device__ __forceinline__ double recip_newton(double p) {
 // Gauss-Jordan elimination without pivoting in symmetric form: valid and stable for SPD H,
 // where every pivot is a Schur-complement diagonal entry, positive exactly when H is SPD.
 //
-// FP64 on this GPU runs at a small fraction of the FP32 rate, so the kernel minimises FP64
-// lane operations: only the lower triangle is kept (in registers, S packed entries per
-// thread), one warp forms 1/d and the scaled pivot column, and every other entry costs one
-// FP64 multiply-add per step.  The pivot column and its scaled copy are broadcast through
-// shared memory (double-buffered, two barriers per step).
+// Division-free form: the kernel holds B = c A for a tracked scalar c > 0 and applies the
+// sweep to B as
+//   b_ij -> 2^e (b_ij b_kk - b_ik b_kj),   b_ik -> c 2^e b_ik,   b_kk -> -c^2 2^e,
+//   c -> c b_kk 2^e,
+// with 2^e the power of two that brings b_kk into [1, 2) (exact scaling, so the entries stay
+// of the size of H); at the end H^{-1} = -B / c with the only reciprocal.  No reciprocal sits
+// on the per-step dependency chain, and each entry costs one FP64 multiply and one
+// multiply-add per step (FP64 runs at a small fraction of the FP32 rate on this GPU, so the
+// work is kept to that).  Only the lower triangle is kept, in registers (S packed entries per
+// thread); the pivot column is broadcast through shared memory (double-buffered, one barrier
+// per step).
 constexpr int kSysThreads = 128;
+
+// x 2^e: exact, on the integer exponent field when x and the result are normal numbers;
+// otherwise (zero, subnormal, NaN, infinity, leaving the normal range) by the multiply, which
+// keeps NaN and infinity what they are.
+__device__ __forceinline__ double scale_pow2(double x, int e, double two_e) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = static_cast<int>((bits >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF || ex + e <= 0 || ex + e >= 0x7FF) return x * two_e;
+  return __longlong_as_double(bits + (static_cast<long long>(e) << 52));
+}
 
 template <int S>
 __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
-  __shared__ double s_col[2][64], s_sc[2][64], s_ip[2];
+  __shared__ double s_col[2][64];
   __shared__ double s_red[kSysThreads / 32];
-  __shared__ int s_fail;
   const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SysView sv = sys_view(a.sys, a.mode, R);
@@ -117,7 +133,6 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
   }
   for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
   if (lane == 0) s_red[warp] = tr;
-  if (tid == 0) s_fail = 0;
   __syncthreads();
   double rho;
   if (a.rho_policy == NTF_RHO_TRACE) {
@@ -128,60 +143,56 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
   } else {
     rho = a.ctrl->rho[a.mode];
   }
-  if (!(rho > 0.0) || !isfinite(rho)) {
-    if (tid == 0) {
-      a.ctrl->bad[a.mode] = 1;
-      atomicOr(&a.ctrl->status, kStNotSpd);
-    }
-    return;  // uniform
-  }
+  bool fail = !(rho > 0.0) || !isfinite(rho);
 #pragma unroll
   for (int q = 0; q < S; ++q)
     if (ii[q] >= 0 && ii[q] == jj[q]) v[q] += rho;
 
-  for (int k = 0; k < R; ++k) {
+  double c = 1.0;  // B = c A, the same value in every thread
+  for (int k = 0; k < R && !fail; ++k) {
     const int b = k & 1;
-    // publish column k (= row k): a_xk for every x
 #pragma unroll
-    for (int q = 0; q < S; ++q) {
+    for (int q = 0; q < S; ++q) {  // publish column k of B
       if (ii[q] == k) s_col[b][jj[q]] = v[q];
       else if (jj[q] == k) s_col[b][ii[q]] = v[q];
     }
-    __syncthreads();
-    if (warp == 0) {
-      const double d = s_col[b][k];
-      const bool bad = !(d > 0.0) || !isfinite(d);
-      const double ip = bad ? 0.0 : recip_newton(d);
-      for (int x = lane; x < R; x += 32) s_sc[b][x] = s_col[b][x] * ip;
-      if (lane == 0) {
-        s_ip[b] = ip;
-        if (bad) s_fail = 1;
-      }
+    __syncthreads();  // one barrier per step: the next step writes the other buffer
+    const double piv = s_col[b][k];
+    const long long pbits = __double_as_longlong(piv);
+    const int pex = static_cast<int>((pbits >> 52) & 0x7FF);
+    if (!(piv > 0.0) || pex == 0 || pex == 0x7FF) {  // not SPD (or not a normal number)
+      fail = true;  // the same shared value in every thread: a uniform exit
+      break;
     }
-    __syncthreads();
-    if (s_fail) break;  // uniform
-    const double ip = s_ip[b];
+    const int e = 1023 - pex;  // piv 2^e in [1, 2)
+    const double two_e = __longlong_as_double(static_cast<long long>(1023 + e) << 52);
+    const double g = scale_pow2(c, e, two_e);  // c 2^e
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       const int i = ii[q], j = jj[q];
       if (i < 0) continue;
-      if (i == k) v[q] = (j == k) ? -ip : s_sc[b][j];
-      else if (j == k) v[q] = s_sc[b][i];
-      else v[q] = fma(-s_col[b][i], s_sc[b][j], v[q]);
+      double x;
+      if (i == k && j == k) x = -c * g;
+      else if (i == k) x = g * s_col[b][j];
+      else if (j == k) x = g * s_col[b][i];
+      else x = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e, two_e);
+      v[q] = x;
     }
+    c = scale_pow2(c * piv, e, two_e);
   }
-  if (s_fail) {
+  if (fail) {
     if (tid == 0) {
       a.ctrl->bad[a.mode] = 1;
       atomicOr(&a.ctrl->status, kStNotSpd);
     }
     return;
   }
+  const double nic = -recip_newton(c);  // H^{-1} = -B / c
 #pragma unroll
   for (int q = 0; q < S; ++q) {
     const int i = ii[q], j = jj[q];
     if (i < 0) continue;
-    const double h = -v[q];  // the swept matrix is -H^{-1}
+    const double h = v[q] * nic;
     sv.hinv64[i * R + j] = h;
     sv.hinv64[j * R + i] = h;
     sv.hinv32[i * R + j] = static_cast<float>(h);
@@ -419,16 +430,29 @@ __device__ void update_reduce_cta(const UpdArgs& a, int nblocks) {
   if (tid == 0) update_finalize(a, s_sum);
 }
 
-// Separate reduction (large partial sets): CTAs 0..gridDim.x-2 sum 256 Gram entries each,
-// the last CTA the scalars.
+// Separate reduction: CTAs 0..gridDim.x-2 sum 64 Gram entries each (4 threads per entry, each
+// over every 4th block, combined in a fixed order), the last CTA the scalars.
 __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
   __shared__ double s_sum[kScal];
+  __shared__ double s_part[256];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.ctrl->bad[a.mode]) return;
   const int RR = a.R * a.R;
   if (blockIdx.x + 1 < gridDim.x) {
-    const int e = blockIdx.x * 256 + tid;
-    if (e < RR) a.gram_out[e] = gram_entry_sum(a, nblocks, e);
+    const int e = blockIdx.x * kRedEntries + tid / 4, part = tid % 4;
+    double s0 = 0.0, s1 = 0.0;
+    if (e < RR) {
+      int b = part;
+      for (; b + 4 < nblocks; b += 8) {
+        s0 += __ldcg(a.gram_part + static_cast<int64_t>(b) * RR + e);
+        s1 += __ldcg(a.gram_part + static_cast<int64_t>(b + 4) * RR + e);
+      }
+      if (b < nblocks) s0 += __ldcg(a.gram_part + static_cast<int64_t>(b) * RR + e);
+    }
+    s_part[tid] = s0 + s1;
+    __syncthreads();
+    if (part == 0 && e < RR)
+      a.gram_out[e] = (s_part[tid] + s_part[tid + 1]) + (s_part[tid + 2] + s_part[tid + 3]);
     return;
   }
   const double v = scalar_sum(a, nblocks, warp, lane);
@@ -520,7 +544,7 @@ bool update_fused(const UpdateCall& u) {
 cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st) {
   if (update_fused(u)) return cudaSuccess;  // done by the rows kernel
   const UpdArgs a = make_args(u);
-  const int gram_ctas = (u.R * u.R + 255) / 256;
+  const int gram_ctas = (u.R * u.R + kRedEntries - 1) / kRedEntries;
   k_update_reduce<<<gram_ctas + 1, 256, 0, st>>>(a, update_blocks(u.I));
   return cudaGetLastError();
 }
