@@ -34,6 +34,9 @@ struct ntf_ctx {
   GemmPlan pn{}, pt{};
   ntf::UmmaPlan un{}, ut{};      // tensor-core plans of the two contractions (on: used)
   int post_split_left = 1, post_split_right = 1;
+  int post4_split_left = 1, post4_split_right = 1;   // vectorised second level (R % 4 == 0)
+  unsigned* post_count = nullptr;  // per-b-block counters of the vectorised slow level
+  int64_t post_count_right = 0;    // offset of the right group's counters
   // workspace
   float* partial = nullptr;      // partial sums of the first contraction and of the posts
   float* partial_b = nullptr;    // partial sums of the second contraction (its own stream)
@@ -63,11 +66,15 @@ struct ntf_ctx {
   ntf_mlp* ws = nullptr;         // attached warm-start network (not owned)
   int ws_sweeps = 0;             // consult it in the first ws_sweeps iterations of a run (0: all)
   bool ws_now = true;            // whether the sweep being enqueued consults it
-  cudaGraphExec_t graph = nullptr;
-  const void* graph_key[3 * ntf::kMaxOrder] = {};
-  int graph_launches = 0;        // kernels in the recorded sweep
-  bool graph_prof = false;       // whether the recorded sweep holds profiling events
-  ntf_mlp* graph_ws = nullptr;   // warm-start network recorded in the sweep
+  // Recorded sweeps: slot 0 without, slot 1 with the warm-start network.
+  struct SweepGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[3 * ntf::kMaxOrder] = {};
+    int launches = 0;            // kernels in the recorded sweep
+    bool prof = false;           // whether it holds profiling events
+    ntf_mlp* ws = nullptr;       // warm-start network recorded in it
+  } graphs[2];
+  bool swept_eagerly = false;    // one eager sweep has set every kernel attribute
   // profiling
   bool prof = false;
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -261,7 +268,15 @@ ntf_status finish_mode(ntf_ctx* c, int mode, const float* T, const float* const*
   }
   const int64_t Ia = c->dims[first], Ib = c->dims[first + 1];
   if (mode == first) {
-    NTF_CUDA(ntf::launch_post_fast(T, Ia, Ib, c->R, F[first + 1], M, st));
+    if (ntf::post4_ok(c->R, T, F[first + 1], M))
+      NTF_CUDA(ntf::launch_post_fast4(T, Ia, Ib, c->R, F[first + 1], M, st));
+    else
+      NTF_CUDA(ntf::launch_post_fast(T, Ia, Ib, c->R, F[first + 1], M, st));
+    c->launches += 1;
+  } else if (ntf::post4_ok(c->R, T, F[first], M)) {
+    const int sp = left ? c->post4_split_left : c->post4_split_right;
+    NTF_CUDA(ntf::launch_post_slow4(T, Ia, Ib, c->R, F[first], sp, c->partial,
+                                    c->post_count + (left ? 0 : c->post_count_right), M, st));
     c->launches += 1;
   } else {
     const int sp = left ? c->post_split_left : c->post_split_right;
@@ -368,7 +383,8 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
 
 void free_ctx(ntf_ctx* c) {
   if (!c) return;
-  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (cudaEvent_t e : {c->ev_start, c->ev_tl, c->ev_b, c->ev_c})
     if (e) cudaEventDestroy(e);
   for (int m = 0; m < ntf::kMaxOrder; ++m)
@@ -380,6 +396,7 @@ void free_ctx(ntf_ctx* c) {
     for (auto& e : pair)
       if (e) cudaEventDestroy(e);
   cudaFree(c->partial);
+  cudaFree(c->post_count);
   cudaFree(c->TR);
   cudaFree(c->TL);
   cudaFree(c->W);
@@ -498,6 +515,20 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     c->post_split_right = ntf::post_slow_splits(dims[c->s_L], dims[c->s_L + 1], R, c->num_sms);
     part = std::max<int64_t>(part, c->post_split_right * dims[c->s_L + 1] * R);
   }
+  int64_t post_counts = 0;
+  if (R % 4 == 0) {
+    if (c->s_R == 2) {
+      c->post4_split_left = ntf::post_slow4_splits(dims[0], dims[1], c->num_sms);
+      part = std::max<int64_t>(part, c->post4_split_left * dims[1] * R);
+      post_counts += ntf::post_slow4_blocks(dims[1]);
+    }
+    c->post_count_right = post_counts;
+    if (order - c->s_L == 2) {
+      c->post4_split_right = ntf::post_slow4_splits(dims[c->s_L], dims[c->s_L + 1], c->num_sms);
+      part = std::max<int64_t>(part, c->post4_split_right * dims[c->s_L + 1] * R);
+      post_counts += ntf::post_slow4_blocks(dims[c->s_L + 1]);
+    }
+  }
   const int64_t w_rows = ntf::kr_rows_padded(c->Q_R), w_rows_b = ntf::kr_rows_padded(c->P_L);
   const int64_t RR = static_cast<int64_t>(R) * R;
   const int upd_blocks = ntf::update_blocks(c->max_dim);
@@ -530,6 +561,9 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     }
   }
   if (e == cudaSuccess) e = alloc((void**)&c->partial, part * sizeof(float));
+  if (e == cudaSuccess) e = alloc((void**)&c->post_count, (post_counts + 1) * sizeof(unsigned));
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->post_count, 0, (post_counts + 1) * sizeof(unsigned), c->st);
   if (e == cudaSuccess) e = alloc((void**)&c->partial_b, part_b * sizeof(float));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sC, cudaStreamNonBlocking);
@@ -759,11 +793,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
 
   // The sweep is recorded once as a CUDA graph (after one eager sweep has set every kernel
   // attribute) and replayed; it is re-recorded only if the state pointers change.  Sweeps
-  // that consult a warm-start network limited to the first iterations run eagerly.
-  bool keys = c->graph != nullptr;
-  for (int m = 0; m < c->N && keys; ++m)
-    keys = c->graph_key[3 * m] == A[m] && c->graph_key[3 * m + 1] == At[m] &&
-           c->graph_key[3 * m + 2] == Y[m];
+  // that consult the warm-start network have their own recording.
   ntf_run_stats rs{};
   rs.rel_err = NAN;
   ntf_status result = NTF_OK;
@@ -773,44 +803,46 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   for (int it = 0; it < max_outer && !done; ++it) {
     c->ws_now = c->ws != nullptr && (c->ws_sweeps == 0 || it < c->ws_sweeps);
     ntf_mlp* const sweep_ws = c->ws_now ? c->ws : nullptr;
-    const bool same = keys && c->graph != nullptr && c->graph_prof == c->prof &&
-                      c->graph_ws == sweep_ws;
+    ntf_ctx::SweepGraph& g = c->graphs[sweep_ws ? 1 : 0];
+    bool same = g.exec != nullptr && g.prof == c->prof && g.ws == sweep_ws;
+    for (int m = 0; m < c->N && same; ++m)
+      same = g.key[3 * m] == A[m] && g.key[3 * m + 1] == At[m] && g.key[3 * m + 2] == Y[m];
     if (same) {
-      NTF_CUDA(cudaGraphLaunch(c->graph, c->st));
-      c->launches += c->graph_launches;
-    } else if (it == 0 || !can_graph || (sweep_ws != nullptr && c->ws_sweeps > 0)) {
+      NTF_CUDA(cudaGraphLaunch(g.exec, c->st));
+      c->launches += g.launches;
+    } else if (!c->swept_eagerly || !can_graph) {
       NTF_TRY(enqueue_sweep(c, A, At, Y));
+      c->swept_eagerly = true;
     } else {
-      if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
+      if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
       }
-      cudaGraph_t g = nullptr;
+      cudaGraph_t gr = nullptr;
       const int64_t before = c->launches;
       bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       ntf_status sw = ok ? enqueue_sweep(c, A, At, Y) : NTF_OK;
-      c->graph_launches = static_cast<int>(c->launches - before);
+      g.launches = static_cast<int>(c->launches - before);
       c->launches = before;
-      if (ok) ok = cudaStreamEndCapture(c->st, &g) == cudaSuccess && sw == NTF_OK;
-      if (ok) ok = cudaGraphInstantiate(&c->graph, g, 0) == cudaSuccess;
-      if (g) cudaGraphDestroy(g);
+      if (ok) ok = cudaStreamEndCapture(c->st, &gr) == cudaSuccess && sw == NTF_OK;
+      if (ok) ok = cudaGraphInstantiate(&g.exec, gr, 0) == cudaSuccess;
+      if (gr) cudaGraphDestroy(gr);
       if (!ok) {
         (void)cudaGetLastError();
-        if (c->graph) cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
         can_graph = false;
         NTF_TRY(enqueue_sweep(c, A, At, Y));
       } else {
-        c->graph_prof = c->prof;
-        c->graph_ws = sweep_ws;
+        g.prof = c->prof;
+        g.ws = sweep_ws;
         for (int m = 0; m < c->N; ++m) {
-          c->graph_key[3 * m] = A[m];
-          c->graph_key[3 * m + 1] = At[m];
-          c->graph_key[3 * m + 2] = Y[m];
+          g.key[3 * m] = A[m];
+          g.key[3 * m + 1] = At[m];
+          g.key[3 * m + 2] = Y[m];
         }
-        keys = true;
-        NTF_CUDA(cudaGraphLaunch(c->graph, c->st));
-        c->launches += c->graph_launches;
+        NTF_CUDA(cudaGraphLaunch(g.exec, c->st));
+        c->launches += g.launches;
       }
     }
     if (c->prof) c->pr.sweeps += 1;

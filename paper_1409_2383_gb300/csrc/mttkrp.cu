@@ -158,6 +158,153 @@ __global__ void k_post_slow(const float* __restrict__ T, int64_t Ia, int64_t Ib,
   out[(static_cast<int64_t>(split) * Ib + b) * R + r] = (s0 + s1) + (s2 + s3);
 }
 
+// Vectorised second tree level for R % 4 == 0 (T, F, out 16-byte aligned), Q = R / 4 float4
+// chunks per row.
+//
+// fast: out[a, :] = sum_b T[a, b, :] * F[b, :].  One CTA (32 Q threads) per a: warp w owns
+// chunk w of every row, lane l the rows b = l, l + 32, ...; four accumulators, then a fixed
+// butterfly over the lanes.
+__global__ void k_post_fast4(const float4* __restrict__ T, int64_t Ia, int64_t Ib, int Q,
+                             const float4* __restrict__ F, float4* __restrict__ out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t a = blockIdx.x; a < Ia; a += gridDim.x) {
+    const float4* Ta = T + a * Ib * Q;
+    float4 s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t b = lane;
+    for (; b + 224 < Ib; b += 256) {  // eight rows per lane in flight
+      float4 t[8], f[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        t[u] = Ta[(b + 32 * u) * Q + w];
+        f[u] = __ldg(F + (b + 32 * u) * Q + w);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        s[u & 3].x = fmaf(t[u].x, f[u].x, s[u & 3].x);
+        s[u & 3].y = fmaf(t[u].y, f[u].y, s[u & 3].y);
+        s[u & 3].z = fmaf(t[u].z, f[u].z, s[u & 3].z);
+        s[u & 3].w = fmaf(t[u].w, f[u].w, s[u & 3].w);
+      }
+    }
+    for (; b + 96 < Ib; b += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 t = Ta[(b + 32 * u) * Q + w], f = __ldg(F + (b + 32 * u) * Q + w);
+        s[u].x = fmaf(t.x, f.x, s[u].x);
+        s[u].y = fmaf(t.y, f.y, s[u].y);
+        s[u].z = fmaf(t.z, f.z, s[u].z);
+        s[u].w = fmaf(t.w, f.w, s[u].w);
+      }
+    }
+    for (; b < Ib; b += 32) {
+      const float4 t = Ta[b * Q + w], f = __ldg(F + b * Q + w);
+      s[0].x = fmaf(t.x, f.x, s[0].x);
+      s[0].y = fmaf(t.y, f.y, s[0].y);
+      s[0].z = fmaf(t.z, f.z, s[0].z);
+      s[0].w = fmaf(t.w, f.w, s[0].w);
+    }
+    float4 v;
+    v.x = (s[0].x + s[1].x) + (s[2].x + s[3].x);
+    v.y = (s[0].y + s[1].y) + (s[2].y + s[3].y);
+    v.z = (s[0].z + s[1].z) + (s[2].z + s[3].z);
+    v.w = (s[0].w + s[1].w) + (s[2].w + s[3].w);
+    for (int off = 16; off > 0; off >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+      v.z += __shfl_xor_sync(0xffffffffu, v.z, off);
+      v.w += __shfl_xor_sync(0xffffffffu, v.w, off);
+    }
+    if (lane == 0) out[a * Q + w] = v;
+  }
+}
+
+// slow: out[b, :] = sum_a T[a, b, :] * F[a, :].  CTA (b-block of kPostBB rows, a-split):
+// thread (bb, chunk) accumulates over its split's a-range; every CTA writes its partial,
+// and the last CTA of a b-block to finish (counter) adds the splits in order 0, 1, ... and
+// resets the counter.
+constexpr int kPostBB = 32;
+__global__ void k_post_slow4(const float4* __restrict__ T, int64_t Ia, int64_t Ib, int Q,
+                             const float4* __restrict__ F, int splits,
+                             float4* __restrict__ partial, unsigned* __restrict__ count,
+                             float4* __restrict__ out) {
+  const int split = blockIdx.y;
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x) * kPostBB;
+  const int t = threadIdx.x;
+  const int bb = t / Q, q = t - bb * Q;
+  const int64_t b = b0 + bb;
+  const int64_t a_beg = Ia * split / splits, a_end = Ia * (split + 1) / splits;
+  float4 s[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) s[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (b < Ib) {
+    int64_t a = a_beg;
+    for (; a + 3 < a_end; a += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 tv = T[((a + u) * Ib + b) * Q + q], f = __ldg(F + (a + u) * Q + q);
+        s[u].x = fmaf(tv.x, f.x, s[u].x);
+        s[u].y = fmaf(tv.y, f.y, s[u].y);
+        s[u].z = fmaf(tv.z, f.z, s[u].z);
+        s[u].w = fmaf(tv.w, f.w, s[u].w);
+      }
+    }
+    for (; a < a_end; ++a) {
+      const float4 tv = T[(a * Ib + b) * Q + q], f = __ldg(F + a * Q + q);
+      s[0].x = fmaf(tv.x, f.x, s[0].x);
+      s[0].y = fmaf(tv.y, f.y, s[0].y);
+      s[0].z = fmaf(tv.z, f.z, s[0].z);
+      s[0].w = fmaf(tv.w, f.w, s[0].w);
+    }
+  }
+  float4 v;
+  v.x = (s[0].x + s[1].x) + (s[2].x + s[3].x);
+  v.y = (s[0].y + s[1].y) + (s[2].y + s[3].y);
+  v.z = (s[0].z + s[1].z) + (s[2].z + s[3].z);
+  v.w = (s[0].w + s[1].w) + (s[2].w + s[3].w);
+  if (splits == 1) {
+    if (b < Ib) out[b * Q + q] = v;
+    return;
+  }
+  if (b < Ib) partial[(static_cast<int64_t>(split) * Ib + b) * Q + q] = v;
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(count + blockIdx.x, 1u) == static_cast<unsigned>(splits - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (b < Ib) {
+    // splits added in order 0, 1, ...; loads issued eight at a time (independent) so that
+    // the L2 round trips overlap
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int k = 0;
+    for (; k + 8 <= splits; k += 8) {
+      float4 p[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        p[u] = __ldcg(partial + (static_cast<int64_t>(k + u) * Ib + b) * Q + q);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc.x += p[u].x;
+        acc.y += p[u].y;
+        acc.z += p[u].z;
+        acc.w += p[u].w;
+      }
+    }
+    for (; k < splits; ++k) {
+      const float4 p = __ldcg(partial + (static_cast<int64_t>(k) * Ib + b) * Q + q);
+      acc.x += p.x;
+      acc.y += p.y;
+      acc.z += p.z;
+      acc.w += p.w;
+    }
+    out[b * Q + q] = acc;
+  }
+  if (t == 0) count[blockIdx.x] = 0;
+}
+
 // ||X||^2 with FP64 accumulation; per-block partials then one block sums them in order.
 template <typename T>
 __global__ void k_norm2(const T* __restrict__ X, int64_t n, double* __restrict__ partial) {
@@ -299,6 +446,41 @@ cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, cons
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   return launch_sum_splits(partial, splits, Ib * R, out, st);
+}
+
+bool post4_ok(int R, const void* T, const void* F, const void* out) {
+  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  return R % 4 == 0 && R <= 128 && al(T) && al(F) && al(out);
+}
+
+cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
+                              float* out, cudaStream_t st) {
+  const int Q = R / 4;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(Ia, 65535));
+  k_post_fast4<<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float4*>(T), Ia, Ib, Q,
+                                          reinterpret_cast<const float4*>(F),
+                                          reinterpret_cast<float4*>(out));
+  return cudaGetLastError();
+}
+
+int post_slow4_splits(int64_t Ia, int64_t Ib, int num_sms) {
+  const int64_t bblocks = (Ib + kPostBB - 1) / kPostBB;
+  int64_t splits = (static_cast<int64_t>(num_sms) * 2 + bblocks - 1) / bblocks;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, Ia / 16)));
+  return static_cast<int>(std::min<int64_t>(splits, 64));
+}
+
+int64_t post_slow4_blocks(int64_t Ib) { return (Ib + kPostBB - 1) / kPostBB; }
+
+cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
+                              int splits, float* partial, unsigned* count, float* out,
+                              cudaStream_t st) {
+  const int Q = R / 4;
+  dim3 grid(static_cast<unsigned>(post_slow4_blocks(Ib)), static_cast<unsigned>(splits));
+  k_post_slow4<<<grid, kPostBB * Q, 0, st>>>(
+      reinterpret_cast<const float4*>(T), Ia, Ib, Q, reinterpret_cast<const float4*>(F), splits,
+      reinterpret_cast<float4*>(partial), count, reinterpret_cast<float4*>(out));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_norm2(const void* X, int dtype, int64_t n, double* partial, int blocks,

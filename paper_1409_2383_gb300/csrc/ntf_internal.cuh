@@ -73,6 +73,16 @@ cudaError_t launch_post_fast(const float* T, int64_t Ia, int64_t Ib, int R, cons
 int post_slow_splits(int64_t Ia, int64_t Ib, int R, int num_sms);
 cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                              int splits, float* partial, float* out, cudaStream_t st);
+// Vectorised variants (R % 4 == 0, 16-byte aligned T, F, out: post4_ok); slow: splits of the
+// reduced range with partials [splits, Ib, R] and per-b-block counters (zeroed, left zeroed)
+bool post4_ok(int R, const void* T, const void* F, const void* out);
+cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
+                              float* out, cudaStream_t st);
+int post_slow4_splits(int64_t Ia, int64_t Ib, int num_sms);
+int64_t post_slow4_blocks(int64_t Ib);
+cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
+                              int splits, float* partial, unsigned* count, float* out,
+                              cudaStream_t st);
 cudaError_t launch_norm2(const void* X, int dtype, int64_t n, double* partial, int blocks,
                          double* out, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* in, uint16_t* out, int64_t n, cudaStream_t st);
