@@ -56,7 +56,7 @@ struct ntf_ctx {
   double* grams_tmp = nullptr;   // [N, R, R] for ntf_fit
   double* chol = nullptr;        // [N, R, R]
   double* sys = nullptr;         // per-factor H^{-1} (FP64, FP32) and H (FP32)
-  double* gram_part = nullptr;   // [update blocks, R, R] per-CTA Gram partial sums
+  double* gram_part = nullptr;   // [update blocks, R (R + 1) / 2] per-CTA Gram partials
   double* scal_part = nullptr;   // [update blocks, 8] per-CTA residual / fit partial sums
   double* fit_part = nullptr;    // [64]
   double* dpart = nullptr;       // [1024] misc FP64 partials

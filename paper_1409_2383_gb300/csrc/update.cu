@@ -26,7 +26,7 @@ constexpr int kScal = 8;      // scalar partials per CTA
 // The rows kernel reduces its own partials (in its last CTA) when there are at most this many
 // Gram partial entries to add; larger sets go to the separate multi-CTA reduction.
 constexpr int64_t kFusedReduceMax = 2048;
-constexpr int kRedEntries = 64;  // Gram entries per CTA of the separate reduction
+constexpr int kRedEntries = 32;  // packed Gram entries per CTA of the separate reduction
 
 // Per-mode system slot: H^{-1} in FP64, H^{-1} and H (without rho) in FP32.
 struct SysView {
@@ -52,7 +52,7 @@ struct UpdArgs {
   float* At;
   float* Y;
   Ctrl* ctrl;
-  double* gram_part;    // [blocks, R, R]
+  double* gram_part;    // [blocks, R (R + 1) / 2] packed lower triangles
   double* scal_part;    // [blocks, kScal]
   double* gram_out;     // [R, R] stored Gram of this factor
   int64_t I;
@@ -206,8 +206,143 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
 
 __device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
 
-// Rows.  Real = float (trace policy) or double.  One warp per row, lanes own elements lane
-// and lane + 32; v and f are broadcast through a per-warp shared buffer.
+// (r, s), r >= s, of packed lower-triangle entry e = r (r + 1) / 2 + s.
+__device__ __forceinline__ void tri_index(int e, int& r, int& s) {
+  int i = static_cast<int>((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > e) --i;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  r = i;
+  s = e - i * (i + 1) / 2;
+}
+
+// End of a rows CTA: the CTA's scalar partials (per-warp values part[] in registers) and its
+// share of the new Gram (packed lower triangle; FP64 accumulation of products of the stored
+// FP32 values, each exact in FP64) from frow [kRowWarps][ld] (zero for absent rows); then,
+// when the reduction is fused, the last CTA reduces.
+__device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
+
+__device__ __forceinline__ void rows_cta_tail(const UpdArgs& a, float (&part)[kScal],
+                                              const float* frow, int ld,
+                                              double (*red)[kScal]) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int R = a.R, T = R * (R + 1) / 2;
+#pragma unroll
+  for (int q = 0; q < kScal; ++q)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part[q] += __shfl_xor_sync(0xffffffffu, part[q], off);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < kScal; ++q) red[warp][q] = part[q];
+  __syncthreads();
+  if (tid < kScal) {
+    double sum = 0.0;
+    for (int w = 0; w < kRowWarps; ++w) sum += red[w][tid];
+    a.scal_part[blockIdx.x * kScal + tid] = sum;
+  }
+  double* gp = a.gram_part + static_cast<int64_t>(blockIdx.x) * T;
+  for (int e = tid; e < T; e += kRowThreads) {
+    int r, c;
+    tri_index(e, r, c);
+    double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRowWarps; w += 2) {
+      g0 = fma(static_cast<double>(frow[w * ld + r]), static_cast<double>(frow[w * ld + c]), g0);
+      g1 = fma(static_cast<double>(frow[(w + 1) * ld + r]),
+               static_cast<double>(frow[(w + 1) * ld + c]), g1);
+    }
+    gp[e] = g0 + g1;
+  }
+  if (!a.fused) return;
+  // the last CTA to finish sums every CTA's partials (fixed order, so the result does not
+  // depend on which CTA that is) and resets the counter for the next launch
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&a.ctrl->red_count[a.mode], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  update_reduce_cta(a, gridDim.x);
+  if (tid == 0) a.ctrl->red_count[a.mode] = 0;
+}
+
+// Rows for R <= 32.  Real = float (trace policy) or double.  One warp per row, lane j owns
+// element j and holds column j of H^{-1} (= row j: symmetric) in registers for the whole
+// update; x = H^{-1} v takes v_k from lane k by shuffles.
+template <typename Real>
+__global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
+  __shared__ float frow[kRowWarps][32];
+  __shared__ double red[kRowWarps][kScal];
+  if (a.ctrl->bad[a.mode]) return;  // uniform
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int R = a.R;
+  const bool h = lane < R;
+  const SysView sv = sys_view(a.sys, a.mode, R);
+  Real hc[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    Real v = 0;
+    if (k < R && h) {
+      if constexpr (sizeof(Real) == 4) v = __ldg(sv.hinv32 + k * R + lane);
+      else v = __ldg(sv.hinv64 + k * R + lane);
+    }
+    hc[k] = v;
+  }
+  const Real rho = static_cast<Real>(a.ctrl->stats[a.mode][5]);
+  const Real rinv = Real(1) / rho;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * kRowWarps + warp;
+  float part[kScal] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float f = 0.0f;
+  if (row < a.I) {
+    const int64_t idx = row * R + lane;
+    const Real m = h ? static_cast<Real>(a.M[idx]) : Real(0);
+    Real t = h ? static_cast<Real>(a.At[idx]) : Real(0);
+    Real y = h ? static_cast<Real>(a.Y[idx]) : Real(0);
+    const Real t_in = t;
+    Real x = 0;
+    for (int it = 0; it < a.inner; ++it) {
+      const Real v = m + rho * t - y;
+      Real p0 = 0, p1 = 0;
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        if (k < R) p0 = fma(hc[k], __shfl_sync(0xffffffffu, v, k), p0);
+        if (k + 1 < R) p1 = fma(hc[k + 1], __shfl_sync(0xffffffffu, v, k + 1), p1);
+      }
+      x = h ? p0 + p1 : Real(0);
+      const Real n = fmax(Real(0), x + y * rinv);
+      y += rho * (x - n);
+      t = n;
+    }
+    if (!h) x = t = y = 0;
+    const float fx = static_cast<float>(x), ft = static_cast<float>(t);
+    if (h) {
+      a.A[idx] = fx;
+      a.At[idx] = ft;
+      a.Y[idx] = static_cast<float>(y);
+    }
+    part[0] = static_cast<float>((x - t) * (x - t));
+    part[1] = static_cast<float>((t - t_in) * (t - t_in));
+    part[2] = static_cast<float>(x * x);
+    part[3] = static_cast<float>(t * t);
+    part[4] = static_cast<float>(y * y);
+    // the factor that feeds the next Khatri-Rao products, as stored (FP32)
+    f = a.kr_aux ? ft : fx;
+    if (a.want_fit) {
+      part[5] = static_cast<float>(m) * f;
+      float g = 0.0f;  // (G f)_j with the FP32 coefficient matrix
+      for (int k = 0; k < R; ++k) {
+        const float fk = __shfl_sync(0xffffffffu, f, k);
+        if (h) g = fmaf(__ldg(sv.h32 + k * R + lane), fk, g);
+      }
+      part[6] = f * g;
+    }
+  }
+  frow[warp][lane] = h ? f : 0.0f;
+  rows_cta_tail(a, part, &frow[0][0], 32, red);
+}
+
+// Rows for any R <= 64.  Real = float (trace policy) or double.  One warp per row, lanes own
+// elements lane and lane + 32; v and f are broadcast through a per-warp shared buffer.
 template <typename Real>
 __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
   extern __shared__ double shd[];
@@ -311,45 +446,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
     if (h0) fr[j0] = 0.0f;
     if (h1) fr[j1] = 0.0f;
   }
-#pragma unroll
-  for (int q = 0; q < kScal; ++q)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part[q] += __shfl_xor_sync(0xffffffffu, part[q], off);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < kScal; ++q) red[warp][q] = part[q];
-  __syncthreads();
-  if (tid < kScal) {
-    double s = 0.0;
-    for (int w = 0; w < kRowWarps; ++w) s += red[w][tid];
-    a.scal_part[blockIdx.x * kScal + tid] = s;
-  }
-  // this CTA's share of the new Gram: FP64 accumulation of products of the stored FP32
-  // values (a product of two FP32 numbers is exact in FP64)
-  double* gp = a.gram_part + static_cast<int64_t>(blockIdx.x) * RR;
-  for (int idx = tid; idx < RR; idx += kRowThreads) {
-    const int r = idx / R, s = idx % R;
-    double g0 = 0.0, g1 = 0.0;
-#pragma unroll
-    for (int w = 0; w < kRowWarps; w += 2) {
-      g0 = fma(static_cast<double>(frow[w * 64 + r]), static_cast<double>(frow[w * 64 + s]), g0);
-      g1 = fma(static_cast<double>(frow[(w + 1) * 64 + r]),
-               static_cast<double>(frow[(w + 1) * 64 + s]), g1);
-    }
-    gp[idx] = g0 + g1;
-  }
-  if (!a.fused) return;
-  // the last CTA to finish sums every CTA's partials (fixed order, so the result does not
-  // depend on which CTA that is) and resets the counter for the next launch
-  __shared__ int s_last;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = atomicAdd(&a.ctrl->red_count[a.mode], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  update_reduce_cta(a, gridDim.x);
-  if (tid == 0) a.ctrl->red_count[a.mode] = 0;
+  rows_cta_tail(a, part, frow, 64, red);
 }
 
 // Residual norms, penalty rule (Sec. III-D) and, for the last factor of a sweep, the fit,
@@ -385,26 +482,43 @@ __device__ void update_finalize(const UpdArgs& a, const double* sum) {
   if (!finite) atomicOr(&c->status, kStNonFinite);
 }
 
-// Gram entry e of the updated factor: the per-CTA partials summed over blocks in a fixed order,
-// read from L2 sixteen blocks at a time (the loads of a batch are independent, so they are in
-// flight together; consecutive threads read consecutive entries).
+// Packed Gram entry e of the updated factor: the per-CTA partials summed over blocks in a
+// fixed order, read from L2 sixteen blocks at a time (the loads of a batch are independent, so
+// they are in flight together; consecutive threads read consecutive entries).
 __device__ __forceinline__ double gram_entry_sum(const UpdArgs& a, int nblocks, int e) {
-  const int RR = a.R * a.R;
+  const int T = a.R * (a.R + 1) / 2;
   constexpr int kB = 16;
   double s = 0.0;
   int b = 0;
   for (; b + kB <= nblocks; b += kB) {
     double t[kB];
 #pragma unroll
-    for (int u = 0; u < kB; ++u) t[u] = __ldcg(a.gram_part + static_cast<int64_t>(b + u) * RR + e);
+    for (int u = 0; u < kB; ++u) t[u] = __ldcg(a.gram_part + static_cast<int64_t>(b + u) * T + e);
 #pragma unroll
     for (int w = kB / 2; w > 0; w >>= 1)
 #pragma unroll
       for (int u = 0; u < w; ++u) t[u] += t[u + w];
     s += t[0];
   }
-  for (; b < nblocks; ++b) s += __ldcg(a.gram_part + static_cast<int64_t>(b) * RR + e);
+  if (b < nblocks) {
+    double t[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u)
+      t[u] = b + u < nblocks ? __ldcg(a.gram_part + static_cast<int64_t>(b + u) * T + e) : 0.0;
+#pragma unroll
+    for (int w = kB / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) t[u] += t[u + w];
+    s += t[0];
+  }
   return s;
+}
+
+__device__ __forceinline__ void store_gram_entry(const UpdArgs& a, int e, double v) {
+  int r, c;
+  tri_index(e, r, c);
+  a.gram_out[r * a.R + c] = v;
+  a.gram_out[c * a.R + r] = v;
 }
 
 // Scalar partial q summed over blocks by one warp: lane l takes blocks l, l + 32, ... and the
@@ -420,8 +534,8 @@ __device__ __forceinline__ double scalar_sum(const UpdArgs& a, int nblocks, int 
 __device__ void update_reduce_cta(const UpdArgs& a, int nblocks) {
   __shared__ double s_sum[kScal];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int RR = a.R * a.R;
-  for (int e = tid; e < RR; e += blockDim.x) a.gram_out[e] = gram_entry_sum(a, nblocks, e);
+  const int T = a.R * (a.R + 1) / 2;
+  for (int e = tid; e < T; e += blockDim.x) store_gram_entry(a, e, gram_entry_sum(a, nblocks, e));
   for (int q = warp; q < kScal; q += blockDim.x / 32) {
     const double v = scalar_sum(a, nblocks, q, lane);
     if (lane == 0) s_sum[q] = v;
@@ -430,29 +544,16 @@ __device__ void update_reduce_cta(const UpdArgs& a, int nblocks) {
   if (tid == 0) update_finalize(a, s_sum);
 }
 
-// Separate reduction: CTAs 0..gridDim.x-2 sum 64 Gram entries each (4 threads per entry, each
-// over every 4th block, combined in a fixed order), the last CTA the scalars.
+// Separate reduction: CTAs 0..gridDim.x-2 sum kRedEntries packed Gram entries each (16
+// blocks' partials in flight per thread, fixed order), the last CTA the scalars.
 __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
   __shared__ double s_sum[kScal];
-  __shared__ double s_part[256];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.ctrl->bad[a.mode]) return;
-  const int RR = a.R * a.R;
+  const int T = a.R * (a.R + 1) / 2;
   if (blockIdx.x + 1 < gridDim.x) {
-    const int e = blockIdx.x * kRedEntries + tid / 4, part = tid % 4;
-    double s0 = 0.0, s1 = 0.0;
-    if (e < RR) {
-      int b = part;
-      for (; b + 4 < nblocks; b += 8) {
-        s0 += __ldcg(a.gram_part + static_cast<int64_t>(b) * RR + e);
-        s1 += __ldcg(a.gram_part + static_cast<int64_t>(b + 4) * RR + e);
-      }
-      if (b < nblocks) s0 += __ldcg(a.gram_part + static_cast<int64_t>(b) * RR + e);
-    }
-    s_part[tid] = s0 + s1;
-    __syncthreads();
-    if (part == 0 && e < RR)
-      a.gram_out[e] = (s_part[tid] + s_part[tid + 1]) + (s_part[tid + 2] + s_part[tid + 3]);
+    const int e = blockIdx.x * kRedEntries + tid;
+    if (tid < kRedEntries && e < T) store_gram_entry(a, e, gram_entry_sum(a, nblocks, e));
     return;
   }
   const double v = scalar_sum(a, nblocks, warp, lane);
@@ -520,6 +621,11 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
   const size_t RR = static_cast<size_t>(u.R) * u.R;
   const int nb = update_blocks(u.I);
   const bool fp32 = u.rho_policy == NTF_RHO_TRACE;
+  if (u.R <= 32) {
+    if (fp32) k_update_rows32<float><<<nb, kRowThreads, 0, st>>>(a);
+    else k_update_rows32<double><<<nb, kRowThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t real = fp32 ? 4 : 8;
   const size_t row_smem = ((RR * real + RR * 4 + 15) / 16) * 16 + kRowWarps * 64 * real +
                           kRowWarps * 64 * 4;
@@ -538,13 +644,13 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
 }
 
 bool update_fused(const UpdateCall& u) {
-  return static_cast<int64_t>(update_blocks(u.I)) * u.R * u.R <= kFusedReduceMax;
+  return static_cast<int64_t>(update_blocks(u.I)) * u.R * (u.R + 1) / 2 <= kFusedReduceMax;
 }
 
 cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st) {
   if (update_fused(u)) return cudaSuccess;  // done by the rows kernel
   const UpdArgs a = make_args(u);
-  const int gram_ctas = (u.R * u.R + kRedEntries - 1) / kRedEntries;
+  const int gram_ctas = (u.R * (u.R + 1) / 2 + kRedEntries - 1) / kRedEntries;
   k_update_reduce<<<gram_ctas + 1, 256, 0, st>>>(a, update_blocks(u.I));
   return cudaGetLastError();
 }
