@@ -473,10 +473,12 @@ def run_sweep_case(args):
         At = [a.clone() for a in A]
         Y = [torch.zeros_like(a) for a in A]
         with ntf.Context(Xd, RANK, p, stream=stream) as ctx:
+            ctx.trace_enable(args.trace)
             rs = ctx.run(A, At, Y, args.steps)
+            trace = ctx.trace_get() if args.trace else None
         stream.synchronize()
     print(json.dumps({"sweep_case": WORKLOAD, "storage": args.storage, "sweeps": args.steps,
-                      "rel_err": rs["rel_err"]}))
+                      "rel_err": rs["rel_err"], "trace_last_sweep": trace}))
 
 
 def main():
@@ -503,6 +505,8 @@ def main():
     ap.add_argument("--engine", default="auto", choices=["auto", "tensor", "simt"])
     ap.add_argument("--sweep-case", action="store_true",
                     help="run --steps outer iterations of the workload (for ncu launch lists)")
+    ap.add_argument("--trace", action="store_true",
+                    help="with --sweep-case: print the per-stream timeline of the last sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.kernel_case:

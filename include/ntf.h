@@ -193,6 +193,25 @@ typedef struct {
 ntf_status ntf_profile_enable(ntf_ctx* ctx, int enable);
 ntf_status ntf_profile_get(ntf_ctx* ctx, ntf_profile* out);
 
+/* Sweep trace.  With tracing on, every step of an outer iteration (first and second
+ * contraction, second tree level of each MTTKRP, warm start, rows, reductions, coefficient
+ * systems) is bracketed by CUDA events on the stream that runs it, inside the recorded CUDA
+ * graph as well.  ntf_trace_get (synchronizes) returns, for the last outer iteration of the
+ * last ntf_run, each step's start and end in microseconds from the start of that iteration,
+ * in enqueue order; *n_entries = the number of steps (at most max_entries are written).
+ * stream: 0 = the context's stream, 1 = the second-contraction stream, 2 = the side stream of
+ * the MTTKRP second levels and the first system.  mode: the factor the step serves. */
+typedef struct {
+  char name[24];
+  int stream;
+  int mode;
+  double start_us;
+  double end_us;
+} ntf_trace_entry;
+
+ntf_status ntf_trace_enable(ntf_ctx* ctx, int enable);
+ntf_status ntf_trace_get(ntf_ctx* ctx, ntf_trace_entry* out, int max_entries, int* n_entries);
+
 /* Synchronize the context's stream; return (and clear) a deferred device-side error. */
 ntf_status ntf_sync(ntf_ctx* ctx);
 

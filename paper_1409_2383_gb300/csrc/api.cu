@@ -50,7 +50,7 @@ struct ntf_ctx {
   cudaStream_t sB = nullptr, sC = nullptr;
   cudaEvent_t ev_start = nullptr, ev_tl = nullptr, ev_b = nullptr, ev_c = nullptr;
   cudaEvent_t ev_sys[ntf::kMaxOrder] = {}, ev_rows[ntf::kMaxOrder] = {},
-              ev_red[ntf::kMaxOrder] = {};
+              ev_red[ntf::kMaxOrder] = {}, ev_post[ntf::kMaxOrder] = {};
   float* Mbuf = nullptr;         // [max_dim, R]
   double* grams = nullptr;       // [N, R, R] stored Grams
   double* grams_tmp = nullptr;   // [N, R, R] for ntf_fit
@@ -72,9 +72,20 @@ struct ntf_ctx {
     const void* key[3 * ntf::kMaxOrder] = {};
     int launches = 0;            // kernels in the recorded sweep
     bool prof = false;           // whether it holds profiling events
+    bool trace = false;          // whether it holds trace events
     ntf_mlp* ws = nullptr;       // warm-start network recorded in it
   } graphs[2];
   bool swept_eagerly = false;    // one eager sweep has set every kernel attribute
+  // tracing: begin/end events of every step of the last enqueued sweep
+  static constexpr int kTraceMax = 48;
+  bool trace = false;
+  cudaEvent_t tr_origin = nullptr;
+  cudaEvent_t tr_ev[2 * kTraceMax] = {};
+  struct TraceInfo {
+    const char* name;
+    int stream, mode;
+  } tr_info[kTraceMax] = {};
+  int tr_n = 0;
   // profiling
   bool prof = false;
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -177,6 +188,30 @@ ntf_status prof_mark(ntf_ctx* c, int k, int which, cudaStream_t st) {
     NTF_CUDA(cudaEventRecord(c->ev[k][which], st));
   if (which == 1) c->ev_pending[k] = true;
   return NTF_OK;
+}
+
+// Record event `ev` on `st` (as a graph node of its own while the stream is captured).
+ntf_status record_any(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NTF_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusActive)
+    NTF_CUDA(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  else
+    NTF_CUDA(cudaEventRecord(ev, st));
+  return NTF_OK;
+}
+
+// Trace step bracket: returns the slot (or -1 when not tracing).
+int trace_begin(ntf_ctx* c, const char* name, int mode, int sid, cudaStream_t st) {
+  if (!c->trace || c->tr_n >= ntf_ctx::kTraceMax) return -1;
+  const int i = c->tr_n++;
+  c->tr_info[i] = {name, sid, mode};
+  if (record_any(c->tr_ev[2 * i], st) != NTF_OK) return -1;
+  return i;
+}
+ntf_status trace_end(ntf_ctx* c, int i, cudaStream_t st) {
+  if (i < 0) return NTF_OK;
+  return record_any(c->tr_ev[2 * i + 1], st);
 }
 
 // T_R[P_R, R] = X[P_R, Q_R] * KR(factors s_R..N-1), on stream st
@@ -335,44 +370,81 @@ ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float*
 }
 
 // One outer iteration in Gauss-Seidel order with two tensor passes.  Three streams: the main
-// stream A runs the first contraction and every factor's rows; B builds the first system and
-// then runs the second contraction as soon as the factors it needs are updated; C builds the
-// coefficient systems of the later factors as soon as their Grams are final.  The last
-// factor's update also forms the fit terms.
+// stream A runs the first contraction, every factor's rows and reductions; B builds the first
+// system and then runs the second contraction as soon as the factors it needs are updated; C
+// forms the next factor's MTTKRP from its contraction (second tree level) while A reduces the
+// current factor's update and, in the same kernel, builds the next factor's coefficient
+// system.  The last factor's update also forms the fit terms.
 ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* const* Y) {
   const float* const* src = c->prm.kr_source == NTF_KR_AUX ? At : A;
   cudaStream_t sa = c->st, sb = c->sB, sc = c->sC;
+  c->tr_n = 0;
+  if (c->trace) NTF_TRY(record_any(c->tr_origin, sa));
   NTF_CUDA(cudaEventRecord(c->ev_start, sa));
   NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_start, 0));
   NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_start, 0));
-  NTF_CUDA(ntf::launch_update_system(make_call(c, 0, c->Mbuf, A[0], At[0], Y[0], false), sb));
-  NTF_CUDA(cudaEventRecord(c->ev_sys[0], sb));
+  int t = trace_begin(c, "system", 0, 2, sc);
+  NTF_CUDA(ntf::launch_update_system(make_call(c, 0, c->Mbuf, A[0], At[0], Y[0], false), sc));
+  NTF_TRY(trace_end(c, t, sc));
+  NTF_CUDA(cudaEventRecord(c->ev_sys[0], sc));
   c->launches += 1;
   const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
+  t = trace_begin(c, "contract_right", 0, 0, sa);
   NTF_TRY(contract_right(c, src, const_cast<float*>(T), sa));
+  NTF_TRY(trace_end(c, t, sa));
+  t = trace_begin(c, "mttkrp_level2", 0, 0, sa);
+  NTF_TRY(finish_mode(c, 0, T, src, c->Mbuf, sa));
+  NTF_TRY(trace_end(c, t, sa));
+  NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_sys[0], 0));
   for (int m = 0; m < c->N; ++m) {
-    const bool left = m < c->s_R;
-    if (m == c->s_R) NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_tl, 0));
-    NTF_TRY(finish_mode(c, m, left ? T : c->TL, src, c->Mbuf, sa));
     const ntf::UpdateCall u = make_call(c, m, c->Mbuf, A[m], At[m], Y[m], m == c->N - 1);
-    NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_sys[m], 0));
-    NTF_TRY(warm_start(c, m, c->Mbuf, At[m], Y[m], sa));
+    const bool fused = ntf::update_fused(u);  // the rows kernel reduces by itself
+    if (m > 0) NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_post[m], 0));
+    if (c->ws && c->ws_now) {
+      t = trace_begin(c, "warm_start", m, 0, sa);
+      NTF_TRY(warm_start(c, m, c->Mbuf, At[m], Y[m], sa));
+      NTF_TRY(trace_end(c, t, sa));
+    }
+    t = trace_begin(c, "rows", m, 0, sa);
     NTF_CUDA(ntf::launch_update_rows(u, sa));
+    NTF_TRY(trace_end(c, t, sa));
     NTF_CUDA(cudaEventRecord(c->ev_rows[m], sa));
-    NTF_CUDA(ntf::launch_update_reduce(u, sa));
-    NTF_CUDA(cudaEventRecord(c->ev_red[m], sa));
+    c->launches += 1;
     if (m == c->s_L - 1) {
+      // B: the second contraction, as soon as factors 0..s_L-1 are updated (enqueued before
+      // any stream waits for it in this sweep)
       NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_rows[m], 0));
+      t = trace_begin(c, "contract_left", c->s_R, 1, sb);
       NTF_TRY(contract_left(c, src, c->TL, sb));
+      NTF_TRY(trace_end(c, t, sb));
       NTF_CUDA(cudaEventRecord(c->ev_tl, sb));
     }
     if (m + 1 < c->N) {
-      NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_red[m], 0));
-      NTF_CUDA(ntf::launch_update_system(
-          make_call(c, m + 1, c->Mbuf, A[m + 1], At[m + 1], Y[m + 1], false), sc));
-      NTF_CUDA(cudaEventRecord(c->ev_sys[m + 1], sc));
+      // A: this factor's reduction, then the next factor's coefficient system
+      const int n = m + 1;
+      const ntf::UpdateCall un = make_call(c, n, c->Mbuf, A[n], At[n], Y[n], false);
+      t = trace_begin(c, fused ? "system" : "reduce+system", n, 0, sa);
+      if (fused) NTF_CUDA(ntf::launch_update_system(un, sa));
+      else NTF_CUDA(ntf::launch_update_reduce_system(u, un, sa));
+      NTF_TRY(trace_end(c, t, sa));
+      c->launches += 1;
+    } else if (!fused) {
+      t = trace_begin(c, "reduce", m, 0, sa);
+      NTF_CUDA(ntf::launch_update_reduce(u, sa));
+      NTF_TRY(trace_end(c, t, sa));
+      c->launches += 1;
     }
-    c->launches += 1 + (ntf::update_fused(u) ? 0 : 1) + (m + 1 < c->N ? 1 : 0);
+    if (m + 1 < c->N) {
+      // C: the next factor's MTTKRP, next to A's reduction (needs factor m updated; the right
+      // group needs T_L, enqueued above in this or an earlier iteration of this sweep)
+      const int n = m + 1;
+      NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_rows[m], 0));
+      if (n >= c->s_R) NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_tl, 0));
+      t = trace_begin(c, "mttkrp_level2", n, 2, sc);
+      NTF_TRY(finish_mode(c, n, n < c->s_R ? T : c->TL, src, c->Mbuf, sc));
+      NTF_TRY(trace_end(c, t, sc));
+      NTF_CUDA(cudaEventRecord(c->ev_post[n], sc));
+    }
   }
   NTF_CUDA(cudaEventRecord(c->ev_b, sb));
   NTF_CUDA(cudaEventRecord(c->ev_c, sc));
@@ -388,13 +460,16 @@ void free_ctx(ntf_ctx* c) {
   for (cudaEvent_t e : {c->ev_start, c->ev_tl, c->ev_b, c->ev_c})
     if (e) cudaEventDestroy(e);
   for (int m = 0; m < ntf::kMaxOrder; ++m)
-    for (cudaEvent_t e : {c->ev_sys[m], c->ev_rows[m], c->ev_red[m]})
+    for (cudaEvent_t e : {c->ev_sys[m], c->ev_rows[m], c->ev_red[m], c->ev_post[m]})
       if (e) cudaEventDestroy(e);
   if (c->sB) cudaStreamDestroy(c->sB);
   if (c->sC) cudaStreamDestroy(c->sC);
   for (auto& pair : c->ev)
     for (auto& e : pair)
       if (e) cudaEventDestroy(e);
+  if (c->tr_origin) cudaEventDestroy(c->tr_origin);
+  for (cudaEvent_t e : c->tr_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->partial);
   cudaFree(c->post_count);
   cudaFree(c->TR);
@@ -573,6 +648,7 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     e = cudaEventCreateWithFlags(&c->ev_sys[m], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_rows[m], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red[m], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_post[m], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = alloc((void**)&c->Mbuf, c->max_dim * R * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->grams, order * RR * sizeof(double));
@@ -744,6 +820,39 @@ ntf_status ntf_profile_enable(ntf_ctx* c, int enable) {
   return NTF_OK;
 }
 
+ntf_status ntf_trace_enable(ntf_ctx* c, int enable) {
+  if (!c) return fail(NTF_ERR_INVALID_ARG, "null context");
+  if (enable) {
+    if (!c->tr_origin) NTF_CUDA(cudaEventCreate(&c->tr_origin));
+    for (cudaEvent_t& e : c->tr_ev)
+      if (!e) NTF_CUDA(cudaEventCreate(&e));
+  }
+  c->trace = enable != 0;
+  c->tr_n = 0;
+  return NTF_OK;
+}
+
+ntf_status ntf_trace_get(ntf_ctx* c, ntf_trace_entry* out, int max_entries, int* n_entries) {
+  if (!c || !n_entries || (max_entries > 0 && !out))
+    return fail(NTF_ERR_INVALID_ARG, "null argument");
+  *n_entries = c->tr_n;
+  if (c->tr_n == 0) return NTF_OK;
+  NTF_CUDA(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < c->tr_n && i < max_entries; ++i) {
+    float b = 0.0f, e = 0.0f;
+    NTF_CUDA(cudaEventElapsedTime(&b, c->tr_origin, c->tr_ev[2 * i]));
+    NTF_CUDA(cudaEventElapsedTime(&e, c->tr_origin, c->tr_ev[2 * i + 1]));
+    ntf_trace_entry& o = out[i];
+    std::memset(o.name, 0, sizeof o.name);
+    std::strncpy(o.name, c->tr_info[i].name, sizeof o.name - 1);
+    o.stream = c->tr_info[i].stream;
+    o.mode = c->tr_info[i].mode;
+    o.start_us = 1000.0 * b;
+    o.end_us = 1000.0 * e;
+  }
+  return NTF_OK;
+}
+
 ntf_status ntf_profile_get(ntf_ctx* c, ntf_profile* out) {
   if (!c || !out) return fail(NTF_ERR_INVALID_ARG, "null argument");
   NTF_TRY(read_ctrl(c));
@@ -804,7 +913,8 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
     c->ws_now = c->ws != nullptr && (c->ws_sweeps == 0 || it < c->ws_sweeps);
     ntf_mlp* const sweep_ws = c->ws_now ? c->ws : nullptr;
     ntf_ctx::SweepGraph& g = c->graphs[sweep_ws ? 1 : 0];
-    bool same = g.exec != nullptr && g.prof == c->prof && g.ws == sweep_ws;
+    bool same = g.exec != nullptr && g.prof == c->prof && g.trace == c->trace &&
+                g.ws == sweep_ws;
     for (int m = 0; m < c->N && same; ++m)
       same = g.key[3 * m] == A[m] && g.key[3 * m + 1] == At[m] && g.key[3 * m + 2] == Y[m];
     if (same) {
@@ -835,6 +945,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
         NTF_TRY(enqueue_sweep(c, A, At, Y));
       } else {
         g.prof = c->prof;
+        g.trace = c->trace;
         g.ws = sweep_ws;
         for (int m = 0; m < c->N; ++m) {
           g.key[3 * m] = A[m];

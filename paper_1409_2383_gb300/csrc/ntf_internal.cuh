@@ -41,6 +41,7 @@ struct Ctrl {
   int pad[3];
   unsigned long long ws_rows[2];  // warm start: rows considered, rows that took the prediction
   unsigned int red_count[kMaxOrder];  // CTAs of the running rows kernel that have finished
+  unsigned int sys_count;             // CTAs of the running reduce-and-system kernel finished
 };
 
 // ------------------------------------------------------------------ kernel launchers
@@ -156,6 +157,10 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st);
 // no-op when the rows kernel reduces its own partials (update_fused)
 cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st);
 bool update_fused(const UpdateCall& u);
+// reduction of u's factor, then (in its last CTA) the coefficient system of `next`'s factor;
+// only for !update_fused(u)
+cudaError_t launch_update_reduce_system(const UpdateCall& u, const UpdateCall& next,
+                                        cudaStream_t st);
 cudaError_t launch_update(const UpdateCall& u, cudaStream_t st);
 
 // mlp.cu: warm-start network (parameter layout, forward, backward, Adam) and its use

@@ -92,7 +92,12 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
   p->args.R = R;
   p->args.tiles = static_cast<int>(tiles);
   p->args.chunks = static_cast<int>(chunks);
-  p->grid = static_cast<int>(std::min<int64_t>(tiles * chunks, num_sms));
+  // Persistent CTAs, one per SM, but two SMs fewer than the GPU has: the sweep runs small
+  // kernels (coefficient systems, reductions) on other streams at the same time, and a CTA
+  // that cannot become resident until such a kernel leaves its SM would hold back its whole
+  // share of tiles.
+  const int64_t ctas = num_sms > 8 ? num_sms - 2 : num_sms;
+  p->grid = static_cast<int>(std::min<int64_t>(tiles * chunks, ctas));
   const CUtensorMapDataType t =
       f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const uint64_t pitch = static_cast<uint64_t>(Q) * es;

@@ -101,10 +101,10 @@ __device__ __forceinline__ double scale_pow2(double x, int e, double two_e) {
   return __longlong_as_double(bits + (static_cast<long long>(e) << 52));
 }
 
-template <int S>
-__global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
+template <int S, int NT>
+__device__ void system_body(const UpdArgs& a) {
   __shared__ double s_col[2][64];
-  __shared__ double s_red[kSysThreads / 32];
+  __shared__ double s_red[NT / 32];
   const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SysView sv = sys_view(a.sys, a.mode, R);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
   double tr = 0.0;
 #pragma unroll
   for (int q = 0; q < S; ++q) {
-    const int p = tid + kSysThreads * q;
+    const int p = tid + NT * q;
     int i = static_cast<int>((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
     while (i * (i + 1) / 2 > p) --i;
     while ((i + 1) * (i + 2) / 2 <= p) ++i;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
   if (a.rho_policy == NTF_RHO_TRACE) {
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < kSysThreads / 32; ++w) t += s_red[w];
+    for (int w = 0; w < NT / 32; ++w) t += s_red[w];
     rho = t / R;
   } else {
     rho = a.ctrl->rho[a.mode];
@@ -264,6 +264,11 @@ __device__ __forceinline__ void rows_cta_tail(const UpdArgs& a, float (&part)[kS
   __threadfence();
   update_reduce_cta(a, gridDim.x);
   if (tid == 0) a.ctrl->red_count[a.mode] = 0;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
+  system_body<S, kSysThreads>(a);
 }
 
 // Rows for R <= 32.  Real = float (trace policy) or double.  One warp per row, lane j owns
@@ -562,6 +567,38 @@ __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
   if (tid == 0) update_finalize(a, s_sum);
 }
 
+// The reduction of factor m's update (as k_update_reduce) followed, in the last of its CTAs
+// to finish, by the coefficient system of factor m + 1 (as k_update_system, 256 threads):
+// that system needs factor m's new Gram and nothing else of this sweep, so it runs without a
+// separate launch.  `as` describes factor m + 1.
+template <int S>
+__global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs as,
+                                                              int nblocks) {
+  __shared__ double s_sum[kScal];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int T = a.R * (a.R + 1) / 2;
+  if (!a.ctrl->bad[a.mode]) {  // uniform
+    if (blockIdx.x + 1 < gridDim.x) {
+      const int e = blockIdx.x * kRedEntries + tid;
+      if (tid < kRedEntries && e < T) store_gram_entry(a, e, gram_entry_sum(a, nblocks, e));
+    } else {
+      const double v = scalar_sum(a, nblocks, warp, lane);
+      if (lane == 0) s_sum[warp] = v;
+      __syncthreads();
+      if (tid == 0) update_finalize(a, s_sum);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&a.ctrl->sys_count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  system_body<S, 256>(as);
+  if (tid == 0) a.ctrl->sys_count = 0;
+}
+
 }  // namespace
 
 const float* update_sys_h32(const double* sys, int mode, int R) {
@@ -640,6 +677,20 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
     if (e == cudaSuccess) k_update_rows<double><<<nb, kRowThreads, row_smem, st>>>(a);
   }
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_reduce_system(const UpdateCall& u, const UpdateCall& next,
+                                        cudaStream_t st) {
+  const UpdArgs a = make_args(u), as = make_args(next);
+  const int gram_ctas = (u.R * (u.R + 1) / 2 + kRedEntries - 1) / kRedEntries;
+  const int T = u.R * (u.R + 1) / 2, nb = update_blocks(u.I);
+  const dim3 grid(gram_ctas + 1);
+  if (T <= 256) k_update_reduce_system<1><<<grid, 256, 0, st>>>(a, as, nb);
+  else if (T <= 512) k_update_reduce_system<2><<<grid, 256, 0, st>>>(a, as, nb);
+  else if (T <= 1024) k_update_reduce_system<4><<<grid, 256, 0, st>>>(a, as, nb);
+  else if (T <= 2304) k_update_reduce_system<9><<<grid, 256, 0, st>>>(a, as, nb);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

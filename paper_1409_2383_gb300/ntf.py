@@ -42,6 +42,11 @@ class Params(ctypes.Structure):
                 ("eps_rel", ctypes.c_double), ("contraction", ctypes.c_int)]
 
 
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("stream", ctypes.c_int), ("mode", ctypes.c_int),
+                ("start_us", ctypes.c_double), ("end_us", ctypes.c_double)]
+
+
 class UpdateStats(ctypes.Structure):
     _fields_ = [("primal_res", ctypes.c_double), ("dual_res", ctypes.c_double),
                 ("norm_A", ctypes.c_double), ("norm_At", ctypes.c_double),
@@ -98,6 +103,9 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_double), _P]),
     "ntf_mlp_last_error": (ctypes.c_char_p, []),
     "ntf_attach_warmstart": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "ntf_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ntf_trace_get": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int)]),
     "ntf_mttkrp_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.c_int,
                                           ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P), _P,
                                           _P]),
@@ -337,6 +345,20 @@ class Context:
                 "contraction_bytes": list(p.contraction_bytes),
                 "ws_rows_considered": p.ws_rows_considered,
                 "ws_rows_accepted": p.ws_rows_accepted}
+
+    def trace_enable(self, enable: bool = True) -> None:
+        _check(lib().ntf_trace_enable(self._h, 1 if enable else 0))
+
+    def trace_get(self) -> list:
+        """Steps of the last traced outer iteration: dicts with name, stream, mode and
+        start/end in microseconds from the iteration's start."""
+        buf = (TraceEntry * 64)()
+        n = ctypes.c_int(0)
+        _check(lib().ntf_trace_get(self._h, ctypes.cast(buf, ctypes.c_void_p), 64,
+                                   ctypes.byref(n)))
+        return [{"name": buf[i].name.decode(), "stream": buf[i].stream, "mode": buf[i].mode,
+                 "start_us": buf[i].start_us, "end_us": buf[i].end_us}
+                for i in range(min(n.value, 64))]
 
     def attach_warmstart(self, net: Optional["Mlp"], sweeps: int = 0) -> None:
         """sweeps >= 1: consult the network in the first `sweeps` outer iterations of each

@@ -62,6 +62,9 @@ SHAPES = [
     ((9, 10, 12, 8), 3),        # 4-way
     ((20, 24, 16, 50), 16),     # 4-way with the short fastest mode of the stress workload
     ((7, 5, 9, 11), 6),         # 4-way, unaligned
+    ((8, 40, 36), 8),           # vectorised second level with one split (short reduced range)
+    ((12, 16, 20, 24), 4),      # 4-way, vectorised second levels
+    ((200, 160, 40), 12),       # vectorised slow level with many splits and b-blocks
 ]
 
 
@@ -144,7 +147,11 @@ def test_system_reports_not_spd(ntf):
                                               ((64, 48, 40), 20, 5, "trace"),
                                               ((90, 30, 20), 50, 5, "trace"),
                                               ((33, 20, 10), 40, 3, "fixed"),
-                                              ((12, 10, 9, 8), 9, 2, "fixed")])
+                                              ((12, 10, 9, 8), 9, 2, "fixed"),
+                                              ((70, 36, 40), 32, 4, "trace"),   # widest 1-lane rows
+                                              ((70, 36, 40), 32, 4, "fixed"),   # same, FP64 rows
+                                              ((50, 44, 41), 33, 3, "trace"),   # first 2-lane rank
+                                              ((300, 20, 12), 1, 2, "fixed")])  # R = 1, many blocks
 def test_admm_update(ntf, dims, R, L, policy):
     X, fs = _problem(dims, R, seed=11, signed=True)
     rng = np.random.default_rng(5)
@@ -348,6 +355,37 @@ def test_profiling_under_graph_replay(ntf):
     torch.cuda.synchronize()
     want = o.mttkrp(X.astype(np.float64), [host(t).astype(np.float64) for t in At], 0)
     assert rel(host(M), want) <= TOL
+
+
+def test_trace_of_a_sweep(ntf):
+    """The trace of the last outer iteration lists every step once per factor, on the
+    documented streams, with start <= end, under graph replay; results are unchanged."""
+    dims, R = (64, 48, 40), 8
+    X, fs, init = synth.workload(dims, R, seed=4, snr_db=20.0)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    s = torch.cuda.Stream()
+    out = []
+    for trace in (False, True):
+        with torch.cuda.stream(s):
+            A = [cuda(F) for F in init]
+            At = [cuda(F) for F in init]
+            Y = [torch.zeros(d, R, device="cuda") for d in dims]
+            with ntf.Context(cuda(X), R, p, stream=s) as ctx:
+                ctx.trace_enable(trace)
+                ctx.run(A, At, Y, 4)
+                tr = ctx.trace_get()
+        torch.cuda.synchronize()
+        out.append([host(t) for t in At])
+        if trace:
+            names = [(e["name"], e["mode"]) for e in tr]
+            assert ("contract_right", 0) in names and ("contract_left", 2) in names
+            assert [e["mode"] for e in tr if e["name"] == "rows"] == [0, 1, 2]
+            assert all(0.0 <= e["start_us"] <= e["end_us"] for e in tr)
+            assert {e["stream"] for e in tr} == {0, 1, 2}
+        else:
+            assert tr == []
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
