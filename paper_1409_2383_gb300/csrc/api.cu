@@ -36,6 +36,7 @@ struct ntf_ctx {
   int post_split_left = 1, post_split_right = 1;
   int post4_split_left = 1, post4_split_right = 1;   // vectorised second level (R % 4 == 0)
   unsigned* post_count = nullptr;  // per-b-block counters of the vectorised slow level
+  unsigned* umma_sched = nullptr;  // [4] work counters of the two tensor-core contractions
   int64_t post_count_right = 0;    // offset of the right group's counters
   // workspace
   float* partial = nullptr;      // partial sums of the first contraction and of the posts
@@ -222,7 +223,7 @@ ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStr
     const int chunks = c->un.args.chunks;
     float* out = chunks > 1 ? c->partial : dst;
     NTF_TRY(prof_mark(c, 0, 0, st));
-    NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, st));
+    NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, c->umma_sched, st));
     NTF_TRY(prof_mark(c, 0, 1, st));
     c->launches += 2;
     if (chunks > 1) {
@@ -252,7 +253,7 @@ ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStre
     const int chunks = c->ut.args.chunks;
     float* out = chunks > 1 ? c->partial_b : dst;
     NTF_TRY(prof_mark(c, 1, 0, st));
-    NTF_CUDA(ntf::launch_umma(c->ut, out, &c->d_ctrl->status, st));
+    NTF_CUDA(ntf::launch_umma(c->ut, out, &c->d_ctrl->status, c->umma_sched + 2, st));
     NTF_TRY(prof_mark(c, 1, 1, st));
     c->launches += 2;
     if (chunks > 1) {
@@ -472,6 +473,7 @@ void free_ctx(ntf_ctx* c) {
     if (e) cudaEventDestroy(e);
   cudaFree(c->partial);
   cudaFree(c->post_count);
+  cudaFree(c->umma_sched);
   cudaFree(c->TR);
   cudaFree(c->TL);
   cudaFree(c->W);
@@ -637,6 +639,8 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   }
   if (e == cudaSuccess) e = alloc((void**)&c->partial, part * sizeof(float));
   if (e == cudaSuccess) e = alloc((void**)&c->post_count, (post_counts + 1) * sizeof(unsigned));
+  if (e == cudaSuccess) e = alloc((void**)&c->umma_sched, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->umma_sched, 0, 4 * sizeof(unsigned), c->st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->post_count, 0, (post_counts + 1) * sizeof(unsigned), c->st);
   if (e == cudaSuccess) e = alloc((void**)&c->partial_b, part_b * sizeof(float));

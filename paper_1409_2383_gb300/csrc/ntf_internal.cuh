@@ -99,6 +99,7 @@ struct Args {
   int chunks;         // K-chunks (> 1: out holds chunk partial sums [chunks][M][R])
   float* out;
   int* err;           // device status word: kStTimeout is or-ed in on a timeout
+  unsigned* sched;    // [2] work-item counter and finished-CTA counter (zero between launches)
 };
 }  // namespace umma
 
@@ -121,7 +122,10 @@ bool umma_plan(UmmaPlan* plan, bool transposed, int dtype, const void* X, int64_
 size_t umma_wsplit_bytes(int64_t K, int R, int dtype);
 cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* Wsplit,
                             cudaStream_t st);
-cudaError_t launch_umma(const UmmaPlan& plan, float* out, int* err, cudaStream_t st);
+// sched: 2 device counters owned by the caller, zero before the first launch (each launch
+// leaves them zero); launches sharing a counter pair must not overlap
+cudaError_t launch_umma(const UmmaPlan& plan, float* out, int* err, unsigned* sched,
+                        cudaStream_t st);
 
 // admm.cu
 cudaError_t launch_gram(const float* F, int64_t I, int R, double* G, cudaStream_t st);

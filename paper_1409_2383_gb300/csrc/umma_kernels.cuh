@@ -40,6 +40,7 @@ namespace ntf {
 namespace umma {
 
 constexpr int kTileM = 128;
+constexpr int kItemQ = 4;  // work-item slots between the producer and the other roles
 constexpr int kSmemBudget = 200 * 1024;
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -217,6 +218,8 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[S], ready[S], empty[S], tfull[2], tempty[2], drain;
+  __shared__ uint64_t ifull[kItemQ], iempty[kItemQ];
+  __shared__ int s_item[kItemQ];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -236,6 +239,10 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
       bar_init(&tempty[b], 4);
     }
     bar_init(&drain, 1);
+    for (int q = 0; q < kItemQ; ++q) {
+      bar_init(&ifull[q], 1);
+      bar_init(&iempty[q], kF32 ? 9 : 5);  // MMA thread, 4 epilogue (+ 4 converter) warps
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -257,6 +264,16 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
     }
   };
 
+  // Work items come from a global counter (dynamic scheduling: a CTA that shares its SM with
+  // another kernel takes fewer items).  The producer fetches them and hands them to the other
+  // roles through a small ring of item slots; every role sees the same sequence, ending with
+  // the sentinel `items`.
+  auto next_item = [&](uint32_t u, int& it) -> bool {  // consumers; false on timeout
+    const int q = u % kItemQ;
+    if (!bar_wait(&ifull[q], (u / kItemQ) & 1, abrt)) return false;
+    it = s_item[q];
+    return true;
+  };
   auto stage_ptr = [&](int slot) { return base + slot * C::kStageBytes; };
   // piece offsets within a stage
   constexpr int kOffA = 0, kOffLo = C::kABytes, kOffRaw = kOffLo + C::kLoBytes,
@@ -269,7 +286,18 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
       asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tw)) : "memory");
       uint32_t g = 0;
       bool ok = true;
-      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      for (uint32_t u = 0; ok; ++u) {
+        const int q = u % kItemQ;
+        if (!bar_wait(&iempty[q], ((u / kItemQ) & 1) ^ 1, abrt)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        int it = static_cast<int>(atomicAdd(a.sched, 1u));
+        if (it > items) it = items;
+        s_item[q] = it;
+        bar_arrive(&ifull[q]);
+        if (it >= items) break;
         const int tile = it % a.tiles, ch = it / a.tiles;
         const int64_t k0 = ch * a.chunk_len;
         const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
@@ -311,7 +339,15 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
       constexpr uint32_t kIdLo = idesc(2u, 0u, kN, kTileM);
       uint32_t g = 0, u = 0;
       bool ok = true, issued = false;
-      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      for (uint32_t v = 0; ok; ++v) {
+        int it;
+        if (!next_item(v, it)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        bar_arrive(&iempty[v % kItemQ]);
+        if (it >= items) break;
         const int ch = it / a.tiles;
         const int64_t k0 = ch * a.chunk_len;
         const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
@@ -368,7 +404,16 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
     // --------------------------------------------------------------------- epilogue
     uint32_t u = 0;
     bool ok = true;
-    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+    for (uint32_t w = 0; ok; ++w) {
+      int it = 0;
+      ok = __all_sync(0xffffffffu, next_item(w, it));
+      if (!ok) {
+        if (lane == 0) give_up();
+        break;
+      }
+      __syncwarp();
+      if (lane == 0) bar_arrive(&iempty[w % kItemQ]);
+      if (it >= items) break;
       const int tile = it % a.tiles, ch = it / a.tiles;
       const int64_t k0 = ch * a.chunk_len;
       const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
@@ -424,7 +469,16 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
     const int t = threadIdx.x - 6 * 32;  // 0..127
     uint32_t g = 0;
     bool ok = true;
-    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+    for (uint32_t w = 0; ok; ++w) {
+      int it = 0;
+      ok = __all_sync(0xffffffffu, next_item(w, it));
+      if (!ok) {
+        if (lane == 0) give_up();
+        break;
+      }
+      __syncwarp();
+      if (lane == 0) bar_arrive(&iempty[w % kItemQ]);
+      if (it >= items) break;
       const int ch = it / a.tiles;
       const int64_t k0 = ch * a.chunk_len;
       const int64_t k1 = a.K < k0 + a.chunk_len ? a.K : k0 + a.chunk_len;
@@ -484,6 +538,12 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"(C::kTmemCols));
+  }
+  // the last CTA to leave resets the item counter for the next launch (every producer has
+  // stopped fetching by then)
+  if (threadIdx.x == 0 && atomicAdd(a.sched + 1, 1u) == gridDim.x - 1) {
+    a.sched[0] = 0;
+    a.sched[1] = 0;
   }
 }
 
