@@ -242,6 +242,35 @@ def train_network(args):
     return net, rep
 
 
+def robustness(args, net, p):
+    """Outer iterations and time to the fit, plain BF16 vs BF16 + learned warm start, on other
+    tensors of the workload generator (drawn on the device): the iteration count to a fit
+    target depends on the path through the slow phase of the factorization, so one tensor
+    says little about the warm start."""
+    import torch
+    from paper_1409_2383_gb300 import ntf, warmstart
+    rows = []
+    for seed in range(100, 100 + args.robust_tensors):
+        X, init = warmstart.synthetic_tensor(DIMS, RANK, seed=seed, snr_db=SNR_DB)
+        A = [f.clone() for f in init]
+        T = [f.clone() for f in init]
+        Y = [torch.zeros_like(f) for f in init]
+        with ntf.Context(X, RANK, p) as c:
+            target = c.run(A, T, Y, MAX_OUTER, check_every=MAX_OUTER)["rel_err"] * (1 + FIT_TOL)
+        Xb = ntf.to_bf16(X)
+        pl = warmstart.time_to_fit(Xb, RANK, init, target, MAX_OUTER)
+        le = warmstart.time_to_fit(Xb, RANK, init, target, MAX_OUTER, net=net,
+                                   ws_sweeps=args.ws_sweeps)
+        rows.append({"seed": seed, "plain_iters": pl["iters"], "learned_iters": le["iters"],
+                     "plain_s": pl["seconds"], "learned_s": le["seconds"]})
+        del X, Xb
+    return {"tensors": rows,
+            "mean_plain_iters": statistics.mean(r["plain_iters"] for r in rows),
+            "mean_learned_iters": statistics.mean(r["learned_iters"] for r in rows),
+            "mean_plain_s": statistics.mean(r["plain_s"] for r in rows),
+            "mean_learned_s": statistics.mean(r["learned_s"] for r in rows)}
+
+
 def run_ntf(args):
     import torch
     world, rank, local = _dist()
@@ -356,6 +385,8 @@ def run_ntf(args):
                                                        ws_sweeps=args.ws_sweeps)
             variants[args.form] = {"seconds": ms / 1000.0, "iters": statistics.mean(iters),
                                    "rel_err": final_rfe}
+            if net is not None and args.robust_tensors > 0:
+                variants["learned_vs_plain_other_tensors"] = robustness(args, net, p)
             if "fp32" in variants:
                 variants["speedup_vs_fp32"] = variants["fp32"]["seconds"] / (ms / 1000.0)
         if net is not None:
@@ -495,6 +526,8 @@ def main():
                          "warm start")
     ap.add_argument("--train-rows", type=int, default=1_000_000)
     ap.add_argument("--train-epochs", type=float, default=20.0)
+    ap.add_argument("--robust-tensors", type=int, default=6,
+                    help="other tensors on which the learned warm start is compared with plain")
     ap.add_argument("--ws-sweeps", type=int, default=1,
                     help="outer iterations of each run in which the network is consulted")
     ap.add_argument("--kernel-case", action="store_true",
