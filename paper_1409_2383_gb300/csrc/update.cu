@@ -148,7 +148,10 @@ __device__ void system_body(const UpdArgs& a) {
   for (int q = 0; q < S; ++q)
     if (ii[q] >= 0 && ii[q] == jj[q]) v[q] += rho;
 
-  double c = 1.0;  // B = c A, the same value in every thread
+  // B = c A; c is kept in shared memory (double-buffered like the column) and advanced by
+  // the thread that owns the pivot, so that the other threads spend no FP64 work on it
+  __shared__ double s_c[2];
+  if (tid == 0) s_c[0] = 1.0;
   for (int k = 0; k < R && !fail; ++k) {
     const int b = k & 1;
 #pragma unroll
@@ -156,7 +159,7 @@ __device__ void system_body(const UpdArgs& a) {
       if (ii[q] == k) s_col[b][jj[q]] = v[q];
       else if (jj[q] == k) s_col[b][ii[q]] = v[q];
     }
-    __syncthreads();  // one barrier per step: the next step writes the other buffer
+    __syncthreads();  // one barrier per step: the next step writes the other buffers
     const double piv = s_col[b][k];
     const long long pbits = __double_as_longlong(piv);
     const int pex = static_cast<int>((pbits >> 52) & 0x7FF);
@@ -166,27 +169,35 @@ __device__ void system_body(const UpdArgs& a) {
     }
     const int e = 1023 - pex;  // piv 2^e in [1, 2)
     const double two_e = __longlong_as_double(static_cast<long long>(1023 + e) << 52);
+    const double c = s_c[b];
     const double g = scale_pow2(c, e, two_e);  // c 2^e
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       const int i = ii[q], j = jj[q];
       if (i < 0) continue;
       double x;
-      if (i == k && j == k) x = -c * g;
-      else if (i == k) x = g * s_col[b][j];
-      else if (j == k) x = g * s_col[b][i];
-      else x = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e, two_e);
+      if (i == k && j == k) {
+        x = -c * g;
+        s_c[b ^ 1] = scale_pow2(c * piv, e, two_e);  // c for the next step
+      } else if (i == k) {
+        x = g * s_col[b][j];
+      } else if (j == k) {
+        x = g * s_col[b][i];
+      } else {
+        x = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e, two_e);
+      }
       v[q] = x;
     }
-    c = scale_pow2(c * piv, e, two_e);
   }
-  if (fail) {
+  if (fail) {  // uniform
     if (tid == 0) {
       a.ctrl->bad[a.mode] = 1;
       atomicOr(&a.ctrl->status, kStNotSpd);
     }
     return;
   }
+  __syncthreads();  // the last pivot's owner has written the final c
+  const double c = s_c[R & 1];
   const double nic = -recip_newton(c);  // H^{-1} = -B / c
 #pragma unroll
   for (int q = 0; q < S; ++q) {
