@@ -107,6 +107,7 @@ struct UmmaPlan {
   bool on = false;
   bool transposed = false;  // GEMM-T (X^T W) rather than GEMM-N (X W)
   bool f32 = false;         // FP32 storage (TF32 split) rather than BF16
+  bool wres = false;        // BF16: whole split table resident in shared memory
   int N = 0;                // MMA N: R rounded up to a multiple of 16
   int splits = 0;           // parts of the W table (3 BF16 or 2 TF32)
   int grid = 0;             // persistent CTAs

@@ -110,6 +110,10 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
     ok = encode(&p->tx, t, X, Q, P, pitch, 128, 32, false);
   ok = ok && encode(&p->tw, t, Wsplit, p->K_pad, static_cast<uint64_t>(p->splits) * p->N,
                     p->K_pad * es, stage_k, p->splits * p->N, true);
+  // BF16 with N <= 32: keep the whole split table in shared memory when it has few enough
+  // 64-deep K blocks (8 for N = 16, 7 for N = 32)
+  const int64_t nks_all = (K + stage_k - 1) / stage_k;
+  p->wres = !f32 && ((p->N <= 16 && nks_all <= 8) || (p->N == 32 && nks_all <= 7));
   p->on = ok;
   return ok;
 }

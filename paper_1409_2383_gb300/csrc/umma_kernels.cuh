@@ -44,17 +44,26 @@ constexpr int kItemQ = 4;  // work-item slots between the producer and the other
 constexpr int kSmemBudget = 200 * 1024;
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
-template <bool kT, bool kF32, int kN>
+// kWRes (BF16 only): the whole split Khatri-Rao table of the contraction (at most kWBlocks
+// 64-deep K blocks) is loaded into shared memory once per CTA, and the stages carry the
+// tensor tile only -- more tensor bytes in flight and half the L2 -> SM traffic.
+template <bool kT, bool kF32, int kN, bool kWRes = false>
 struct Cfg {
+  static_assert(!(kWRes && kF32), "resident tables are for BF16 storage");
   static constexpr int kStageK = kF32 ? 32 : 64;   // K per stage: 128 bytes of one row
   static constexpr int kSplits = kF32 ? 2 : 3;     // W parts
   static constexpr int kABytes = kTileM * 128;     // operand tile (hi part for FP32)
   static constexpr int kLoBytes = kF32 ? kTileM * 128 : 0;
   static constexpr int kRawBytes = (kF32 && kT) ? kTileM * 128 : 0;  // untransposed X rows
-  static constexpr int kWBytes = kSplits * kN * 128;
+  static constexpr int kWBlockBytes = kSplits * kN * 128;            // W rows of one K block
+  static constexpr int kWBytes = kWRes ? 0 : kWBlockBytes;           // W per stage
+  static constexpr int kWBlocks = kWRes ? (kN <= 16 ? 8 : 7) : 0;    // resident K blocks
+  static constexpr int kWResBytes = kWBlocks * kWBlockBytes;
   static constexpr int kStageBytes = kABytes + kLoBytes + kRawBytes + kWBytes;
-  static constexpr int kStagesRaw = kSmemBudget / kStageBytes;
-  static constexpr int kStages = kStagesRaw > 6 ? 6 : kStagesRaw;
+  static constexpr int kStagesRaw =
+      ((kWRes ? 224 * 1024 : kSmemBudget) - kWResBytes) / kStageBytes;
+  static constexpr int kStagesMax = kWRes ? 8 : 6;
+  static constexpr int kStages = kStagesRaw > kStagesMax ? kStagesMax : kStagesRaw;
   static constexpr int kTxBytes = ((kF32 && kT) ? kRawBytes : kABytes) + kWBytes;
   static constexpr int kWarps = kF32 ? 10 : 6;
   static constexpr int kThreads = kWarps * 32;
@@ -68,9 +77,10 @@ struct Cfg {
   // error, ~2^-24 of the sum); capping the number of MMAs per accumulator caps that bias
   // at 32 main-block additions (~2e-6 relative), and the register sums round to nearest.
   static constexpr int kSegStages = 8;
-  static constexpr int kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack
+  static constexpr int kSmemBytes = kWResBytes + kStages * kStageBytes + 1024;  // + alignment
   static_assert(kStages >= 2, "stage does not fit");
   static_assert(kStageBytes % 1024 == 0, "stage pieces must stay 1024-byte aligned");
+  static_assert(kWBlockBytes % 1024 == 0, "W blocks must stay 1024-byte aligned");
   static_assert(kN % 16 == 0 && kN >= 16 && kN <= 64, "N must be 16..64 in steps of 16");
   static_assert(kTmemCols <= 512, "accumulators exceed the tensor memory");
 };
@@ -210,14 +220,14 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 }
 
 // ---------------------------------------------------------------------------- kernel
-template <bool kT, bool kF32, int kN>
-__global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
+template <bool kT, bool kF32, int kN, bool kWRes>
+__global__ void __launch_bounds__(Cfg<kT, kF32, kN, kWRes>::kThreads, 1)
     k_umma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw,
            Args a) {
-  using C = Cfg<kT, kF32, kN>;
+  using C = Cfg<kT, kF32, kN, kWRes>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full[S], ready[S], empty[S], tfull[2], tempty[2], drain;
+  __shared__ uint64_t full[S], ready[S], empty[S], tfull[2], tempty[2], drain, wfull;
   __shared__ uint64_t ifull[kItemQ], iempty[kItemQ];
   __shared__ int s_item[kItemQ];
   __shared__ uint32_t tmem_base;
@@ -227,6 +237,7 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
   const uint32_t base_s = (saddr(smem_raw) + 1023u) & ~1023u;
   uint8_t* base = smem_raw + (base_s - saddr(smem_raw));
   const int items = a.tiles * a.chunks;
+  const int nks_all = static_cast<int>((a.K + C::kStageK - 1) / C::kStageK);  // K blocks
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -239,6 +250,7 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
       bar_init(&tempty[b], 4);
     }
     bar_init(&drain, 1);
+    bar_init(&wfull, 1);
     for (int q = 0; q < kItemQ; ++q) {
       bar_init(&ifull[q], 1);
       bar_init(&iempty[q], kF32 ? 9 : 5);  // MMA thread, 4 epilogue (+ 4 converter) warps
@@ -274,7 +286,11 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
     it = s_item[q];
     return true;
   };
-  auto stage_ptr = [&](int slot) { return base + slot * C::kStageBytes; };
+  // shared memory: [resident W blocks (kWRes)] [stages]
+  uint8_t* const wres = base;
+  const uint32_t wres_s = base_s;
+  const uint32_t stages_s = base_s + C::kWResBytes;
+  auto stage_ptr = [&](int slot) { return base + C::kWResBytes + slot * C::kStageBytes; };
   // piece offsets within a stage
   constexpr int kOffA = 0, kOffLo = C::kABytes, kOffRaw = kOffLo + C::kLoBytes,
                 kOffW = kOffRaw + C::kRawBytes;
@@ -284,6 +300,11 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tx)) : "memory");
       asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tw)) : "memory");
+      if constexpr (kWRes) {  // the whole split table, once
+        bar_arrive_tx(&wfull, static_cast<uint32_t>(nks_all * C::kWBlockBytes));
+        for (int kb = 0; kb < nks_all; ++kb)
+          tma_2d(wres + kb * C::kWBlockBytes, &tw, kb * C::kStageK, 0, &wfull);
+      }
       uint32_t g = 0;
       bool ok = true;
       for (uint32_t u = 0; ok; ++u) {
@@ -321,13 +342,15 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
           } else {
             tma_2d(st + kOffRaw, &tx, m0, kx, &full[slot]);
           }
-          tma_2d(st + kOffW, &tw, kx, 0, &full[slot]);
+          if constexpr (!kWRes) tma_2d(st + kOffW, &tw, kx, 0, &full[slot]);
         }
       }
       // copies still in flight (only possible after a timeout) land before the CTA exits:
       // the last use of every slot has completed its phase
-      if (!ok)
+      if (!ok) {
         for (uint32_t h = g > S ? g - S : 0; h < g; ++h) bar_wait(&full[h % S], (h / S) & 1, nullptr);
+        if constexpr (kWRes) bar_wait(&wfull, 0, nullptr);
+      }
     }
   } else if (warp == 5) {
     // ------------------------------------------------------------------- MMA issuer
@@ -339,6 +362,12 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
       constexpr uint32_t kIdLo = idesc(2u, 0u, kN, kTileM);
       uint32_t g = 0, u = 0;
       bool ok = true, issued = false;
+      if constexpr (kWRes) {
+        if (!bar_wait(&wfull, 0, abrt)) {
+          give_up();
+          ok = false;
+        }
+      }
       for (uint32_t v = 0; ok; ++v) {
         int it;
         if (!next_item(v, it)) {
@@ -370,11 +399,15 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
               break;
             }
             fence_after();
-            const uint32_t st = base_s + slot * C::kStageBytes;
+            const uint32_t st = stages_s + slot * C::kStageBytes;
+            // W block of this stage: in the stage, or resident at its K-block index
+            const uint32_t wblk = kWRes ? wres_s + static_cast<uint32_t>(k0 / C::kStageK + ks) *
+                                                       C::kWBlockBytes
+                                        : st + kOffW;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const uint32_t acc = (ks != s0 || k != 0);
-              const uint64_t w = sdesc(st + kOffW + k * 32, 16, 1024);
+              const uint64_t w = sdesc(wblk + k * 32, 16, 1024);
               if constexpr (kF32) {
                 const uint64_t ah = sdesc(st + kOffA + k * 32, 16, 1024);
                 const uint64_t al = sdesc(st + kOffLo + k * 32, 16, 1024);
@@ -553,10 +586,10 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN>::kThreads, 1)
 namespace ntf {
 namespace umma {
 
-template <bool kT, bool kF32, int kN>
+template <bool kT, bool kF32, int kN, bool kWRes>
 cudaError_t run(const UmmaPlan& p, const Args& a, cudaStream_t st) {
-  using C = Cfg<kT, kF32, kN>;
-  auto kern = k_umma<kT, kF32, kN>;
+  using C = Cfg<kT, kF32, kN, kWRes>;
+  auto kern = k_umma<kT, kF32, kN, kWRes>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
@@ -564,17 +597,31 @@ cudaError_t run(const UmmaPlan& p, const Args& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// K blocks of the split table that fit in shared memory for the resident-table kernel
+inline int wres_blocks(int N) { return N <= 16 ? 8 : N <= 32 ? 7 : 0; }
+
 template <bool kF32>
 cudaError_t dispatch(const UmmaPlan& p, const Args& a, cudaStream_t st) {
+  if constexpr (!kF32) {
+    if (p.wres) {
+      switch (p.N * 2 + (p.transposed ? 1 : 0)) {
+        case 32: return run<false, false, 16, true>(p, a, st);
+        case 33: return run<true, false, 16, true>(p, a, st);
+        case 64: return run<false, false, 32, true>(p, a, st);
+        case 65: return run<true, false, 32, true>(p, a, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
   switch (p.N * 2 + (p.transposed ? 1 : 0)) {
-    case 32: return run<false, kF32, 16>(p, a, st);
-    case 33: return run<true, kF32, 16>(p, a, st);
-    case 64: return run<false, kF32, 32>(p, a, st);
-    case 65: return run<true, kF32, 32>(p, a, st);
-    case 96: return run<false, kF32, 48>(p, a, st);
-    case 97: return run<true, kF32, 48>(p, a, st);
-    case 128: return run<false, kF32, 64>(p, a, st);
-    case 129: return run<true, kF32, 64>(p, a, st);
+    case 32: return run<false, kF32, 16, false>(p, a, st);
+    case 33: return run<true, kF32, 16, false>(p, a, st);
+    case 64: return run<false, kF32, 32, false>(p, a, st);
+    case 65: return run<true, kF32, 32, false>(p, a, st);
+    case 96: return run<false, kF32, 48, false>(p, a, st);
+    case 97: return run<true, kF32, 48, false>(p, a, st);
+    case 128: return run<false, kF32, 64, false>(p, a, st);
+    case 129: return run<true, kF32, 64, false>(p, a, st);
     default: return cudaErrorInvalidValue;
   }
 }
