@@ -215,6 +215,19 @@ ntf_status ntf_trace_get(ntf_ctx* ctx, ntf_trace_entry* out, int max_entries, in
 /* Synchronize the context's stream; return (and clear) a deferred device-side error. */
 ntf_status ntf_sync(ntf_ctx* ctx);
 
+/* Failure detection.  Every device-side wait of the library's kernels (the mbarrier rings
+ * between the roles of the tensor-core contractions) is bounded: a wait that has not ended
+ * after 2 s sets the timeout bit of the context's device status word; the kernel's roles then
+ * leave their loops, wait (again bounded) for their copies in flight, free their tensor memory
+ * and return, and the next call that reads the status (ntf_sync, ntf_run, ntf_mttkrp, ...)
+ * returns NTF_ERR_TIMEOUT and clears it; the context stays usable.  ntf_watchdog_check runs
+ * that bounded wait on the context's stream on an mbarrier that nothing completes, with the
+ * limit limit_ms (0 < limit_ms <= 2000), and returns what ntf_sync then reports:
+ * NTF_ERR_TIMEOUT when the wait gave up as it must.  A status already pending before the
+ * call is returned first (and the check is not run); NTF_ERR_INVALID_ARG for a null context
+ * or a limit out of range. */
+ntf_status ntf_watchdog_check(ntf_ctx* ctx, double limit_ms);
+
 /* ---------------------------------------------------------------------------------------
  * Learned warm start (not in the paper; an addition evaluated against the plain method).
  * With the other factors fixed each row of a factor solves the non-negative least squares

@@ -887,6 +887,16 @@ ntf_status ntf_sync(ntf_ctx* c) {
   return take_status(c);
 }
 
+ntf_status ntf_watchdog_check(ntf_ctx* c, double limit_ms) {
+  if (!c) return fail(NTF_ERR_INVALID_ARG, "null context");
+  if (!(limit_ms > 0.0 && limit_ms <= 2000.0))
+    return fail(NTF_ERR_INVALID_ARG, "limit_ms must be in (0, 2000]");
+  NTF_TRY(ntf_sync(c));  // a status that was already pending is reported first
+  NTF_CUDA(ntf::launch_wait_check(&c->d_ctrl->status, static_cast<uint64_t>(limit_ms * 1e6),
+                                  c->st));
+  return ntf_sync(c);
+}
+
 ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* Y, int max_outer,
                    double target_rfe, int check_every, double* rfe_hist, ntf_run_stats* out) {
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's

@@ -127,6 +127,9 @@ cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* W
 // leaves them zero); launches sharing a counter pair must not overlap
 cudaError_t launch_umma(const UmmaPlan& plan, float* out, int* err, unsigned* sched,
                         cudaStream_t st);
+// The contractions' bounded mbarrier wait, on a barrier that nothing completes: ors
+// kStTimeout into *err after limit_ns.
+cudaError_t launch_wait_check(int* err, uint64_t limit_ns, cudaStream_t st);
 
 // admm.cu
 cudaError_t launch_gram(const float* F, int64_t I, int R, double* G, cudaStream_t st);

@@ -123,10 +123,11 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
-// Bounded wait for the phase of parity `parity` to complete; false on timeout or, when
+// Bounded wait for the phase of parity `parity` to complete; false after limit_ns or, when
 // abort_flag is given, once another role has given up.
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
-                                         volatile int* abort_flag) {
+                                         volatile int* abort_flag,
+                                         uint64_t limit_ns = kWaitNs) {
   uint64_t t0 = 0;
   for (uint32_t n = 0;; ++n) {
     if (bar_try(b, parity)) return true;
@@ -134,7 +135,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
     if ((n & 255u) == 0) {
       const uint64_t t = now_ns();
       if (n == 0) t0 = t;
-      else if (t - t0 > kWaitNs) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }

@@ -27,6 +27,7 @@ constexpr int kScal = 8;      // scalar partials per CTA
 // Gram partial entries to add; larger sets go to the separate multi-CTA reduction.
 constexpr int64_t kFusedReduceMax = 2048;
 constexpr int kRedEntries = 32;  // packed Gram entries per CTA of the separate reduction
+                                 // (256 threads, 8 per entry)
 
 // Per-mode system slot: H^{-1} in FP64, H^{-1} and H (without rho) in FP32.
 struct SysView {
@@ -80,30 +81,37 @@ __device__ __forceinline__ double recip_newton(double p) {
 //
 // Division-free form: the kernel holds B = c A for a tracked scalar c > 0 and applies the
 // sweep to B as
-//   b_ij -> 2^e (b_ij b_kk - b_ik b_kj),   b_ik -> c 2^e b_ik,   b_kk -> -c^2 2^e,
-//   c -> c b_kk 2^e,
+//   b_ij -> 2^e (b_ij b_kk - b_ik b_kj),   b_ik -> 2^e c b_ik,   b_kk -> -2^e c^2,
+//   c -> 2^e c b_kk,
 // with 2^e the power of two that brings b_kk into [1, 2) (exact scaling, so the entries stay
 // of the size of H); at the end H^{-1} = -B / c with the only reciprocal.  No reciprocal sits
-// on the per-step dependency chain, and each entry costs one FP64 multiply and one
-// multiply-add per step (FP64 runs at a small fraction of the FP32 rate on this GPU, so the
-// work is kept to that).  Only the lower triangle is kept, in registers (S packed entries per
-// thread); the pivot column is broadcast through shared memory (double-buffered, one barrier
-// per step).
-constexpr int kSysThreads = 128;
+// on the per-step dependency chain.  Every entry takes the same two FP64 instructions per
+// step, 2^e fma(-u_i, u_j, b_ij g), where u is column k of B with its pivot entry replaced by
+// zero and g = b_kk off row/column k, g = c on it: on row/column k one of u_i, u_j is that
+// zero, and the pivot's owner has replaced its entry by -c beforehand.  (FP64 runs at a small
+// fraction of the FP32 rate on this GPU, and a warp whose lanes took different branches
+// would issue each branch's FP64 instructions in turn, so operands are selected, not
+// branched on.)  Only the lower triangle is kept, in registers (S packed entries per thread);
+// u, b_kk and c are published through shared memory (double-buffered, one barrier per step).
+constexpr int kSysThreads = 256;
 
-// x 2^e: exact, on the integer exponent field when x and the result are normal numbers;
-// otherwise (zero, subnormal, NaN, infinity, leaving the normal range) by the multiply, which
-// keeps NaN and infinity what they are.
-__device__ __forceinline__ double scale_pow2(double x, int e, double two_e) {
-  const long long bits = __double_as_longlong(x);
-  const int ex = static_cast<int>((bits >> 52) & 0x7FF);
-  if (ex == 0 || ex == 0x7FF || ex + e <= 0 || ex + e >= 0x7FF) return x * two_e;
-  return __longlong_as_double(bits + (static_cast<long long>(e) << 52));
+// x 2^e for the scale factor of a pivot, e in [-1023, 1022]: exact, on the exponent field,
+// when x and the result are normal numbers; otherwise (zero, subnormal, NaN, infinity,
+// leaving the normal range) by scalbn, which keeps zero, NaN and infinity what they are.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7FF;
+  if (static_cast<unsigned>(ex - 1) < 0x7FEu && static_cast<unsigned>(ex + e - 1) < 0x7FEu)
+    return __hiloint2double(static_cast<int>(static_cast<unsigned>(hi) +
+                                             (static_cast<unsigned>(e) << 20)),
+                            __double2loint(x));
+  return scalbn(x, e);
 }
 
 template <int S, int NT>
 __device__ void system_body(const UpdArgs& a) {
-  __shared__ double s_col[2][64];
+  __shared__ double s_col[2][64];  // u: column k of B, zero at the pivot
+  __shared__ double s_piv[2], s_c[2];
   __shared__ double s_red[NT / 32];
   const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -122,9 +130,13 @@ __device__ void system_body(const UpdArgs& a) {
     jj[q] = p < T ? j : -1;
     double h = 0.0;
     if (p < T) {
-      h = 1.0;
-      for (int m = 0; m < a.N; ++m)
-        if (m != a.mode) h *= a.grams[m * RR + i * R + j];
+      double g[kMaxOrder];  // loads first, then the product
+#pragma unroll
+      for (int m = 0; m < kMaxOrder; ++m)
+        g[m] = m < a.N && m != a.mode ? a.grams[m * RR + i * R + j] : 1.0;
+      h = g[0];
+#pragma unroll
+      for (int m = 1; m < kMaxOrder; ++m) h *= g[m];
       sv.h32[i * R + j] = static_cast<float>(h);
       sv.h32[j * R + i] = static_cast<float>(h);
       if (i == j) tr += h;
@@ -148,45 +160,39 @@ __device__ void system_body(const UpdArgs& a) {
   for (int q = 0; q < S; ++q)
     if (ii[q] >= 0 && ii[q] == jj[q]) v[q] += rho;
 
-  // B = c A; c is kept in shared memory (double-buffered like the column) and advanced by
-  // the thread that owns the pivot, so that the other threads spend no FP64 work on it
-  __shared__ double s_c[2];
-  if (tid == 0) s_c[0] = 1.0;
+  double c = 1.0, piv = 1.0;  // c and b_kk of the current step (the same in every thread)
+  int e = 0;
   for (int k = 0; k < R && !fail; ++k) {
     const int b = k & 1;
 #pragma unroll
-    for (int q = 0; q < S; ++q) {  // publish column k of B
-      if (ii[q] == k) s_col[b][jj[q]] = v[q];
-      else if (jj[q] == k) s_col[b][ii[q]] = v[q];
+    for (int q = 0; q < S; ++q) {  // publish u (column k); the pivot's owner also b_kk, c
+      const int i = ii[q], j = jj[q];
+      if (i == k || j == k) {
+        const bool pivot = i == j;
+        s_col[b][i + j - k] = pivot ? 0.0 : v[q];
+        if (pivot) {
+          const double ck = k ? scale_pow2(c * piv, e) : 1.0;  // c after the previous step
+          s_piv[b] = v[q];
+          s_c[b] = ck;
+          v[q] = -ck;
+        }
+      }
     }
     __syncthreads();  // one barrier per step: the next step writes the other buffers
-    const double piv = s_col[b][k];
-    const long long pbits = __double_as_longlong(piv);
-    const int pex = static_cast<int>((pbits >> 52) & 0x7FF);
-    if (!(piv > 0.0) || pex == 0 || pex == 0x7FF) {  // not SPD (or not a normal number)
+    piv = s_piv[b];
+    c = s_c[b];
+    const int pex = __double2hiint(piv) >> 20;  // negative when the sign bit is set
+    if (static_cast<unsigned>(pex - 1) >= 0x7FEu) {  // not SPD (or not a normal number)
       fail = true;  // the same shared value in every thread: a uniform exit
       break;
     }
-    const int e = 1023 - pex;  // piv 2^e in [1, 2)
-    const double two_e = __longlong_as_double(static_cast<long long>(1023 + e) << 52);
-    const double c = s_c[b];
-    const double g = scale_pow2(c, e, two_e);  // c 2^e
+    e = 1023 - pex;  // b_kk 2^e in [1, 2)
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       const int i = ii[q], j = jj[q];
       if (i < 0) continue;
-      double x;
-      if (i == k && j == k) {
-        x = -c * g;
-        s_c[b ^ 1] = scale_pow2(c * piv, e, two_e);  // c for the next step
-      } else if (i == k) {
-        x = g * s_col[b][j];
-      } else if (j == k) {
-        x = g * s_col[b][i];
-      } else {
-        x = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e, two_e);
-      }
-      v[q] = x;
+      const double g = i == k || j == k ? c : piv;
+      v[q] = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * g), e);
     }
   }
   if (fail) {  // uniform
@@ -196,9 +202,7 @@ __device__ void system_body(const UpdArgs& a) {
     }
     return;
   }
-  __syncthreads();  // the last pivot's owner has written the final c
-  const double c = s_c[R & 1];
-  const double nic = -recip_newton(c);  // H^{-1} = -B / c
+  const double nic = -recip_newton(scale_pow2(c * piv, e));  // H^{-1} = -B / c
 #pragma unroll
   for (int q = 0; q < S; ++q) {
     const int i = ii[q], j = jj[q];
@@ -228,12 +232,14 @@ __device__ __forceinline__ void tri_index(int e, int& r, int& s) {
 
 // End of a rows CTA: the CTA's scalar partials (per-warp values part[] in registers) and its
 // share of the new Gram (packed lower triangle; FP64 accumulation of products of the stored
-// FP32 values, each exact in FP64) from frow [kRowWarps][ld] (zero for absent rows); then,
-// when the reduction is fused, the last CTA reduces.
+// FP32 values, each exact in FP64) from frow [kRowWarps][ld] (zero for absent rows; FP64
+// copies of the FP32 values, or the FP32 values themselves); then, when the reduction is
+// fused, the last CTA reduces.
 __device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
 
+template <typename F>
 __device__ __forceinline__ void rows_cta_tail(const UpdArgs& a, float (&part)[kScal],
-                                              const float* frow, int ld,
+                                              const F* frow, int ld,
                                               double (*red)[kScal]) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R = a.R, T = R * (R + 1) / 2;
@@ -284,19 +290,22 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
 
 // Rows for R <= 32.  Real = float (trace policy) or double.  One warp per row, lane j owns
 // element j and holds column j of H^{-1} (= row j: symmetric) in registers for the whole
-// update; x = H^{-1} v takes v_k from lane k by shuffles.
-template <typename Real>
+// update; x = H^{-1} v takes v_k from lane k by shuffles.  kR = R rounded up to a multiple of
+// 4 fixes the loop lengths at compile time (the padding lanes and columns hold zeros).
+template <typename Real, int kR>
 __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
-  __shared__ float frow[kRowWarps][32];
+  __shared__ double frow[kRowWarps][32];  // FP64 copies: one conversion per element
   __shared__ double red[kRowWarps][kScal];
-  if (a.ctrl->bad[a.mode]) return;  // uniform
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R = a.R;
   const bool h = lane < R;
   const SysView sv = sys_view(a.sys, a.mode, R);
-  Real hc[32];
+  // every load is issued before the status test, so that their latencies overlap (the
+  // system slot and the rows are valid memory either way)
+  const int bad = a.ctrl->bad[a.mode];
+  Real hc[kR];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
+  for (int k = 0; k < kR; ++k) {
     Real v = 0;
     if (k < R && h) {
       if constexpr (sizeof(Real) == 4) v = __ldg(sv.hinv32 + k * R + lane);
@@ -305,26 +314,30 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
     hc[k] = v;
   }
   const Real rho = static_cast<Real>(a.ctrl->stats[a.mode][5]);
-  const Real rinv = Real(1) / rho;
   const int64_t row = static_cast<int64_t>(blockIdx.x) * kRowWarps + warp;
+  const bool live = row < a.I && h;
+  const int64_t idx = row * R + lane;
+  const Real m = live ? static_cast<Real>(a.M[idx]) : Real(0);
+  Real t = live ? static_cast<Real>(a.At[idx]) : Real(0);
+  Real y = live ? static_cast<Real>(a.Y[idx]) : Real(0);
+  if (bad) return;  // uniform: the system of this factor failed; the state is kept
+  const Real rinv = Real(1) / rho;
   float part[kScal] = {0, 0, 0, 0, 0, 0, 0, 0};
   float f = 0.0f;
   if (row < a.I) {
-    const int64_t idx = row * R + lane;
-    const Real m = h ? static_cast<Real>(a.M[idx]) : Real(0);
-    Real t = h ? static_cast<Real>(a.At[idx]) : Real(0);
-    Real y = h ? static_cast<Real>(a.Y[idx]) : Real(0);
     const Real t_in = t;
     Real x = 0;
     for (int it = 0; it < a.inner; ++it) {
-      const Real v = m + rho * t - y;
-      Real p0 = 0, p1 = 0;
+      const Real v = m + rho * t - y;  // zero in the padding lanes
+      Real p0 = 0, p1 = 0, p2 = 0, p3 = 0;
 #pragma unroll
-      for (int k = 0; k < 32; k += 2) {
-        if (k < R) p0 = fma(hc[k], __shfl_sync(0xffffffffu, v, k), p0);
-        if (k + 1 < R) p1 = fma(hc[k + 1], __shfl_sync(0xffffffffu, v, k + 1), p1);
+      for (int k = 0; k < kR; k += 4) {
+        p0 = fma(hc[k], __shfl_sync(0xffffffffu, v, k), p0);
+        p1 = fma(hc[k + 1], __shfl_sync(0xffffffffu, v, k + 1), p1);
+        p2 = fma(hc[k + 2], __shfl_sync(0xffffffffu, v, k + 2), p2);
+        p3 = fma(hc[k + 3], __shfl_sync(0xffffffffu, v, k + 3), p3);
       }
-      x = h ? p0 + p1 : Real(0);
+      x = h ? (p0 + p1) + (p2 + p3) : Real(0);
       const Real n = fmax(Real(0), x + y * rinv);
       y += rho * (x - n);
       t = n;
@@ -346,14 +359,15 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
     if (a.want_fit) {
       part[5] = static_cast<float>(m) * f;
       float g = 0.0f;  // (G f)_j with the FP32 coefficient matrix
-      for (int k = 0; k < R; ++k) {
+#pragma unroll
+      for (int k = 0; k < kR; ++k) {
         const float fk = __shfl_sync(0xffffffffu, f, k);
-        if (h) g = fmaf(__ldg(sv.h32 + k * R + lane), fk, g);
+        if (k < R && h) g = fmaf(__ldg(sv.h32 + k * R + lane), fk, g);
       }
       part[6] = f * g;
     }
   }
-  frow[warp][lane] = h ? f : 0.0f;
+  frow[warp][lane] = h ? static_cast<double>(f) : 0.0;
   rows_cta_tail(a, part, &frow[0][0], 32, red);
 }
 
@@ -530,6 +544,33 @@ __device__ __forceinline__ double gram_entry_sum(const UpdArgs& a, int nblocks, 
   return s;
 }
 
+// The same sum by the 8 lanes of a group (lanes 8g .. 8g+7 of a warp, called by the whole
+// warp): lane s of the group takes blocks s, s + 8, ... (eight loads in flight per batch), and
+// a fixed butterfly over the group gives every lane of it the same sum.  Entries e >= T read
+// nothing and sum to zero.
+__device__ __forceinline__ double gram_entry_sum8(const UpdArgs& a, int nblocks, int e, int s) {
+  const int T = a.R * (a.R + 1) / 2;
+  constexpr int kB = 8;
+  double acc = 0.0;
+  for (int b0 = s; b0 < nblocks; b0 += 8 * kB) {
+    double t[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int b = b0 + 8 * u;
+      t[u] = b < nblocks && e < T ? __ldcg(a.gram_part + static_cast<int64_t>(b) * T + e) : 0.0;
+    }
+#pragma unroll
+    for (int w = kB / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) t[u] += t[u + w];
+    acc += t[0];
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  return acc;
+}
+
 __device__ __forceinline__ void store_gram_entry(const UpdArgs& a, int e, double v) {
   int r, c;
   tri_index(e, r, c);
@@ -560,16 +601,17 @@ __device__ void update_reduce_cta(const UpdArgs& a, int nblocks) {
   if (tid == 0) update_finalize(a, s_sum);
 }
 
-// Separate reduction: CTAs 0..gridDim.x-2 sum kRedEntries packed Gram entries each (16
-// blocks' partials in flight per thread, fixed order), the last CTA the scalars.
+// Separate reduction: CTAs 0..gridDim.x-2 sum kRedEntries packed Gram entries each (8 lanes
+// per entry, fixed order), the last CTA the scalars.
 __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
   __shared__ double s_sum[kScal];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.ctrl->bad[a.mode]) return;
   const int T = a.R * (a.R + 1) / 2;
   if (blockIdx.x + 1 < gridDim.x) {
-    const int e = blockIdx.x * kRedEntries + tid;
-    if (tid < kRedEntries && e < T) store_gram_entry(a, e, gram_entry_sum(a, nblocks, e));
+    const int e = blockIdx.x * kRedEntries + (tid >> 3);
+    const double v = gram_entry_sum8(a, nblocks, e, tid & 7);
+    if ((tid & 7) == 0 && e < T) store_gram_entry(a, e, v);
     return;
   }
   const double v = scalar_sum(a, nblocks, warp, lane);
@@ -591,8 +633,9 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
   const int T = a.R * (a.R + 1) / 2;
   if (!a.ctrl->bad[a.mode]) {  // uniform
     if (blockIdx.x + 1 < gridDim.x) {
-      const int e = blockIdx.x * kRedEntries + tid;
-      if (tid < kRedEntries && e < T) store_gram_entry(a, e, gram_entry_sum(a, nblocks, e));
+      const int e = blockIdx.x * kRedEntries + (tid >> 3);
+      const double v = gram_entry_sum8(a, nblocks, e, tid & 7);
+      if ((tid & 7) == 0 && e < T) store_gram_entry(a, e, v);
     } else {
       const double v = scalar_sum(a, nblocks, warp, lane);
       if (lane == 0) s_sum[warp] = v;
@@ -658,8 +701,7 @@ cudaError_t launch_update_system(const UpdateCall& u, cudaStream_t st) {
   if (T <= 1 * kSysThreads) k_update_system<1><<<1, kSysThreads, 0, st>>>(a);
   else if (T <= 2 * kSysThreads) k_update_system<2><<<1, kSysThreads, 0, st>>>(a);
   else if (T <= 4 * kSysThreads) k_update_system<4><<<1, kSysThreads, 0, st>>>(a);
-  else if (T <= 8 * kSysThreads) k_update_system<8><<<1, kSysThreads, 0, st>>>(a);
-  else if (T <= 17 * kSysThreads) k_update_system<17><<<1, kSysThreads, 0, st>>>(a);
+  else if (T <= 9 * kSysThreads) k_update_system<9><<<1, kSysThreads, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -670,8 +712,17 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
   const int nb = update_blocks(u.I);
   const bool fp32 = u.rho_policy == NTF_RHO_TRACE;
   if (u.R <= 32) {
-    if (fp32) k_update_rows32<float><<<nb, kRowThreads, 0, st>>>(a);
-    else k_update_rows32<double><<<nb, kRowThreads, 0, st>>>(a);
+    switch ((u.R + 3) / 4) {
+#define NTF_ROWS32(q)                                                       \
+  case q:                                                                   \
+    if (fp32) k_update_rows32<float, 4 * q><<<nb, kRowThreads, 0, st>>>(a); \
+    else k_update_rows32<double, 4 * q><<<nb, kRowThreads, 0, st>>>(a);     \
+    break;
+      NTF_ROWS32(1) NTF_ROWS32(2) NTF_ROWS32(3) NTF_ROWS32(4)
+      NTF_ROWS32(5) NTF_ROWS32(6) NTF_ROWS32(7) NTF_ROWS32(8)
+#undef NTF_ROWS32
+      default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
   }
   const size_t real = fp32 ? 4 : 8;

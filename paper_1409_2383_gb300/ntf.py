@@ -89,6 +89,7 @@ _SIGS = {
                                ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(RunStats)]),
     "ntf_sync": (ctypes.c_int, [_P]),
+    "ntf_watchdog_check": (ctypes.c_int, [_P, ctypes.c_double]),
     "ntf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ntf_profile_get": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "ntf_to_bf16": (ctypes.c_int, [_P, _P, _I64, _P]),
@@ -333,6 +334,11 @@ class Context:
 
     def sync(self) -> None:
         _check(lib().ntf_sync(self._h))
+
+    def watchdog_check(self, limit_ms: float) -> None:
+        """Runs the bounded device-side wait on a barrier that nothing completes; raises
+        NTFError (NTF_ERR_TIMEOUT) when it gave up, as it must."""
+        _check(lib().ntf_watchdog_check(self._h, float(limit_ms)))
 
     def profile_enable(self, enable: bool = True) -> None:
         _check(lib().ntf_profile_enable(self._h, 1 if enable else 0))

@@ -68,6 +68,7 @@ def test_create_rejects_bad_params(lib):
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.ntf_destroy(None) == 0
     assert lib.ntf_sync(None) == 1
+    assert lib.ntf_watchdog_check(None, ctypes.c_double(10.0)) == 1
     assert lib.ntf_mttkrp(None, 0, None, None) == 1
     assert lib.ntf_to_bf16(None, None, 4, None) == 1
     assert lib.ntf_status_string(4) == b"coefficient matrix not positive definite"
