@@ -370,12 +370,41 @@ ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float*
   return NTF_OK;
 }
 
-// One outer iteration in Gauss-Seidel order with two tensor passes.  Three streams: the main
-// stream A runs the first contraction, every factor's rows and reductions; B builds the first
-// system and then runs the second contraction as soon as the factors it needs are updated; C
-// forms the next factor's MTTKRP from its contraction (second tree level) while A reduces the
-// current factor's update and, in the same kernel, builds the next factor's coefficient
-// system.  The last factor's update also forms the fit terms.
+// Factor 0's MTTKRP: the first contraction (T_R) and its second tree level, on stream st.
+ntf_status enqueue_lead(ntf_ctx* c, const float* const* src, cudaStream_t st, int sid) {
+  const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
+  int t = trace_begin(c, "contract_right", 0, sid, st);
+  NTF_TRY(contract_right(c, src, const_cast<float*>(T), st));
+  NTF_TRY(trace_end(c, t, st));
+  t = trace_begin(c, "mttkrp_level2", 0, sid, st);
+  NTF_TRY(finish_mode(c, 0, T, src, c->Mbuf, st));
+  NTF_TRY(trace_end(c, t, st));
+  return NTF_OK;
+}
+
+// What every sweep expects at its start: factor 0's coefficient system and MTTKRP (the system
+// on the side stream next to the contraction).  Each sweep leaves the same for the next one.
+ntf_status enqueue_prologue(ntf_ctx* c, float* const* A, float* const* At, float* const* Y) {
+  const float* const* src = c->prm.kr_source == NTF_KR_AUX ? At : A;
+  cudaStream_t sa = c->st, sc = c->sC;
+  NTF_CUDA(cudaEventRecord(c->ev_start, sa));
+  NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_start, 0));
+  NTF_CUDA(ntf::launch_update_system(make_call(c, 0, c->Mbuf, A[0], At[0], Y[0], false), sc));
+  NTF_CUDA(cudaEventRecord(c->ev_sys[0], sc));
+  c->launches += 1;
+  NTF_TRY(enqueue_lead(c, src, sa, 0));
+  NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_sys[0], 0));
+  return NTF_OK;
+}
+
+// One outer iteration in Gauss-Seidel order with two tensor passes, from factor 0's system
+// and MTTKRP (left by the prologue or the previous sweep).  Three streams: the main stream A
+// runs every factor's rows, reductions and coefficient systems; B runs the second
+// contraction as soon as the factors it needs are updated and, after the last factor's rows,
+// the next sweep's first contraction and factor 0's MTTKRP; C forms the next factor's MTTKRP
+// from its contraction (second tree level) while A reduces the current factor's update and,
+// in the same kernel, builds the next factor's coefficient system (after the last factor:
+// factor 0's, for the next sweep).  The last factor's update also forms the fit terms.
 ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* const* Y) {
   const float* const* src = c->prm.kr_source == NTF_KR_AUX ? At : A;
   cudaStream_t sa = c->st, sb = c->sB, sc = c->sC;
@@ -384,19 +413,8 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
   NTF_CUDA(cudaEventRecord(c->ev_start, sa));
   NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_start, 0));
   NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_start, 0));
-  int t = trace_begin(c, "system", 0, 2, sc);
-  NTF_CUDA(ntf::launch_update_system(make_call(c, 0, c->Mbuf, A[0], At[0], Y[0], false), sc));
-  NTF_TRY(trace_end(c, t, sc));
-  NTF_CUDA(cudaEventRecord(c->ev_sys[0], sc));
-  c->launches += 1;
   const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
-  t = trace_begin(c, "contract_right", 0, 0, sa);
-  NTF_TRY(contract_right(c, src, const_cast<float*>(T), sa));
-  NTF_TRY(trace_end(c, t, sa));
-  t = trace_begin(c, "mttkrp_level2", 0, 0, sa);
-  NTF_TRY(finish_mode(c, 0, T, src, c->Mbuf, sa));
-  NTF_TRY(trace_end(c, t, sa));
-  NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_sys[0], 0));
+  int t = -1;
   for (int m = 0; m < c->N; ++m) {
     const ntf::UpdateCall u = make_call(c, m, c->Mbuf, A[m], At[m], Y[m], m == c->N - 1);
     const bool fused = ntf::update_fused(u);  // the rows kernel reduces by itself
@@ -420,25 +438,24 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
       NTF_TRY(trace_end(c, t, sb));
       NTF_CUDA(cudaEventRecord(c->ev_tl, sb));
     }
-    if (m + 1 < c->N) {
-      // A: this factor's reduction, then the next factor's coefficient system
-      const int n = m + 1;
-      const ntf::UpdateCall un = make_call(c, n, c->Mbuf, A[n], At[n], Y[n], false);
-      t = trace_begin(c, fused ? "system" : "reduce+system", n, 0, sa);
-      if (fused) NTF_CUDA(ntf::launch_update_system(un, sa));
-      else NTF_CUDA(ntf::launch_update_reduce_system(u, un, sa));
-      NTF_TRY(trace_end(c, t, sa));
-      c->launches += 1;
-    } else if (!fused) {
-      t = trace_begin(c, "reduce", m, 0, sa);
-      NTF_CUDA(ntf::launch_update_reduce(u, sa));
-      NTF_TRY(trace_end(c, t, sa));
-      c->launches += 1;
+    if (m + 1 == c->N) {
+      // B: the next sweep's factor-0 MTTKRP (needs the last factor updated; T_R and the
+      // MTTKRP buffer are free once this factor's rows have run)
+      NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_rows[m], 0));
+      NTF_TRY(enqueue_lead(c, src, sb, 1));
     }
+    // A: this factor's reduction, then the next factor's coefficient system (after the last
+    // factor, factor 0's for the next sweep)
+    const int n = m + 1 < c->N ? m + 1 : 0;
+    const ntf::UpdateCall un = make_call(c, n, c->Mbuf, A[n], At[n], Y[n], false);
+    t = trace_begin(c, fused ? "system" : "reduce+system", n, 0, sa);
+    if (fused) NTF_CUDA(ntf::launch_update_system(un, sa));
+    else NTF_CUDA(ntf::launch_update_reduce_system(u, un, sa));
+    NTF_TRY(trace_end(c, t, sa));
+    c->launches += 1;
     if (m + 1 < c->N) {
       // C: the next factor's MTTKRP, next to A's reduction (needs factor m updated; the right
       // group needs T_L, enqueued above in this or an earlier iteration of this sweep)
-      const int n = m + 1;
       NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_rows[m], 0));
       if (n >= c->s_R) NTF_CUDA(cudaStreamWaitEvent(sc, c->ev_tl, 0));
       t = trace_begin(c, "mttkrp_level2", n, 2, sc);
@@ -913,6 +930,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   const int64_t RR = static_cast<int64_t>(c->R) * c->R;
   for (int m = 0; m < c->N; ++m)
     NTF_CUDA(ntf::launch_gram(src[m], c->dims[m], c->R, c->grams + m * RR, c->st));
+  NTF_TRY(enqueue_prologue(c, A, At, Y));
 
   // The sweep is recorded once as a CUDA graph (after one eager sweep has set every kernel
   // attribute) and replayed; it is re-recorded only if the state pointers change.  Sweeps
