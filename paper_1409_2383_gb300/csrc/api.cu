@@ -11,6 +11,7 @@
 // tensor twice, whatever N is, and every M_n equals the MTTKRP of its definition up to
 // summation order.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -70,6 +71,8 @@ struct ntf_ctx {
   // Recorded sweeps: slot 0 without, slot 1 with the warm-start network.
   struct SweepGraph {
     cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;          // kept for the event-node updates of a replay
+    cudaGraphNode_t prof_node[2][2] = {};  // profiling event records [contraction][start, end]
     const void* key[3 * ntf::kMaxOrder] = {};
     int launches = 0;            // kernels in the recorded sweep
     bool prof = false;           // whether it holds profiling events
@@ -87,10 +90,16 @@ struct ntf_ctx {
     int stream, mode;
   } tr_info[kTraceMax] = {};
   int tr_n = 0;
-  // profiling
+  // profiling: events around the two contractions, one set per sweep parity (a sweep is
+  // enqueued before the previous one is read back)
   bool prof = false;
-  cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  bool ev_pending[2] = {false, false};
+  int prof_par = 0;
+  cudaEvent_t ev[2][2][2] = {};  // [parity][contraction][start, end]
+  bool ev_pending[2][2] = {};
+  // outcome of the sweeps of ntf_run (host-mapped, two slots) and their completion events
+  ntf::SweepSnap* h_snap = nullptr;
+  ntf::SweepSnap* d_snap = nullptr;
+  cudaEvent_t ev_sweep[2] = {};
   int64_t launches = 0;          // kernel launches enqueued (counted at enqueue time)
   ntf_profile pr{};
 };
@@ -184,10 +193,10 @@ ntf_status prof_mark(ntf_ctx* c, int k, int which, cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   NTF_CUDA(cudaStreamIsCapturing(st, &cs));
   if (cs == cudaStreamCaptureStatusActive)
-    NTF_CUDA(cudaEventRecordWithFlags(c->ev[k][which], st, cudaEventRecordExternal));
+    NTF_CUDA(cudaEventRecordWithFlags(c->ev[c->prof_par][k][which], st, cudaEventRecordExternal));
   else
-    NTF_CUDA(cudaEventRecord(c->ev[k][which], st));
-  if (which == 1) c->ev_pending[k] = true;
+    NTF_CUDA(cudaEventRecord(c->ev[c->prof_par][k][which], st));
+  if (which == 1) c->ev_pending[c->prof_par][k] = true;
   return NTF_OK;
 }
 
@@ -223,7 +232,8 @@ ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStr
     const int chunks = c->un.args.chunks;
     float* out = chunks > 1 ? c->partial : dst;
     NTF_TRY(prof_mark(c, 0, 0, st));
-    NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, c->umma_sched, st));
+    NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, c->umma_sched, &c->d_ctrl->stop,
+                              st));
     NTF_TRY(prof_mark(c, 0, 1, st));
     c->launches += 2;
     if (chunks > 1) {
@@ -253,7 +263,8 @@ ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStre
     const int chunks = c->ut.args.chunks;
     float* out = chunks > 1 ? c->partial_b : dst;
     NTF_TRY(prof_mark(c, 1, 0, st));
-    NTF_CUDA(ntf::launch_umma(c->ut, out, &c->d_ctrl->status, c->umma_sched + 2, st));
+    NTF_CUDA(ntf::launch_umma(c->ut, out, &c->d_ctrl->status, c->umma_sched + 2,
+                              &c->d_ctrl->stop, st));
     NTF_TRY(prof_mark(c, 1, 1, st));
     c->launches += 2;
     if (chunks > 1) {
@@ -276,16 +287,21 @@ ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStre
 }
 
 // After a host synchronisation: add the device time of the last recorded contractions.
-void prof_collect(ntf_ctx* c) {
+// (par: the parity set of a sweep that has completed; -1: both sets, after a full sync)
+void prof_collect(ntf_ctx* c, int par = -1) {
   if (!c->prof) return;
-  for (int k = 0; k < 2; ++k) {
-    if (!c->ev_pending[k]) continue;
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, c->ev[k][0], c->ev[k][1]) == cudaSuccess) {
-      c->pr.contractions[k] += 1;
-      c->pr.contraction_ms[k] += ms;
-    } else {
-      (void)cudaGetLastError();  // not recorded: leave no stale error behind
+  for (int q = 0; q < 2; ++q) {
+    if (par >= 0 && q != par) continue;
+    for (int k = 0; k < 2; ++k) {
+      if (!c->ev_pending[q][k]) continue;
+      c->ev_pending[q][k] = false;
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, c->ev[q][k][0], c->ev[q][k][1]) == cudaSuccess) {
+        c->pr.contractions[k] += 1;
+        c->pr.contraction_ms[k] += ms;
+      } else {
+        (void)cudaGetLastError();  // not recorded: leave no stale error behind
+      }
     }
   }
 }
@@ -416,7 +432,8 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
   const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
   int t = -1;
   for (int m = 0; m < c->N; ++m) {
-    const ntf::UpdateCall u = make_call(c, m, c->Mbuf, A[m], At[m], Y[m], m == c->N - 1);
+    ntf::UpdateCall u = make_call(c, m, c->Mbuf, A[m], At[m], Y[m], m == c->N - 1);
+    if (m + 1 == c->N) u.snap = c->d_snap;     // the sweep's outcome and stopping decision
     const bool fused = ntf::update_fused(u);  // the rows kernel reduces by itself
     if (m > 0) NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_post[m], 0));
     if (c->ws && c->ws_now) {
@@ -471,10 +488,49 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
   return NTF_OK;
 }
 
+// The profiling event records of a recorded sweep, so that each replay can be given the
+// event set of its parity.
+ntf_status find_prof_nodes(ntf_ctx* c, cudaGraph_t gr, ntf_ctx::SweepGraph& g) {
+  for (auto& k : g.prof_node) k[0] = k[1] = nullptr;
+  if (!c->prof) return NTF_OK;
+  size_t n = 0;
+  NTF_CUDA(cudaGraphGetNodes(gr, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  NTF_CUDA(cudaGraphGetNodes(gr, nodes.data(), &n));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    NTF_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t e = nullptr;
+    NTF_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &e));
+    for (int k = 0; k < 2; ++k)
+      for (int w = 0; w < 2; ++w)
+        if (e == c->ev[c->prof_par][k][w]) g.prof_node[k][w] = nd;
+  }
+  return NTF_OK;
+}
+
+// Replay a recorded sweep on the context's stream (profiling events of parity c->prof_par).
+ntf_status launch_graph(ntf_ctx* c, ntf_ctx::SweepGraph& g) {
+  if (g.prof)
+    for (int k = 0; k < 2; ++k) {
+      for (int w = 0; w < 2; ++w)
+        if (g.prof_node[k][w])
+          NTF_CUDA(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.prof_node[k][w],
+                                                        c->ev[c->prof_par][k][w]));
+      if (g.prof_node[k][1]) c->ev_pending[c->prof_par][k] = true;
+    }
+  NTF_CUDA(cudaGraphLaunch(g.exec, c->st));
+  c->launches += g.launches;
+  return NTF_OK;
+}
+
 void free_ctx(ntf_ctx* c) {
   if (!c) return;
-  for (auto& g : c->graphs)
+  for (auto& g : c->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
   for (cudaEvent_t e : {c->ev_start, c->ev_tl, c->ev_b, c->ev_c})
     if (e) cudaEventDestroy(e);
   for (int m = 0; m < ntf::kMaxOrder; ++m)
@@ -482,9 +538,10 @@ void free_ctx(ntf_ctx* c) {
       if (e) cudaEventDestroy(e);
   if (c->sB) cudaStreamDestroy(c->sB);
   if (c->sC) cudaStreamDestroy(c->sC);
-  for (auto& pair : c->ev)
-    for (auto& e : pair)
-      if (e) cudaEventDestroy(e);
+  for (auto& set : c->ev)
+    for (auto& pair : set)
+      for (auto& e : pair)
+        if (e) cudaEventDestroy(e);
   if (c->tr_origin) cudaEventDestroy(c->tr_origin);
   for (cudaEvent_t e : c->tr_ev)
     if (e) cudaEventDestroy(e);
@@ -509,6 +566,9 @@ void free_ctx(ntf_ctx* c) {
   cudaFree(c->dpart);
   cudaFree(c->d_ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_snap) cudaFreeHost(c->h_snap);
+  for (cudaEvent_t e : c->ev_sweep)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -683,6 +743,11 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   if (e == cudaSuccess) e = alloc((void**)&c->dpart, 1024 * sizeof(double));
   if (e == cudaSuccess) e = alloc((void**)&c->d_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_ctrl, sizeof(Ctrl));
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&c->h_snap, 2 * sizeof(ntf::SweepSnap), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->d_snap, c->h_snap, 0);
+  for (cudaEvent_t& ev : c->ev_sweep)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_ctx(c);
     return fail(e == cudaErrorMemoryAllocation ? NTF_ERR_OOM : NTF_ERR_CUDA,
@@ -828,12 +893,13 @@ ntf_status ntf_fit_from_mttkrp(ntf_ctx* c, const float* d_M_last, const float* d
 ntf_status ntf_profile_enable(ntf_ctx* c, int enable) {
   if (!c) return fail(NTF_ERR_INVALID_ARG, "null context");
   if (enable)
-    for (auto& pair : c->ev)
-      for (auto& e : pair)
-        if (!e) NTF_CUDA(cudaEventCreate(&e));
+    for (auto& set : c->ev)
+      for (auto& pair : set)
+        for (auto& e : pair)
+          if (!e) NTF_CUDA(cudaEventCreate(&e));
   c->prof = enable != 0;
   c->pr = ntf_profile{};
-  c->ev_pending[0] = c->ev_pending[1] = false;
+  for (auto& q : c->ev_pending) q[0] = q[1] = false;
   c->launches = 0;
   NTF_CUDA(cudaMemsetAsync(c->d_ctrl->ws_rows, 0, sizeof(c->d_ctrl->ws_rows), c->st));
   const double esize = c->dtype == NTF_BF16 ? 2.0 : 4.0;
@@ -932,6 +998,31 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
     NTF_CUDA(ntf::launch_gram(src[m], c->dims[m], c->R, c->grams + m * RR, c->st));
   NTF_TRY(enqueue_prologue(c, A, At, Y));
 
+  // Run control in the control block: the stopping rules are evaluated on the device by the
+  // last factor's reduction of every checked sweep, which also writes the sweep's outcome to a
+  // host-mapped slot.  The host enqueues sweep `it` before it reads the outcome of sweep it-1,
+  // so the GPU does not wait for the host between sweeps; when sweep it-1 met a rule, sweep
+  // it finds `stop` set and every kernel that would change the state returns at once.  (Sweeps
+  // that consult the warm-start network, and traced sweeps, are read back before the next one
+  // is enqueued: the network's kernels do not test `stop`, and a trace shows the last sweep.)
+  {
+    Ctrl& h = *c->h_ctrl;  // staging of the run-control fields
+    h.stop = h.stop_next = h.sweep = 0;
+    h.use_tgt = use_tgt;
+    h.use_res = use_res;
+    h.check_every = check_every;
+    h.max_outer = max_outer;
+    h.target_rfe = target_rfe;
+    h.eps_rel = c->prm.eps_rel;
+    for (int m = 0; m < c->N; ++m)
+      h.res_base[m] = std::sqrt(static_cast<double>(c->dims[m]) * c->R) * c->prm.eps_abs;
+    const size_t off = offsetof(Ctrl, stop), len = sizeof(Ctrl) - off;
+    NTF_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(c->d_ctrl) + off,
+                             reinterpret_cast<char*>(c->h_ctrl) + off, len,
+                             cudaMemcpyHostToDevice, c->st));
+    c->h_snap[0].sweep = c->h_snap[1].sweep = -1;
+  }
+
   // The sweep is recorded once as a CUDA graph (after one eager sweep has set every kernel
   // attribute) and replayed; it is re-recorded only if the state pointers change.  Sweeps
   // that consult the warm-start network have their own recording.
@@ -941,25 +1032,52 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   bool done = false;
   // Capture needs a non-legacy stream; otherwise (or if capture fails) launch eagerly.
   bool can_graph = c->st != nullptr;
+  int unread = -1;  // a checked sweep whose outcome has not been read yet
+  // read the outcome of sweep k (completed or not): stopping rules, history, status
+  auto read_sweep = [&](int k) -> ntf_status {
+    NTF_CUDA(cudaEventSynchronize(c->ev_sweep[k & 1]));
+    prof_collect(c, k & 1);
+    const ntf::SweepSnap sn = c->h_snap[k & 1];
+    if (sn.sweep != k + 1 || sn.status != 0) {
+      // no outcome (a system failed) or a device-side error: the status says which
+      NTF_CUDA(cudaStreamSynchronize(c->st));
+      NTF_TRY(read_ctrl(c));
+      NTF_TRY(take_status(c));
+      if (sn.sweep != k + 1) return fail(NTF_ERR_CUDA, "sweep %d left no outcome", k);
+    }
+    rs.iters = k + 1;
+    rs.rel_err = sn.rel_err;
+    if (rfe_hist) rfe_hist[k] = sn.rel_err;
+    if (sn.stop & 1) rs.reached_target = 1;
+    if (sn.stop & 2) rs.converged = 1;
+    if (sn.stop) done = true;
+    return NTF_OK;
+  };
+  ntf_status st_run = NTF_OK;
   for (int it = 0; it < max_outer && !done; ++it) {
     c->ws_now = c->ws != nullptr && (c->ws_sweeps == 0 || it < c->ws_sweeps);
+    if (unread >= 0 && (c->ws_now || c->trace)) {  // read before such a sweep is enqueued
+      st_run = read_sweep(unread);
+      unread = -1;
+      if (st_run != NTF_OK || done) break;
+    }
     ntf_mlp* const sweep_ws = c->ws_now ? c->ws : nullptr;
     ntf_ctx::SweepGraph& g = c->graphs[sweep_ws ? 1 : 0];
+    c->prof_par = it & 1;
     bool same = g.exec != nullptr && g.prof == c->prof && g.trace == c->trace &&
                 g.ws == sweep_ws;
     for (int m = 0; m < c->N && same; ++m)
       same = g.key[3 * m] == A[m] && g.key[3 * m + 1] == At[m] && g.key[3 * m + 2] == Y[m];
     if (same) {
-      NTF_CUDA(cudaGraphLaunch(g.exec, c->st));
-      c->launches += g.launches;
+      NTF_TRY(launch_graph(c, g));
     } else if (!c->swept_eagerly || !can_graph) {
       NTF_TRY(enqueue_sweep(c, A, At, Y));
       c->swept_eagerly = true;
     } else {
-      if (g.exec) {
-        cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
-      }
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+      g.exec = nullptr;
+      g.graph = nullptr;
       cudaGraph_t gr = nullptr;
       const int64_t before = c->launches;
       bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -967,15 +1085,17 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
       g.launches = static_cast<int>(c->launches - before);
       c->launches = before;
       if (ok) ok = cudaStreamEndCapture(c->st, &gr) == cudaSuccess && sw == NTF_OK;
+      if (ok) ok = find_prof_nodes(c, gr, g) == NTF_OK;
       if (ok) ok = cudaGraphInstantiate(&g.exec, gr, 0) == cudaSuccess;
-      if (gr) cudaGraphDestroy(gr);
       if (!ok) {
         (void)cudaGetLastError();
+        if (gr) cudaGraphDestroy(gr);
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
         can_graph = false;
         NTF_TRY(enqueue_sweep(c, A, At, Y));
       } else {
+        g.graph = gr;
         g.prof = c->prof;
         g.trace = c->trace;
         g.ws = sweep_ws;
@@ -984,37 +1104,33 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
           g.key[3 * m + 1] = At[m];
           g.key[3 * m + 2] = Y[m];
         }
-        NTF_CUDA(cudaGraphLaunch(g.exec, c->st));
-        c->launches += g.launches;
+        NTF_TRY(launch_graph(c, g));
       }
     }
+    NTF_CUDA(cudaEventRecord(c->ev_sweep[it & 1], c->st));
     if (c->prof) c->pr.sweeps += 1;
     rs.iters = it + 1;
-    const bool check = ((it + 1) % check_every == 0) || it + 1 == max_outer;
-    if (!check) continue;
-    NTF_TRY(read_ctrl(c));
-    prof_collect(c);
-    NTF_TRY(take_status(c));
-    rs.rel_err = c->h_ctrl->rel_err;
-    if (rfe_hist) rfe_hist[it] = rs.rel_err;
-    if (use_tgt && rs.rel_err <= target_rfe) {
-      rs.reached_target = 1;
-      done = true;
+    if (unread >= 0) {  // the previous checked sweep, while this one runs
+      st_run = read_sweep(unread);
+      unread = -1;
+      if (st_run != NTF_OK) break;
+      if (done) {
+        rs.iters = it;  // sweep `it` finds stop set and leaves the state as it is
+        break;
+      }
     }
-    if (use_res) {
-      bool all = true;
-      for (int m = 0; m < c->N && all; ++m) {
-        const double* s = c->h_ctrl->stats[m];
-        const double base = std::sqrt(static_cast<double>(c->dims[m]) * c->R) * c->prm.eps_abs;
-        all = s[0] <= base + c->prm.eps_rel * std::max(s[2], s[3]) &&
-              s[1] <= base + c->prm.eps_rel * s[4];
-      }
-      if (all) {
-        rs.converged = 1;
-        done = true;
-      }
+    const bool check = ((it + 1) % check_every == 0) || it + 1 == max_outer;
+    if (check) unread = it;
+    if (check && (c->ws_now || c->trace || it + 1 == max_outer)) {
+      st_run = read_sweep(unread);
+      unread = -1;
+      if (st_run != NTF_OK) break;
     }
   }
+  if (st_run == NTF_OK && unread >= 0) st_run = read_sweep(unread);
+  // the run is over: the sweep kernels must not skip outside it
+  NTF_CUDA(cudaMemsetAsync(&c->d_ctrl->stop, 0, 3 * sizeof(int), c->st));
+  if (st_run != NTF_OK) return st_run;
   if (!done && (use_res || use_tgt)) result = NTF_ERR_NOT_CONVERGED;
   if (out) *out = rs;
   if (result != NTF_OK) fail(result, "no stopping criterion met in %d iterations", max_outer);

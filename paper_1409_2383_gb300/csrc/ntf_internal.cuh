@@ -27,6 +27,16 @@ struct Group {
 // Deferred device-side error bits.
 enum : int { kStNotSpd = 1, kStNonFinite = 2, kStTimeout = 4 };
 
+// Outcome of one sweep of ntf_run, written by the last factor's reduction into host-mapped
+// memory (slot = sweep & 1), so that the host reads it without a copy on the stream.
+struct SweepSnap {
+  int sweep;       // sweeps finished in the run, this one included
+  int status;      // kSt* bits at the end of the sweep
+  int stop;        // 1: fit target reached, 2: residual criteria of Sec. III-C met
+  int pad;
+  double rel_err;
+};
+
 // Small device-resident control block: penalties, residual norms and fit terms live here so
 // that a whole sweep runs without host round trips.
 struct Ctrl {
@@ -42,6 +52,15 @@ struct Ctrl {
   unsigned long long ws_rows[2];  // warm start: rows considered, rows that took the prediction
   unsigned int red_count[kMaxOrder];  // CTAs of the running rows kernel that have finished
   unsigned int sys_count;             // CTAs of the running reduce-and-system kernel finished
+  // Run control (ntf_run): at a checked sweep the last factor's reduction decides whether the
+  // run stops there; the rows, reductions and systems of every later sweep then return at once
+  // (the host enqueues a sweep before it reads the outcome of the previous one).
+  int stop;                // read by the sweep kernels
+  int stop_next;           // decided by the running sweep; moved to stop by the last CTA
+  int sweep;               // sweeps finished in the current run
+  int use_tgt, use_res, check_every, max_outer;
+  double target_rfe, eps_rel;
+  double res_base[kMaxOrder];  // sqrt(I_m R) eps_abs
 };
 
 // ------------------------------------------------------------------ kernel launchers
@@ -100,6 +119,7 @@ struct Args {
   float* out;
   int* err;           // device status word: kStTimeout is or-ed in on a timeout
   unsigned* sched;    // [2] work-item counter and finished-CTA counter (zero between launches)
+  const int* skip;    // nonzero flag (read once per CTA): no work; may be null
 };
 }  // namespace umma
 
@@ -126,7 +146,7 @@ cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* W
 // sched: 2 device counters owned by the caller, zero before the first launch (each launch
 // leaves them zero); launches sharing a counter pair must not overlap
 cudaError_t launch_umma(const UmmaPlan& plan, float* out, int* err, unsigned* sched,
-                        cudaStream_t st);
+                        const int* skip, cudaStream_t st);
 // The contractions' bounded mbarrier wait, on a barrier that nothing completes: ors
 // kStTimeout into *err after limit_ns.
 cudaError_t launch_wait_check(int* err, uint64_t limit_ns, cudaStream_t st);
@@ -152,6 +172,7 @@ struct UpdateCall {
   double* gram_part;
   double* scal_part;
   double* gram_out;
+  SweepSnap* snap;  // a sweep of ntf_run: its outcome slots (host-mapped), else null
   int64_t I;
   int N, mode, R, inner, rho_policy;
   bool kr_aux, want_fit;

@@ -119,12 +119,13 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
 }
 
 cudaError_t launch_umma(const UmmaPlan& p, float* out, int* err, unsigned* sched,
-                        cudaStream_t st) {
+                        const int* skip, cudaStream_t st) {
   if (!p.on || !sched) return cudaErrorInvalidValue;
   umma::Args a = p.args;
   a.out = out;
   a.err = err;
   a.sched = sched;
+  a.skip = skip;
   return p.f32 ? umma::launch_f32(p, a, st) : umma::launch_bf16(p, a, st);
 }
 

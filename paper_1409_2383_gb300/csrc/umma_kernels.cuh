@@ -233,6 +233,20 @@ __global__ void __launch_bounds__(Cfg<kT, kF32, kN, kWRes>::kThreads, 1)
   __shared__ int s_item[kItemQ];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ int skip_flag;
+
+  // No work (a sweep of a run that has stopped): the CTA only takes part in the counter
+  // protocol.  The flag is read once per CTA; CTAs that read it before it was set take every
+  // item between them through the work-item counter.
+  if (threadIdx.x == 0) skip_flag = a.skip ? *reinterpret_cast<const volatile int*>(a.skip) : 0;
+  __syncthreads();
+  if (skip_flag) {
+    if (threadIdx.x == 0 && atomicAdd(a.sched + 1, 1u) == gridDim.x - 1) {
+      a.sched[0] = 0;
+      a.sched[1] = 0;
+    }
+    return;
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base_s = (saddr(smem_raw) + 1023u) & ~1023u;

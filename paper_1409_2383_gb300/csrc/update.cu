@@ -56,6 +56,7 @@ struct UpdArgs {
   double* gram_part;    // [blocks, R (R + 1) / 2] packed lower triangles
   double* scal_part;    // [blocks, kScal]
   double* gram_out;     // [R, R] stored Gram of this factor
+  SweepSnap* snap;      // a sweep of ntf_run: its outcome slots (host-mapped), else null
   int64_t I;
   int N, mode, R, inner, rho_policy, kr_aux, want_fit;
   int fused;            // rows kernel also reduces (last CTA)
@@ -280,11 +281,16 @@ __device__ __forceinline__ void rows_cta_tail(const UpdArgs& a, float (&part)[kS
   if (!s_last) return;
   __threadfence();
   update_reduce_cta(a, gridDim.x);
-  if (tid == 0) a.ctrl->red_count[a.mode] = 0;
+  if (tid == 0) {
+    a.ctrl->red_count[a.mode] = 0;
+    // every CTA of this kernel has read stop by now
+    if (a.snap && a.want_fit) a.ctrl->stop = a.ctrl->stop_next;
+  }
 }
 
 template <int S>
 __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
+  if (a.ctrl->stop) return;  // the run has stopped
   system_body<S, kSysThreads>(a);
 }
 
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
   const SysView sv = sys_view(a.sys, a.mode, R);
   // every load is issued before the status test, so that their latencies overlap (the
   // system slot and the rows are valid memory either way)
-  const int bad = a.ctrl->bad[a.mode];
+  const int bad = a.ctrl->bad[a.mode] | a.ctrl->stop;
   Real hc[kR];
 #pragma unroll
   for (int k = 0; k < kR; ++k) {
@@ -320,7 +326,8 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
   const Real m = live ? static_cast<Real>(a.M[idx]) : Real(0);
   Real t = live ? static_cast<Real>(a.At[idx]) : Real(0);
   Real y = live ? static_cast<Real>(a.Y[idx]) : Real(0);
-  if (bad) return;  // uniform: the system of this factor failed; the state is kept
+  if (bad) return;  // uniform: the system of this factor failed, or the run has stopped; the
+                    // state is kept
   const Real rinv = Real(1) / rho;
   float part[kScal] = {0, 0, 0, 0, 0, 0, 0, 0};
   float f = 0.0f;
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
   Real* vbuf = reinterpret_cast<Real*>(shd + ((RR * sizeof(Real) + RR * 4 + 15) / 16) * 2);
   float* frow = reinterpret_cast<float*>(vbuf + kRowWarps * 64); // [kRowWarps][64]
   __shared__ double red[kRowWarps][kScal];
-  if (a.ctrl->bad[a.mode]) return;  // uniform
+  if (a.ctrl->bad[a.mode] || a.ctrl->stop) return;  // uniform
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const SysView sv = sys_view(a.sys, a.mode, R);
   for (int idx = tid; idx < RR; idx += kRowThreads) {
@@ -510,6 +517,32 @@ __device__ void update_finalize(const UpdArgs& a, const double* sum) {
     finite = finite && isfinite(e2);
   }
   if (!finite) atomicOr(&c->status, kStNonFinite);
+  if (a.snap && a.want_fit) {
+    // the last factor of a sweep of ntf_run: at a checked sweep, the stopping rules (the fit
+    // target; the residual criteria of Sec. III-C over every factor's norms of this sweep)
+    const int k = c->sweep;
+    int stop = 0;
+    if ((k + 1) % c->check_every == 0 || k + 1 == c->max_outer) {
+      if (c->use_tgt && c->rel_err <= c->target_rfe) stop |= 1;
+      if (c->use_res) {
+        bool all = true;
+        for (int m = 0; m < a.N && all; ++m) {
+          const double* s = c->stats[m];
+          all = s[0] <= c->res_base[m] + c->eps_rel * fmax(s[2], s[3]) &&
+                s[1] <= c->res_base[m] + c->eps_rel * s[4];
+        }
+        if (all) stop |= 2;
+      }
+    }
+    const int status = c->status;
+    SweepSnap* sn = a.snap + (k & 1);
+    sn->sweep = k + 1;
+    sn->status = status;
+    sn->stop = stop;
+    sn->rel_err = c->rel_err;
+    c->stop_next = stop != 0 || status != 0;
+    c->sweep = k + 1;
+  }
 }
 
 // Packed Gram entry e of the updated factor: the per-CTA partials summed over blocks in a
@@ -631,6 +664,9 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
   __shared__ int s_last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int T = a.R * (a.R + 1) / 2;
+  // the run has stopped (stop changes only in this kernel's last CTA, after every CTA has
+  // read it): nothing to do
+  if (a.ctrl->stop) return;
   if (!a.ctrl->bad[a.mode]) {  // uniform
     if (blockIdx.x + 1 < gridDim.x) {
       const int e = blockIdx.x * kRedEntries + (tid >> 3);
@@ -650,7 +686,11 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
   if (!s_last) return;
   __threadfence();
   system_body<S, 256>(as);
-  if (tid == 0) a.ctrl->sys_count = 0;
+  if (tid == 0) {
+    a.ctrl->sys_count = 0;
+    // every CTA of this kernel has read stop by now
+    if (a.snap && a.want_fit) a.ctrl->stop = a.ctrl->stop_next;
+  }
 }
 
 }  // namespace
@@ -679,6 +719,7 @@ UpdArgs make_args(const UpdateCall& u) {
   a.gram_part = u.gram_part;
   a.scal_part = u.scal_part;
   a.gram_out = u.gram_out;
+  a.snap = u.snap;
   a.I = u.I;
   a.N = u.N;
   a.mode = u.mode;

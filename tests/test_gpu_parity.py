@@ -294,6 +294,40 @@ def test_stopping_rule_and_target(ntf):
     assert rs["reached_target"] == 1 and rs["rel_err"] <= 0.2 and rs["iters"] < 400
 
 
+@pytest.mark.parametrize("check_every,rule", [(1, "target"), (3, "target"), (1, "residual"),
+                                               (2, "residual")])
+def test_run_stops_at_the_first_sweep_that_meets_the_rule(ntf, check_every, rule):
+    """The host enqueues a sweep before it reads the previous sweep's outcome; the sweep after
+    the one that met the stopping rule must leave the state untouched.  The stopped run's state
+    equals, bit for bit, that of a run of exactly as many sweeps without a rule, and the rule's
+    value at that sweep matches."""
+    dims, R = (40, 36, 32), 4
+    X, fs, init = synth.workload(dims, R, seed=3, snr_db=20.0)
+    eps = 1e-3 if rule == "residual" else 0.0
+    p = ntf.default_params(paper_mode=False, eps_abs=eps, eps_rel=eps)
+    fresh = lambda: ([cuda(F) for F in init], [cuda(F) for F in init],
+                     [torch.zeros(d, R, device="cuda") for d in dims])
+    with ntf.Context(cuda(X), R, p) as ctx:
+        A, At, Y = fresh()
+        h = ctx.run(A, At, Y, 60, check_every=1, history=True)["history"]
+        target = h[9] if rule == "target" else 0.0
+        A, At, Y = fresh()
+        rs = ctx.run(A, At, Y, 400, target_rfe=target, check_every=check_every)
+        k = rs["iters"]
+        if rule == "target":
+            assert rs["reached_target"] == 1 and rs["rel_err"] <= target
+            want = next(j for j in range(check_every, 61, check_every) if h[j - 1] <= target)
+            assert k == want and rs["rel_err"] == h[k - 1]
+        else:
+            assert rs["converged"] == 1 and k < 400 and k % check_every == 0
+        A2, At2, Y2 = fresh()
+        p2 = ctx.run(A2, At2, Y2, k, check_every=k)
+        assert p2["rel_err"] == rs["rel_err"]
+        for S, S2 in ((A, A2), (At, At2), (Y, Y2)):
+            for a, b in zip(S, S2):
+                assert torch.equal(a, b)
+
+
 # ------------------------------------------------------------------ full-size workloads
 
 def _sampled_rows(ntf, dims, R, structure="uniform", storage="f32", snr=20.0, nrows=3):
