@@ -371,7 +371,7 @@ ntf_status warm_start(ntf_ctx* c, int mode, const float* M, float* At, float* Y,
   if (!c->ws || !c->ws_now) return NTF_OK;
   NTF_CUDA(ntf::mlp_warm_start(c->ws, c->sys, mode, M, At, Y, c->dims[mode],
                                c->d_ctrl->ws_rows, st));
-  c->launches += 8;
+  c->launches += ntf::mlp_ws_launches(c->ws);
   return NTF_OK;
 }
 

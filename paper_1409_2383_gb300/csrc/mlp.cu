@@ -415,7 +415,319 @@ __global__ void k_ws_judge(const float* __restrict__ out, const float* __restric
   }
 }
 
+// The warm start of one factor in two kernels (one coefficient matrix G shared by all rows):
+// k_ws_group forms the group term W1_G vec(G/s) once; k_ws_fused, per CTA of kWsRows rows,
+// the inputs [m/s ; Hinv m], the three layers (weights and activations in shared memory) and
+// the judge (one warp per row).  Layers: warp w forms outputs w, w + 8, ...; lane l takes the
+// inputs l, l + 32, ... of every row (weights read along their rows, so a warp's loads are
+// contiguous), and the eight rows' partial sums are combined across the lanes by a fixed
+// exchange-and-add tree.
+constexpr int kWsRows = 8;
+constexpr int kWsMaxK = 256;  // widest layer input held in registers (8 per lane)
+
+__device__ __forceinline__ void ws_judge_row(const float* out, const float* G, const float* M,
+                                             float s, float* At, float* Y, int64_t row, int R,
+                                             float* xs, int lane,
+                                             unsigned long long* counters) {
+  float xc[2], yc[2], xo[2], m[2];
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    xc[h] = yc[h] = xo[h] = m[h] = 0.0f;
+    if (j < R) {
+      xc[h] = fmaxf(0.0f, out[j]);
+      yc[h] = fminf(0.0f, s * out[R + j]);
+      xo[h] = At[row * R + j];
+      m[h] = M[row * R + j];
+      xs[j] = xc[h];
+      xs[64 + j] = xo[h];
+    }
+  }
+  __syncwarp();
+  float rc = 0.0f, ro = 0.0f, qc = 0.0f, qo = 0.0f;  // q: twice the row objective
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    if (j >= R) continue;
+    float gc = -m[h], go = -m[h];
+    for (int k = 0; k < R; ++k) {
+      const float gk = G[k * R + j];  // G symmetric
+      gc = fmaf(gk, xs[k], gc);
+      go = fmaf(gk, xs[64 + k], go);
+    }
+    const float a = fminf(xc[h], gc), b = fminf(xo[h], go);
+    rc += a * a;
+    ro += b * b;
+    qc += xc[h] * (gc - m[h]);
+    qo += xo[h] * (go - m[h]);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    rc += __shfl_xor_sync(0xffffffffu, rc, off);
+    ro += __shfl_xor_sync(0xffffffffu, ro, off);
+    qc += __shfl_xor_sync(0xffffffffu, qc, off);
+    qo += __shfl_xor_sync(0xffffffffu, qo, off);
+  }
+  const bool take = rc < ro && qc < qo;
+  if (take) {
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      if (j < R) {
+        At[row * R + j] = xc[h];
+        Y[row * R + j] = yc[h];
+      }
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&counters[0], 1ull);
+    if (take) atomicAdd(&counters[1], 1ull);
+  }
+}
+
+// Sums of v[0..7] over the 32 lanes: lane l returns the sum for row (l >> 2) & 7.  Halves of
+// the set are exchanged at distances 16, 8, 4 (each lane keeps the half its lane bit selects
+// and adds its partner's copy), then distances 2 and 1 complete the sum.
+__device__ __forceinline__ float rows8_sum(const float (&v)[kWsRows], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float w[4], u[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b4 ? v[i] : v[i + 4];
+    const float keep = b4 ? v[i + 4] : v[i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b3 ? w[i] : w[i + 2];
+    const float keep = b3 ? w[i + 2] : w[i];
+    u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float t = (b2 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, b2 ? u[0] : u[1], 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
+// One layer for the CTA's rows: y[r][o] = act(b[o] + W[o, 0:K] x[r]) for o < Nout, W
+// [Nout][K] (BF16), b, x [kWsRows][K] and y [kWsRows][ldy] in shared memory, K <= kWsMaxK;
+// warp w of nw forms outputs w, w + nw, ...
+template <bool kGelu>
+__device__ __forceinline__ void ws_layer(const __nv_bfloat16* W, int K, int Nout,
+                                         const float* bias, const float* x, float* y, int ldy,
+                                         int warp, int nw, int lane) {
+  float xr[kWsMaxK / 32][kWsRows];
+#pragma unroll
+  for (int j = 0; j < kWsMaxK / 32; ++j)
+#pragma unroll
+    for (int r = 0; r < kWsRows; ++r) {
+      const int k = lane + 32 * j;
+      xr[j][r] = k < K ? x[r * K + k] : 0.0f;
+    }
+  const int rl = (lane >> 2) & 7;
+  // four outputs per pass, so that their exchange trees overlap
+  for (int o0 = 4 * warp; o0 < Nout; o0 += 4 * nw) {
+    float acc[4][kWsRows] = {};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = o0 + q < Nout ? o0 + q : Nout - 1;  // (a repeat past the end is dropped)
+      const __nv_bfloat16* w = W + o * K;
+#pragma unroll
+      for (int j = 0; j < kWsMaxK / 32; ++j) {
+        const int k = lane + 32 * j;
+        if (32 * j < K) {
+          const float wk = k < K ? __bfloat162float(w[k]) : 0.0f;
+#pragma unroll
+          for (int r = 0; r < kWsRows; ++r) acc[q][r] = fmaf(xr[j][r], wk, acc[q][r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = o0 + q;
+      const float t = rows8_sum(acc[q], lane);
+      if ((lane & 3) == 0 && o < Nout) {  // rows past nr: from zeros
+        const float z = t + bias[o];
+        y[rl * ldy + o] = kGelu ? gelu(z) : z;
+      }
+    }
+  }
+}
+
+// n BF16 values from global to shared memory: asynchronous 16-byte copies (cp.async, all in
+// flight until ws_stage_wait) when both ends allow, else plain loads eight at a time.
+// (rot: where the copy order starts, so that CTAs copying the same block begin at different
+// places of it and spread over the L2 slices)
+__device__ __forceinline__ void ws_stage(__nv_bfloat16* dst, const __nv_bfloat16* src, int n,
+                                         int tid, int nt, int rot = 0) {
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0 &&
+      n % 8 == 0) {
+    const int n8 = n / 8;
+    for (int i0 = tid; i0 < n8; i0 += nt) {
+      const int i = (i0 + rot) % n8;
+      const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + 8 * i));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + 8 * i)
+                   : "memory");
+    }
+  } else {
+    for (int i0 = tid; i0 < n; i0 += 8 * nt) {
+      __nv_bfloat16 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * nt < n) v[u] = src[i0 + u * nt];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * nt < n) dst[i0 + u * nt] = v[u];
+    }
+  }
+}
+__device__ __forceinline__ void ws_stage_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+constexpr int kWsThreads = 512;
+
+// trace(G) by one warp in a fixed order (lane l adds the diagonal entries l, l + 32, then a
+// butterfly), the same in both warm-start kernels
+__device__ __forceinline__ float ws_trace(const float* G, int R, int lane) {
+  float t = 0.0f;
+  for (int i = lane; i < R; i += 32) t += G[i * R + i];
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  return t;
+}
+
+// The group term of the first layer, hG = W1_G vec(G/s) (s = trace(G)/R), once per factor:
+// warp per hidden unit, lanes along the R^2 inputs.
+__global__ void __launch_bounds__(256)
+    k_ws_group(MlpShape s, const __nv_bfloat16* __restrict__ pb, const float* __restrict__ G,
+               float* __restrict__ hG) {
+  const int R = s.R, RR = R * R, lane = threadIdx.x & 31;
+  const int h = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (h >= s.H) return;  // whole warps
+  const float inv = 1.0f / (ws_trace(G, R, lane) / R);
+  const __nv_bfloat16* w = pb + s.oW1 + static_cast<int64_t>(h) * s.Din;
+  float g = 0.0f;
+  for (int k0 = 0; k0 < RR; k0 += 32 * 16) {
+    float gv[16], wv[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = k0 + lane + 32 * j;
+      gv[j] = k < RR ? G[k] : 0.0f;
+      wv[j] = k < RR ? __bfloat162float(w[k]) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) g = fmaf(gv[j] * inv, wv[j], g);
+  }
+  for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
+  if (lane == 0) hG[h] = g;
+}
+
+size_t ws_fused_smem(const MlpShape& s) {
+  const size_t RR = static_cast<size_t>(s.R) * s.R, H = s.H, P = s.P, D = s.Dout;
+  const size_t wbytes = (H * H + D * H + H * P) * sizeof(__nv_bfloat16);
+  const size_t fbytes =
+      (2 * RR + kWsRows * (s.R + P + 2 * H + D) + 3 * H + D + kWsRows * 128) * sizeof(float);
+  return ((wbytes + 15) / 16) * 16 + fbytes;
+}
+
+__global__ void __launch_bounds__(kWsThreads)
+    k_ws_fused(MlpShape s, const float* __restrict__ p, const __nv_bfloat16* __restrict__ pb,
+               const float* __restrict__ hG, const float* __restrict__ G,
+               const float* __restrict__ Hinv, const float* __restrict__ M,
+               float* __restrict__ At, float* __restrict__ Y, int64_t I,
+               unsigned long long* counters) {
+  extern __shared__ __align__(16) unsigned char ws_smem[];
+  __shared__ float s_scale[2];
+  const int R = s.R, P = s.P, H = s.H, D = s.Dout, RR = R * R;
+  __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(ws_smem);  // [H][H]
+  __nv_bfloat16* sW3 = sW2 + H * H;                                  // [D][H]
+  __nv_bfloat16* sW1u = sW3 + D * H;                                 // [H][P]
+  const size_t wbytes = (static_cast<size_t>(H) * H + D * H + H * P) * sizeof(__nv_bfloat16);
+  float* sG = reinterpret_cast<float*>(ws_smem + ((wbytes + 15) / 16) * 16);  // [RR] G
+  float* sHi = sG + RR;           // [RR] (G + rho I)^{-1}
+  float* sM = sHi + RR;           // [kWsRows][R] MTTKRP rows
+  float* su = sM + kWsRows * R;   // [kWsRows][P] per-row inputs
+  float* sh1 = su + kWsRows * P;  // [kWsRows][H]
+  float* sh2 = sh1 + kWsRows * H; // [kWsRows][H]
+  float* sout = sh2 + kWsRows * H;// [kWsRows][D]
+  float* sg = sout + kWsRows * D; // [H] group term + b1
+  float* sb2 = sg + H;            // [H]
+  float* sb3 = sb2 + H;           // [D]
+  float* sxs = sb3 + D;           // [kWsRows][128] judge scratch
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
+  const int nw = nt >> 5;
+  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kWsRows;
+  const int nr = static_cast<int>(I - row0 < kWsRows ? I - row0 : kWsRows);
+  // the small inputs first (one round of loads), then the weights of layers 2, 3 and the
+  // per-row part of layer 1 by asynchronous copies, in flight while the inputs are formed
+  for (int i = tid; i < RR; i += nt) {
+    sG[i] = G[i];
+    sHi[i] = Hinv[i];
+  }
+  for (int i = tid; i < kWsRows * R; i += nt) sM[i] = i < nr * R ? M[row0 * R + i] : 0.0f;
+  for (int i = tid; i < H; i += nt) {
+    sg[i] = hG[i] + p[s.ob1 + i];
+    sb2[i] = p[s.ob2 + i];
+  }
+  for (int i = tid; i < D; i += nt) sb3[i] = p[s.ob3 + i];
+  const int rot = blockIdx.x * 997;
+  ws_stage(sW2, pb + s.oW2, H * H, tid, nt, rot);
+  ws_stage(sW3, pb + s.oW3, D * H, tid, nt, rot);
+  for (int h0 = 0; h0 < H; h0 += nw) {  // the per-row columns of W1, row by row
+    const int h = (h0 + warp + blockIdx.x) % H;
+    if (h0 + warp < H)
+      ws_stage(sW1u + h * P, pb + s.oW1 + static_cast<int64_t>(h) * s.Din + RR, P, lane, 32);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const float tr = ws_trace(sG, R, lane);
+    if (lane == 0) {
+      const float sc = tr / R;
+      s_scale[0] = sc;
+      s_scale[1] = 1.0f / sc;
+    }
+  }
+  __syncthreads();
+  const float sc = s_scale[0], inv = s_scale[1];
+  for (int i = tid; i < kWsRows * P; i += nt) {
+    const int r = i / P, c = i - r * P;
+    const float* m = sM + r * R;  // zeros past nr
+    float v;
+    if (c < R) {
+      v = m[c] * inv;
+    } else {
+      v = 0.0f;
+      for (int j = 0; j < R; ++j) v = fmaf(sHi[j * R + (c - R)], m[j], v);  // Hinv symmetric
+    }
+    su[i] = v;
+  }
+  ws_stage_wait();
+  __syncthreads();
+  ws_layer<true>(sW1u, P, H, sg, su, sh1, H, warp, nw, lane);
+  __syncthreads();
+  ws_layer<true>(sW2, H, H, sb2, sh1, sh2, H, warp, nw, lane);
+  __syncthreads();
+  ws_layer<false>(sW3, H, D, sb3, sh2, sout, D, warp, nw, lane);
+  __syncthreads();
+  if (warp < nr)
+    ws_judge_row(sout + warp * D, sG, M, sc, At, Y, row0 + warp, R, sxs + warp * 128, lane,
+                 counters);
+}
+
 }  // namespace
+
+bool ws_fused_ok(const MlpShape& s) {
+  return s.H <= kWsMaxK && s.P <= kWsMaxK && ws_fused_smem(s) <= 220 * 1024;
+}
+
+cudaError_t ws_fused(const MlpShape& s, const float* p, const __nv_bfloat16* pb, float* hG,
+                     const float* G, const float* Hinv, const float* M, float* At, float* Y,
+                     int64_t I, unsigned long long* counters, cudaStream_t st) {
+  const size_t smem = ws_fused_smem(s);
+  cudaError_t e = cudaFuncSetAttribute(k_ws_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_ws_group<<<(s.H + 7) / 8, 256, 0, st>>>(s, pb, G, hG);
+  k_ws_fused<<<static_cast<unsigned>((I + kWsRows - 1) / kWsRows), kWsThreads, smem, st>>>(
+      s, p, pb, hG, G, Hinv, M, At, Y, I, counters);
+  return cudaGetLastError();
+}
 
 cudaError_t ws_prepare(const float* G, const float* Hinv, const float* M, int R, int64_t I,
                        float* Gn, float* mrows, float* s_out, cudaStream_t st) {

@@ -86,6 +86,9 @@ cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float*
                            float* Y, int64_t I, unsigned long long* counters, cudaStream_t st) {
   const int R = n->s.R;
   const float* G = update_sys_h32(sys, mode, R);
+  if (ws_fused_ok(n->s))
+    return ws_fused(n->s, n->p, n->pb, n->hG, G, update_sys_hinv32(sys, mode, R), M, At, Y, I,
+                    counters, st);
   cudaError_t e = ws_prepare(G, update_sys_hinv32(sys, mode, R), M, R, I, n->Gn, n->mrows,
                              n->s_dev, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->row_group, 0, I * sizeof(int), st);
@@ -97,6 +100,7 @@ cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float*
   return e;
 }
 int mlp_rank(const ntf_mlp* n) { return n->s.R; }
+int mlp_ws_launches(const ntf_mlp* n) { return ws_fused_ok(n->s) ? 2 : 9; }
 int mlp_max_rows(const ntf_mlp* n) { return n->max_rows; }
 }  // namespace ntf
 

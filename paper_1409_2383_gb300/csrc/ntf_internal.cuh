@@ -219,6 +219,13 @@ cudaError_t ws_prepare(const float* G, const float* Hinv, const float* M, int R,
 cudaError_t ws_judge(const float* out, const float* G, const float* M, const float* s_ptr,
                      float* At, float* Y, int64_t I, int R, unsigned long long* counters,
                      cudaStream_t st);
+// The whole warm start of a factor (inputs, network, judge) in one kernel, when the hidden
+// width and shared memory allow (ws_fused_ok); the computation of ws_prepare + forward +
+// ws_judge with other summation orders in the products.
+bool ws_fused_ok(const MlpShape& s);
+cudaError_t ws_fused(const MlpShape& s, const float* p, const __nv_bfloat16* pb, float* hG,
+                     const float* G, const float* Hinv, const float* M, float* At, float* Y,
+                     int64_t I, unsigned long long* counters, cudaStream_t st);
 // update.cu: FP32 coefficient matrix (no rho) and FP32 (G + rho I)^{-1} of factor `mode` in
 // its system slot
 const float* update_sys_h32(const double* sys, int mode, int R);
@@ -228,6 +235,7 @@ const float* update_sys_hinv32(const double* sys, int mode, int R);
 cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float* M, float* At,
                            float* Y, int64_t I, unsigned long long* counters, cudaStream_t st);
 int mlp_rank(const ntf_mlp* n);
+int mlp_ws_launches(const ntf_mlp* n);  // kernels one mlp_warm_start launches
 int mlp_max_rows(const ntf_mlp* n);
 
 }  // namespace ntf
