@@ -161,62 +161,53 @@ __global__ void k_post_slow(const float* __restrict__ T, int64_t Ia, int64_t Ib,
 // Vectorised second tree level for R % 4 == 0 (T, F, out 16-byte aligned), Q = R / 4 float4
 // chunks per row.
 //
-// fast: out[a, :] = sum_b T[a, b, :] * F[b, :].  One CTA (32 Q threads) per a: warp w owns
-// chunk w of every row, lane l the rows b = l, l + 32, ...; four accumulators, then a fixed
-// butterfly over the lanes.
-__global__ void k_post_fast4(const float4* __restrict__ T, int64_t Ia, int64_t Ib, int Q,
-                             const float4* __restrict__ F, float4* __restrict__ out) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// fast: out[a, :] = sum_b T[a, b, :] * F[b, :].  One CTA (32 Q threads) per a; the slab
+// T[a] (Ib Q float4, contiguous) is read in order: thread t takes chunk q = t % Q of rows
+// b = t / Q, t / Q + 32, ... (eight rows in flight), so consecutive threads read
+// consecutive float4; then the 32 partial sums of each chunk are added in a fixed order
+// through shared memory.
+__global__ void __launch_bounds__(512) k_post_fast4(const float4* __restrict__ T, int64_t Ia,
+                                                   int64_t Ib, int Q,
+                                                   const float4* __restrict__ F,
+                                                   float4* __restrict__ out) {
+  __shared__ float4 part[512];
+  const int t = threadIdx.x, q = t % Q, b0 = t / Q;
   for (int64_t a = blockIdx.x; a < Ia; a += gridDim.x) {
     const float4* Ta = T + a * Ib * Q;
-    float4 s[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int64_t b = lane;
-    for (; b + 224 < Ib; b += 256) {  // eight rows per lane in flight
-      float4 t[8], f[8];
+    float4 s[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    for (int64_t bb = b0; bb < Ib; bb += 32 * 8) {
+      float4 tv[8], fv[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        t[u] = Ta[(b + 32 * u) * Q + w];
-        f[u] = __ldg(F + (b + 32 * u) * Q + w);
+        const int64_t b = bb + 32 * u;
+        tv[u] = fv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (b < Ib) {
+          tv[u] = Ta[b * Q + q];
+          fv[u] = __ldg(F + b * Q + q);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        s[u & 3].x = fmaf(t[u].x, f[u].x, s[u & 3].x);
-        s[u & 3].y = fmaf(t[u].y, f[u].y, s[u & 3].y);
-        s[u & 3].z = fmaf(t[u].z, f[u].z, s[u & 3].z);
-        s[u & 3].w = fmaf(t[u].w, f[u].w, s[u & 3].w);
+        s[u & 1].x = fmaf(tv[u].x, fv[u].x, s[u & 1].x);
+        s[u & 1].y = fmaf(tv[u].y, fv[u].y, s[u & 1].y);
+        s[u & 1].z = fmaf(tv[u].z, fv[u].z, s[u & 1].z);
+        s[u & 1].w = fmaf(tv[u].w, fv[u].w, s[u & 1].w);
       }
     }
-    for (; b + 96 < Ib; b += 128) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 t = Ta[(b + 32 * u) * Q + w], f = __ldg(F + (b + 32 * u) * Q + w);
-        s[u].x = fmaf(t.x, f.x, s[u].x);
-        s[u].y = fmaf(t.y, f.y, s[u].y);
-        s[u].z = fmaf(t.z, f.z, s[u].z);
-        s[u].w = fmaf(t.w, f.w, s[u].w);
+    part[t] = make_float4(s[0].x + s[1].x, s[0].y + s[1].y, s[0].z + s[1].z, s[0].w + s[1].w);
+    __syncthreads();
+    if (t < Q) {  // chunk t: partials t, t + Q, ..., t + 31 Q
+      float4 v = part[t];
+      for (int j = 1; j < 32; ++j) {
+        const float4 p = part[t + j * Q];
+        v.x += p.x;
+        v.y += p.y;
+        v.z += p.z;
+        v.w += p.w;
       }
+      out[a * Q + t] = v;
     }
-    for (; b < Ib; b += 32) {
-      const float4 t = Ta[b * Q + w], f = __ldg(F + b * Q + w);
-      s[0].x = fmaf(t.x, f.x, s[0].x);
-      s[0].y = fmaf(t.y, f.y, s[0].y);
-      s[0].z = fmaf(t.z, f.z, s[0].z);
-      s[0].w = fmaf(t.w, f.w, s[0].w);
-    }
-    float4 v;
-    v.x = (s[0].x + s[1].x) + (s[2].x + s[3].x);
-    v.y = (s[0].y + s[1].y) + (s[2].y + s[3].y);
-    v.z = (s[0].z + s[1].z) + (s[2].z + s[3].z);
-    v.w = (s[0].w + s[1].w) + (s[2].w + s[3].w);
-    for (int off = 16; off > 0; off >>= 1) {
-      v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
-      v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
-      v.z += __shfl_xor_sync(0xffffffffu, v.z, off);
-      v.w += __shfl_xor_sync(0xffffffffu, v.w, off);
-    }
-    if (lane == 0) out[a * Q + w] = v;
+    __syncthreads();
   }
 }
 
