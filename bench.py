@@ -178,6 +178,16 @@ def _stored_iterations():
     return next(i + 1 for i, v in enumerate(h) if v <= target), len(h)
 
 
+def max_over_ranks(values, device):
+    """Whole-job figures of a replicas run: the maximum over ranks of each value (the slowest
+    rank sets the job's time).  One all-reduce of a small vector; nothing else is exchanged."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -394,9 +404,7 @@ def run_ntf(args):
 
     value_s = ms / 1000.0
     if world > 1:
-        t = torch.tensor([value_s, e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        value_s, e2e_s = t.tolist()
+        value_s, e2e_s = max_over_ranks([value_s, e2e_s], "cuda")
     if rank != 0:
         return
 

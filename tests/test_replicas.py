@@ -1,0 +1,69 @@
+"""The multi-process path of bench.py on CPU (gloo, world size 2): replicas run independently
+and the job's figures are the maximum over ranks; the reference arm runs on rank 0 only."""
+import importlib.util
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    bench = _bench()
+    w, r, local = bench._dist()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # per-rank time and end-to-end time of a replica; the job's are the maxima
+        got = bench.max_over_ranks([1.0 + rank, 10.0 - rank], "cpu")
+        out.put((rank, (w, r, local), got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, (w, r, local), got in res:
+        assert (w, r, local) == (2, rank, rank)
+        assert got == [2.0, 10.0]
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    bench = _bench()
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+
+    class Args:
+        gpus, steps, warmup = 2, 1, 0
+
+    called = []
+    monkeypatch.setattr(bench, "_workload", lambda seed: called.append(seed))
+    bench.run_reference(Args())
+    assert called == [] and capsys.readouterr().out == ""
