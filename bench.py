@@ -86,7 +86,8 @@ def _traffic_record(kernel: str):
 
 
 class ClockSampler:
-    """nvidia-smi sampling (200 ms) while the timed region runs."""
+    """nvidia-smi sampling (every 20 ms) while the timed region runs; entering waits until the
+    sampler is live, so that the samples fall inside the region."""
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -95,15 +96,20 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and self.proc.poll() is None and time.time() - t0 < 3.0:
+                time.sleep(0.005)
+            self.skip = len(self.lines)  # samples taken before the timed region
         except Exception:
             self.proc = None
         return self
@@ -123,7 +129,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # the samples taken inside the timed region (all of them if it was shorter than the
+        # sampling period)
+        for ln in (self.lines[self.skip:] if len(self.lines) > self.skip else self.lines):
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) != 6:
                 continue
