@@ -224,18 +224,23 @@ ntf_status trace_end(ntf_ctx* c, int i, cudaStream_t st) {
   return record_any(c->tr_ev[2 * i + 1], st);
 }
 
-// T_R[P_R, R] = X[P_R, Q_R] * KR(factors s_R..N-1), on stream st
-ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st) {
+// T_R[P_R, R] = X[P_R, Q_R] * KR(factors s_R..N-1), on stream st (table_ready: the split
+// table was written by the last factor's rows kernel)
+ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st,
+                          bool table_ready = false) {
   const Group g = make_group(c, c->s_R, c->N - c->s_R, F);
   if (c->un.on) {
-    NTF_CUDA(ntf::launch_kr_split(g, c->un, c->R, c->Wu, st));
+    if (!table_ready) {
+      NTF_CUDA(ntf::launch_kr_split(g, c->un, c->R, c->Wu, st));
+      c->launches += 1;
+    }
     const int chunks = c->un.args.chunks;
     float* out = chunks > 1 ? c->partial : dst;
     NTF_TRY(prof_mark(c, 0, 0, st));
     NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, c->umma_sched, &c->d_ctrl->stop,
                               st));
     NTF_TRY(prof_mark(c, 0, 1, st));
-    c->launches += 2;
+    c->launches += 1;
     if (chunks > 1) {
       NTF_CUDA(ntf::launch_sum_splits(c->partial, chunks, c->P_R * c->R, dst, st));
       c->launches += 1;
@@ -255,18 +260,23 @@ ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStr
   return NTF_OK;
 }
 
-// T_L[Q_L, R] = X[P_L, Q_L]^T * KR(factors 0..s_L-1), on stream st
-ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st) {
+// T_L[Q_L, R] = X[P_L, Q_L]^T * KR(factors 0..s_L-1), on stream st (table_ready: the split
+// table was written by factor 0's rows kernel)
+ntf_status contract_left(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st,
+                         bool table_ready = false) {
   const Group g = make_group(c, 0, c->s_L, F);
   if (c->ut.on) {
-    NTF_CUDA(ntf::launch_kr_split(g, c->ut, c->R, c->Wu_b, st));
+    if (!table_ready) {
+      NTF_CUDA(ntf::launch_kr_split(g, c->ut, c->R, c->Wu_b, st));
+      c->launches += 1;
+    }
     const int chunks = c->ut.args.chunks;
     float* out = chunks > 1 ? c->partial_b : dst;
     NTF_TRY(prof_mark(c, 1, 0, st));
     NTF_CUDA(ntf::launch_umma(c->ut, out, &c->d_ctrl->status, c->umma_sched + 2,
                               &c->d_ctrl->stop, st));
     NTF_TRY(prof_mark(c, 1, 1, st));
-    c->launches += 2;
+    c->launches += 1;
     if (chunks > 1) {
       NTF_CUDA(ntf::launch_sum_splits(c->partial_b, chunks, c->Q_L * c->R, dst, st));
       c->launches += 1;
@@ -387,10 +397,11 @@ ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float*
 }
 
 // Factor 0's MTTKRP: the first contraction (T_R) and its second tree level, on stream st.
-ntf_status enqueue_lead(ntf_ctx* c, const float* const* src, cudaStream_t st, int sid) {
+ntf_status enqueue_lead(ntf_ctx* c, const float* const* src, cudaStream_t st, int sid,
+                        bool table_ready = false) {
   const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
   int t = trace_begin(c, "contract_right", 0, sid, st);
-  NTF_TRY(contract_right(c, src, const_cast<float*>(T), st));
+  NTF_TRY(contract_right(c, src, const_cast<float*>(T), st, table_ready));
   NTF_TRY(trace_end(c, t, st));
   t = trace_begin(c, "mttkrp_level2", 0, sid, st);
   NTF_TRY(finish_mode(c, 0, T, src, c->Mbuf, st));
@@ -434,6 +445,18 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
   for (int m = 0; m < c->N; ++m) {
     ntf::UpdateCall u = make_call(c, m, c->Mbuf, A[m], At[m], Y[m], m == c->N - 1);
     if (m + 1 == c->N) u.snap = c->d_snap;     // the sweep's outcome and stopping decision
+    // A contraction whose Khatri-Rao operand is this factor alone (3-way tensors: the second
+    // contraction after factor 0, the next sweep's first after the last factor) takes its
+    // split table from this factor's rows kernel instead of a separate launch.
+    const ntf::UmmaPlan* tp = m == 0 && c->s_L == 1 && c->ut.on ? &c->ut
+                              : m + 1 == c->N && c->N - c->s_R == 1 && c->un.on ? &c->un
+                                                                                : nullptr;
+    if (tp) {
+      u.wsplit = tp == &c->ut ? c->Wu_b : c->Wu;
+      u.ws_kpad = tp->K_pad;
+      u.ws_n = tp->N;
+      u.ws_bf16 = !tp->f32;
+    }
     const bool fused = ntf::update_fused(u);  // the rows kernel reduces by itself
     if (m > 0) NTF_CUDA(cudaStreamWaitEvent(sa, c->ev_post[m], 0));
     if (c->ws && c->ws_now) {
@@ -451,7 +474,7 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
       // any stream waits for it in this sweep)
       NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_rows[m], 0));
       t = trace_begin(c, "contract_left", c->s_R, 1, sb);
-      NTF_TRY(contract_left(c, src, c->TL, sb));
+      NTF_TRY(contract_left(c, src, c->TL, sb, m == 0 && c->s_L == 1 && c->ut.on));
       NTF_TRY(trace_end(c, t, sb));
       NTF_CUDA(cudaEventRecord(c->ev_tl, sb));
     }
@@ -459,7 +482,7 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
       // B: the next sweep's factor-0 MTTKRP (needs the last factor updated; T_R and the
       // MTTKRP buffer are free once this factor's rows have run)
       NTF_CUDA(cudaStreamWaitEvent(sb, c->ev_rows[m], 0));
-      NTF_TRY(enqueue_lead(c, src, sb, 1));
+      NTF_TRY(enqueue_lead(c, src, sb, 1, c->N - c->s_R == 1 && c->un.on));
     }
     // A: this factor's reduction, then the next factor's coefficient system (after the last
     // factor, factor 0's for the next sweep)
@@ -698,6 +721,11 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   if (e == cudaSuccess && p->contraction != NTF_CONTRACT_SIMT) {
     e = alloc(&c->Wu, ntf::umma_wsplit_bytes(c->Q_R, R, dtype));
     if (e == cudaSuccess) e = alloc(&c->Wu_b, ntf::umma_wsplit_bytes(c->P_L, R, dtype));
+    // zero padding (a rows kernel that writes a table writes only its entries)
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(c->Wu, 0, ntf::umma_wsplit_bytes(c->Q_R, R, dtype), c->st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(c->Wu_b, 0, ntf::umma_wsplit_bytes(c->P_L, R, dtype), c->st);
     if (e == cudaSuccess) {
       const bool okn = ntf::umma_plan(&c->un, false, dtype, d_tensor, c->P_R, c->Q_R, R, c->Wu,
                                       c->num_sms);

@@ -62,9 +62,7 @@ __global__ void k_kr_table(Group g, int64_t K, int R, int RP, int64_t n, float* 
 }
 
 // Split Khatri-Rao table of the tensor-core contractions: [splits * N rows][K_pad], K
-// contiguous; row s * N + r holds part s of column r.  BF16: W = w1 + w2 + w3 with
-// w1 = bf16(W), w2 = bf16(W - w1), w3 = bf16(W - w1 - w2) (each remainder is exact in FP32).
-// FP32: W = wh + wl, wh = W truncated to TF32, wl = W - wh (exact).
+// contiguous; row s * N + r holds part s of column r (split_store).
 template <bool kBF16>
 __global__ void k_kr_split(Group g, int64_t K, int R, int N, int64_t K_pad, void* __restrict__ W) {
   const int64_t n = static_cast<int64_t>(N) * K_pad;
@@ -73,21 +71,7 @@ __global__ void k_kr_split(Group g, int64_t K, int R, int N, int64_t K_pad, void
     const int r = static_cast<int>(idx / K_pad);
     const int64_t q = idx % K_pad;
     const float w = (q < K && r < R) ? kr_entry(g, q, r, R) : 0.0f;
-    if constexpr (kBF16) {
-      __nv_bfloat16* o = static_cast<__nv_bfloat16*>(W);
-      const __nv_bfloat16 b1 = __float2bfloat16_rn(w);
-      const float r1 = w - __bfloat162float(b1);
-      const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
-      const float r2 = r1 - __bfloat162float(b2);
-      o[idx] = b1;
-      o[n + idx] = b2;
-      o[2 * n + idx] = __float2bfloat16_rn(r2);
-    } else {
-      float* o = static_cast<float*>(W);
-      const float hi = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
-      o[idx] = hi;
-      o[n + idx] = w - hi;
-    }
+    split_store(W, n, idx, w, kBF16);
   }
 }
 

@@ -12,6 +12,29 @@
 namespace ntf {
 
 constexpr int kMaxOrder = 4;
+
+// Entry idx of a split Khatri-Rao table of the tensor-core contractions (parts n apart):
+// BF16, W = w1 + w2 + w3 with w1 = bf16(W), w2 = bf16(W - w1), w3 = bf16(W - w1 - w2) (each
+// remainder exact in FP32); FP32 (TF32 operands), W = wh + wl, wh = W truncated to TF32,
+// wl = W - wh (exact).
+__device__ __forceinline__ void split_store(void* W, int64_t n, int64_t idx, float w,
+                                            bool bf16) {
+  if (bf16) {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(W);
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(w);
+    const float r1 = w - __bfloat162float(b1);
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b2);
+    o[idx] = b1;
+    o[n + idx] = b2;
+    o[2 * n + idx] = __float2bfloat16_rn(r2);
+  } else {
+    float* o = static_cast<float*>(W);
+    const float hi = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+    o[idx] = hi;
+    o[n + idx] = w - hi;
+  }
+}
 constexpr int kMaxRank = 64;
 constexpr int kNumSM = 152;  // used only to size grids; the real count is queried at create
 
@@ -173,6 +196,12 @@ struct UpdateCall {
   double* scal_part;
   double* gram_out;
   SweepSnap* snap;  // a sweep of ntf_run: its outcome slots (host-mapped), else null
+  // the split Khatri-Rao table of the contraction that this factor alone forms (3-way
+  // tensors), written by the rows kernel from the new rows; null: none
+  void* wsplit;
+  int64_t ws_kpad;  // table row length
+  int ws_n;         // rows per part
+  bool ws_bf16;
   int64_t I;
   int N, mode, R, inner, rho_policy;
   bool kr_aux, want_fit;

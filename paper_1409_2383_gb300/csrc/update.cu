@@ -57,6 +57,9 @@ struct UpdArgs {
   double* scal_part;    // [blocks, kScal]
   double* gram_out;     // [R, R] stored Gram of this factor
   SweepSnap* snap;      // a sweep of ntf_run: its outcome slots (host-mapped), else null
+  void* wsplit;         // split Khatri-Rao table to write from the new rows (or null)
+  int64_t ws_kpad;
+  int ws_n, ws_bf16;
   int64_t I;
   int N, mode, R, inner, rho_policy, kr_aux, want_fit;
   int fused;            // rows kernel also reduces (last CTA)
@@ -363,6 +366,9 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
     part[4] = static_cast<float>(y * y);
     // the factor that feeds the next Khatri-Rao products, as stored (FP32)
     f = a.kr_aux ? ft : fx;
+    if (a.wsplit && h)  // its entry (row, lane) of the next contraction's split table
+      split_store(a.wsplit, static_cast<int64_t>(a.ws_n) * a.ws_kpad,
+                  static_cast<int64_t>(lane) * a.ws_kpad + row, f, a.ws_bf16);
     if (a.want_fit) {
       part[5] = static_cast<float>(m) * f;
       float g = 0.0f;  // (G f)_j with the FP32 coefficient matrix
@@ -468,6 +474,11 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
     const float f0 = a.kr_aux ? ft0 : fx0, f1 = a.kr_aux ? ft1 : fx1;
     if (h0) fr[j0] = f0;
     if (h1) fr[j1] = f1;
+    if (a.wsplit) {  // entries (row, j) of the next contraction's split table
+      const int64_t nt = static_cast<int64_t>(a.ws_n) * a.ws_kpad;
+      if (h0) split_store(a.wsplit, nt, static_cast<int64_t>(j0) * a.ws_kpad + row, f0, a.ws_bf16);
+      if (h1) split_store(a.wsplit, nt, static_cast<int64_t>(j1) * a.ws_kpad + row, f1, a.ws_bf16);
+    }
     if (a.want_fit) {
       part[5] = static_cast<float>(m0) * f0 + static_cast<float>(m1) * f1;
       __syncwarp();
@@ -720,6 +731,10 @@ UpdArgs make_args(const UpdateCall& u) {
   a.scal_part = u.scal_part;
   a.gram_out = u.gram_out;
   a.snap = u.snap;
+  a.wsplit = u.wsplit;
+  a.ws_kpad = u.ws_kpad;
+  a.ws_n = u.ws_n;
+  a.ws_bf16 = u.ws_bf16 ? 1 : 0;
   a.I = u.I;
   a.N = u.N;
   a.mode = u.mode;
