@@ -280,17 +280,41 @@ __global__ void k_post_slow4(const float4* __restrict__ T, int64_t Ia, int64_t I
   if (t == 0) count[blockIdx.x] = 0;
 }
 
-// ||X||^2 with FP64 accumulation; per-block partials then one block sums them in order.
+// ||X||^2: every thread sums the squares of its elements (16-byte loads where aligned) as a
+// pair of FP32 numbers hi + lo: each square is split exactly into p + e (p = v v rounded,
+// e = fma(v, v, -p)), p is added to hi by Knuth's two-sum, whose exact error goes to lo with
+// e (relative error of the pair about 2^-44); the block adds the threads' hi + lo in FP64 by
+// a fixed tree, and k_sum_doubles adds the blocks' in FP64 in a fixed order.  (FP64 per
+// element would run at this GPU's FP64 rate, a small fraction of its FP32 rate.)
 template <typename T>
 __global__ void k_norm2(const T* __restrict__ X, int64_t n, double* __restrict__ partial) {
   __shared__ double red[256];
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double v = static_cast<double>(Elem<T>::load1(X + i));
-    s = fma(v, v, s);
+  float hi = 0.0f, lo = 0.0f;
+  const auto add = [&](float v) {  // (rounded operations that the compiler may not fuse)
+    const float p = __fmul_rn(v, v);
+    const float e = fmaf(v, v, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+    hi = s;
+  };
+  constexpr int kV = Elem<T>::kPer16;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  int64_t done = 0;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    const int64_t nv = n / kV;
+    const uint4* X4 = reinterpret_cast<const uint4*>(X);
+    for (int64_t i = tid; i < nv; i += stride) {
+      float f[kV];
+      Elem<T>::unpack16(__ldg(X4 + i), f);
+#pragma unroll
+      for (int u = 0; u < kV; ++u) add(f[u]);
+    }
+    done = nv * kV;
   }
-  red[threadIdx.x] = s;
+  for (int64_t i = done + tid; i < n; i += stride) add(Elem<T>::load1(X + i));
+  red[threadIdx.x] = static_cast<double>(hi) + static_cast<double>(lo);
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -299,12 +323,14 @@ __global__ void k_norm2(const T* __restrict__ X, int64_t n, double* __restrict__
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// out = sum of v[0..n): one warp, lane l adds v[l], v[l + 32], ..., then a fixed butterfly.
 __global__ void k_sum_doubles(const double* __restrict__ v, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += v[i];
-    *out = s;
-  }
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += v[i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) *out = s;
 }
 
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
