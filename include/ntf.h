@@ -305,7 +305,11 @@ ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int rank, int dtyp
                               const void* d_tensor, int mode, const float* const* d_factors,
                               float* d_M, void* stream);
 
-/* FP32 -> BF16 storage conversion (round to nearest even), n elements, on `stream`. */
+/* FP32 -> BF16 storage conversion (round to nearest even), n elements, on `stream`.  d_out:
+ * device memory.  d_in: device memory, or page-locked host memory that the device addresses
+ * directly (cudaHostAlloc / cudaMallocHost under unified addressing): the kernel then reads
+ * it over the host link, so that the copy to the device and the conversion are one pass that
+ * writes half the bytes. */
 ntf_status ntf_to_bf16(const float* d_in, uint16_t* d_out, int64_t n, void* stream);
 
 const char* ntf_status_string(ntf_status s);

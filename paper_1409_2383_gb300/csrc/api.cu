@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -39,7 +40,9 @@ struct ntf_ctx {
   unsigned* post_count = nullptr;  // per-b-block counters of the vectorised slow level
   unsigned* umma_sched = nullptr;  // [4] work counters of the two tensor-core contractions
   int64_t post_count_right = 0;    // offset of the right group's counters
-  // workspace
+  // workspace: every device buffer below is carved from arena[0] (sized before the
+  // tensor-core plans) or arena[1] (the partial sums, sized by the plans)
+  void* arena[2] = {nullptr, nullptr};
   float* partial = nullptr;      // partial sums of the first contraction and of the posts
   float* partial_b = nullptr;    // partial sums of the second contraction (its own stream)
   float* TR = nullptr;           // [P_R, R]
@@ -511,6 +514,40 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
   return NTF_OK;
 }
 
+// Page-locked, device-mapped control blocks (the host mirror of Ctrl followed by the two
+// sweep-outcome slots): allocating and freeing page-locked memory is slow, so blocks of
+// destroyed contexts are kept for the next ones.
+constexpr size_t kPinnedBytes =
+    ((sizeof(Ctrl) + 63) / 64) * 64 + 2 * sizeof(ntf::SweepSnap);
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+
+cudaError_t pinned_acquire(void** p) {
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaHostAlloc(p, kPinnedBytes, cudaHostAllocMapped);
+}
+void pinned_release(void* p) {
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.push_back(p);
+}
+
+// Offsets of the buffers carved from one arena (256-byte aligned).
+struct Carver {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (std::max<size_t>(bytes, 16) + 255) / 256 * 256;
+    return o;
+  }
+};
+
 // The profiling event records of a recorded sweep, so that each replay can be given the
 // event set of its parity.
 ntf_status find_prof_nodes(ntf_ctx* c, cudaGraph_t gr, ntf_ctx::SweepGraph& g) {
@@ -568,28 +605,9 @@ void free_ctx(ntf_ctx* c) {
   if (c->tr_origin) cudaEventDestroy(c->tr_origin);
   for (cudaEvent_t e : c->tr_ev)
     if (e) cudaEventDestroy(e);
-  cudaFree(c->partial);
-  cudaFree(c->post_count);
-  cudaFree(c->umma_sched);
-  cudaFree(c->TR);
-  cudaFree(c->TL);
-  cudaFree(c->W);
-  cudaFree(c->W_b);
-  cudaFree(c->Wu);
-  cudaFree(c->Wu_b);
-  cudaFree(c->partial_b);
-  cudaFree(c->Mbuf);
-  cudaFree(c->grams);
-  cudaFree(c->grams_tmp);
-  cudaFree(c->chol);
-  cudaFree(c->sys);
-  cudaFree(c->gram_part);
-  cudaFree(c->scal_part);
-  cudaFree(c->fit_part);
-  cudaFree(c->dpart);
-  cudaFree(c->d_ctrl);
-  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
-  if (c->h_snap) cudaFreeHost(c->h_snap);
+  cudaFree(c->arena[0]);
+  cudaFree(c->arena[1]);
+  if (c->h_ctrl) pinned_release(c->h_ctrl);
   for (cudaEvent_t e : c->ev_sweep)
     if (e) cudaEventDestroy(e);
   delete c;
@@ -709,23 +727,58 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   const int64_t w_rows = ntf::kr_rows_padded(c->Q_R), w_rows_b = ntf::kr_rows_padded(c->P_L);
   const int64_t RR = static_cast<int64_t>(R) * R;
   const int upd_blocks = ntf::update_blocks(c->max_dim);
-  auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
-    return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
-  };
-  e = cudaSuccess;
-  if (e == cudaSuccess) e = alloc((void**)&c->TR, c->P_R * R * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->TL, c->Q_L * R * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->W, w_rows * ntf::round_rp(R) * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->W_b, w_rows_b * ntf::round_rp(R) * sizeof(float));
+  // arena 0: every buffer whose size is known before the tensor-core plans (whose tensor maps
+  // need the split tables' addresses)
+  const bool tc = p->contraction != NTF_CONTRACT_SIMT;
+  const size_t wu_bytes = tc ? ntf::umma_wsplit_bytes(c->Q_R, R, dtype) : 0;
+  const size_t wub_bytes = tc ? ntf::umma_wsplit_bytes(c->P_L, R, dtype) : 0;
+  Carver a0;
+  const size_t oTR = a0.take(c->P_R * R * sizeof(float));
+  const size_t oTL = a0.take(c->Q_L * R * sizeof(float));
+  const size_t oW = a0.take(w_rows * ntf::round_rp(R) * sizeof(float));
+  const size_t oWb = a0.take(w_rows_b * ntf::round_rp(R) * sizeof(float));
+  const size_t oWu = a0.take(wu_bytes), oWub = a0.take(wub_bytes);
+  const size_t oPC = a0.take((post_counts + 1) * sizeof(unsigned));
+  const size_t oUS = a0.take(4 * sizeof(unsigned));
+  const size_t oM = a0.take(c->max_dim * R * sizeof(float));
+  const size_t oG = a0.take(order * RR * sizeof(double));
+  const size_t oGt = a0.take(order * RR * sizeof(double));
+  const size_t oCh = a0.take(order * RR * sizeof(double));
+  const size_t oSys = a0.take(ntf::update_sys_bytes(order, R));
+  const size_t oGp = a0.take(upd_blocks * RR * sizeof(double));
+  const size_t oSp = a0.take(upd_blocks * ntf::update_scalars() * sizeof(double));
+  const size_t oFp = a0.take(64 * sizeof(double));
+  const size_t oDp = a0.take(1024 * sizeof(double));
+  const size_t oCtl = a0.take(sizeof(Ctrl));
+  e = cudaMalloc(&c->arena[0], a0.off);
+  if (e == cudaSuccess) {
+    char* b = static_cast<char*>(c->arena[0]);
+    c->TR = reinterpret_cast<float*>(b + oTR);
+    c->TL = reinterpret_cast<float*>(b + oTL);
+    c->W = reinterpret_cast<float*>(b + oW);
+    c->W_b = reinterpret_cast<float*>(b + oWb);
+    if (tc) {
+      c->Wu = b + oWu;
+      c->Wu_b = b + oWub;
+    }
+    c->post_count = reinterpret_cast<unsigned*>(b + oPC);
+    c->umma_sched = reinterpret_cast<unsigned*>(b + oUS);
+    c->Mbuf = reinterpret_cast<float*>(b + oM);
+    c->grams = reinterpret_cast<double*>(b + oG);
+    c->grams_tmp = reinterpret_cast<double*>(b + oGt);
+    c->chol = reinterpret_cast<double*>(b + oCh);
+    c->sys = reinterpret_cast<double*>(b + oSys);
+    c->gram_part = reinterpret_cast<double*>(b + oGp);
+    c->scal_part = reinterpret_cast<double*>(b + oSp);
+    c->fit_part = reinterpret_cast<double*>(b + oFp);
+    c->dpart = reinterpret_cast<double*>(b + oDp);
+    c->d_ctrl = reinterpret_cast<Ctrl*>(b + oCtl);
+  }
   // tensor-core plans: the split tables must exist before the tensor maps are encoded
-  if (e == cudaSuccess && p->contraction != NTF_CONTRACT_SIMT) {
-    e = alloc(&c->Wu, ntf::umma_wsplit_bytes(c->Q_R, R, dtype));
-    if (e == cudaSuccess) e = alloc(&c->Wu_b, ntf::umma_wsplit_bytes(c->P_L, R, dtype));
+  if (e == cudaSuccess && tc) {
     // zero padding (a rows kernel that writes a table writes only its entries)
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(c->Wu, 0, ntf::umma_wsplit_bytes(c->Q_R, R, dtype), c->st);
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(c->Wu_b, 0, ntf::umma_wsplit_bytes(c->P_L, R, dtype), c->st);
+    e = cudaMemsetAsync(c->Wu, 0, wu_bytes, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->Wu_b, 0, wub_bytes, c->st);
     if (e == cudaSuccess) {
       const bool okn = ntf::umma_plan(&c->un, false, dtype, d_tensor, c->P_R, c->Q_R, R, c->Wu,
                                       c->num_sms);
@@ -742,13 +795,17 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
         part_b = std::max<int64_t>(part_b, c->ut.args.chunks * c->Q_L * R);
     }
   }
-  if (e == cudaSuccess) e = alloc((void**)&c->partial, part * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->post_count, (post_counts + 1) * sizeof(unsigned));
-  if (e == cudaSuccess) e = alloc((void**)&c->umma_sched, 4 * sizeof(unsigned));
+  // arena 1: the partial sums, sized by the plans
+  Carver a1;
+  const size_t oP = a1.take(part * sizeof(float)), oPb = a1.take(part_b * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->arena[1], a1.off);
+  if (e == cudaSuccess) {
+    c->partial = reinterpret_cast<float*>(static_cast<char*>(c->arena[1]) + oP);
+    c->partial_b = reinterpret_cast<float*>(static_cast<char*>(c->arena[1]) + oPb);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->umma_sched, 0, 4 * sizeof(unsigned), c->st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->post_count, 0, (post_counts + 1) * sizeof(unsigned), c->st);
-  if (e == cudaSuccess) e = alloc((void**)&c->partial_b, part_b * sizeof(float));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sC, cudaStreamNonBlocking);
   for (cudaEvent_t* ev : {&c->ev_start, &c->ev_tl, &c->ev_b, &c->ev_c})
@@ -759,21 +816,14 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red[m], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_post[m], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = alloc((void**)&c->Mbuf, c->max_dim * R * sizeof(float));
-  if (e == cudaSuccess) e = alloc((void**)&c->grams, order * RR * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->grams_tmp, order * RR * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->chol, order * RR * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->sys, ntf::update_sys_bytes(order, R));
-  if (e == cudaSuccess) e = alloc((void**)&c->gram_part, upd_blocks * RR * sizeof(double));
-  if (e == cudaSuccess)
-    e = alloc((void**)&c->scal_part, upd_blocks * ntf::update_scalars() * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->fit_part, 64 * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->dpart, 1024 * sizeof(double));
-  if (e == cudaSuccess) e = alloc((void**)&c->d_ctrl, sizeof(Ctrl));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_ctrl, sizeof(Ctrl));
-  if (e == cudaSuccess)
-    e = cudaHostAlloc((void**)&c->h_snap, 2 * sizeof(ntf::SweepSnap), cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->d_snap, c->h_snap, 0);
+  void* pin = nullptr;
+  if (e == cudaSuccess) e = pinned_acquire(&pin);
+  if (e == cudaSuccess) {
+    c->h_ctrl = static_cast<Ctrl*>(pin);
+    c->h_snap = reinterpret_cast<ntf::SweepSnap*>(static_cast<char*>(pin) +
+                                                  kPinnedBytes - 2 * sizeof(ntf::SweepSnap));
+    e = cudaHostGetDevicePointer((void**)&c->d_snap, c->h_snap, 0);
+  }
   for (cudaEvent_t& ev : c->ev_sweep)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -1168,7 +1218,19 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
 ntf_status ntf_to_bf16(const float* d_in, uint16_t* d_out, int64_t n, void* stream) {
   if (!d_in || !d_out || n < 0) return fail(NTF_ERR_INVALID_ARG, "bad argument");
   if (n == 0) return NTF_OK;
-  NTF_CUDA(ntf::launch_to_bf16(d_in, d_out, n, static_cast<cudaStream_t>(stream)));
+  // the input is read through its device address: device memory as it is, page-locked host
+  // memory through the address the device maps it at; anything else is refused
+  cudaPointerAttributes at{};
+  NTF_CUDA(cudaPointerGetAttributes(&at, d_in));
+  const float* src = d_in;
+  if (at.type == cudaMemoryTypeHost) {
+    if (!at.devicePointer)
+      return fail(NTF_ERR_INVALID_ARG, "host input is not mapped into the device address space");
+    src = static_cast<const float*>(at.devicePointer);
+  } else if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+    return fail(NTF_ERR_INVALID_ARG, "input is neither device memory nor page-locked host memory");
+  }
+  NTF_CUDA(ntf::launch_to_bf16(src, d_out, n, static_cast<cudaStream_t>(stream)));
   return NTF_OK;
 }
 

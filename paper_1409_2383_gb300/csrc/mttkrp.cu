@@ -333,11 +333,28 @@ __global__ void k_sum_doubles(const double* __restrict__ v, int n, double* __res
   if (lane == 0) *out = s;
 }
 
+// FP32 -> BF16, round to nearest even.  16-byte loads and 8-byte stores when both arrays
+// allow (the input may be host memory that the device reads over the host link: wide reads
+// matter there), then the tail one by one.
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
                           int64_t n) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    out[i] = __float2bfloat16_rn(in[i]);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  int64_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(in) & 15) | (reinterpret_cast<uintptr_t>(out) & 7)) == 0) {
+    const int64_t n4 = n / 4;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    uint2* out4 = reinterpret_cast<uint2*>(out);
+    for (int64_t i = tid; i < n4; i += stride) {
+      const float4 v = in4[i];
+      const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+      out4[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
+                           *reinterpret_cast<const uint32_t*>(&b));
+    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + tid; i < n; i += stride) out[i] = __float2bfloat16_rn(in[i]);
 }
 
 }  // namespace

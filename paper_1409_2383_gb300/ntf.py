@@ -171,10 +171,14 @@ def _mat(t: torch.Tensor, rows: int, R: int, name: str, dtype=torch.float32) -> 
 
 
 def to_bf16(x: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
-    """FP32 -> BF16 (round to nearest even) with the library's conversion kernel."""
-    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
-        raise ValueError("to_bf16 needs a contiguous CUDA float32 tensor")
-    out = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    """FP32 -> BF16 (round to nearest even) with the library's conversion kernel.  x: a CUDA
+    tensor, or a page-locked (pinned) host tensor, which the kernel reads directly over the
+    host link (copy and conversion in one pass; the result is on the current CUDA device)."""
+    pinned = not x.is_cuda and x.is_pinned()
+    if x.dtype != torch.float32 or not (x.is_cuda or pinned) or not x.is_contiguous():
+        raise ValueError("to_bf16 needs a contiguous float32 tensor on the GPU or pinned")
+    dev = x.device if x.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty(x.shape, dtype=torch.bfloat16, device=dev)
     _check(lib().ntf_to_bf16(_ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)))
     return out
 

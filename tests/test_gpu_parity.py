@@ -85,6 +85,21 @@ def test_mttkrp_all_modes(ntf, dims, R, storage):
             assert rel(M, want) <= TOL, (n, rel(M, want))
 
 
+@pytest.mark.parametrize("n", [1 << 20, 1000003])
+def test_to_bf16_from_pinned_host_memory(ntf, n):
+    """The conversion reads page-locked host memory directly (copy and conversion in one
+    pass): the result equals the conversion of the same values in device memory, bit for bit,
+    also for a length that leaves a tail and an input that starts off the 16-byte grid."""
+    x = torch.randn(n + 1, dtype=torch.float32).pin_memory()
+    for src in (x[:n], x[1:]):
+        got = ntf.to_bf16(src)
+        want = ntf.to_bf16(src.cuda())
+        torch.cuda.synchronize()
+        assert got.is_cuda and torch.equal(got.view(torch.int16), want.view(torch.int16))
+    with pytest.raises(ValueError):
+        ntf.to_bf16(torch.randn(16))  # pageable host memory is refused
+
+
 def test_to_bf16_matches_round_to_nearest_even(ntf):
     rng = np.random.default_rng(3)
     x = (rng.standard_normal(100003) * 10.0 ** rng.integers(-20, 20, 100003)).astype(np.float32)
