@@ -215,6 +215,21 @@ __global__ void k_post_slow4(const float4* __restrict__ T, int64_t Ia, int64_t I
   for (int u = 0; u < 4; ++u) s[u] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (b < Ib) {
     int64_t a = a_beg;
+    for (; a + 7 < a_end; a += 8) {  // eight rows' loads in flight
+      float4 tv[8], fv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        tv[u] = T[((a + u) * Ib + b) * Q + q];
+        fv[u] = __ldg(F + (a + u) * Q + q);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        s[u & 3].x = fmaf(tv[u].x, fv[u].x, s[u & 3].x);
+        s[u & 3].y = fmaf(tv[u].y, fv[u].y, s[u & 3].y);
+        s[u & 3].z = fmaf(tv[u].z, fv[u].z, s[u & 3].z);
+        s[u & 3].w = fmaf(tv[u].w, fv[u].w, s[u & 3].w);
+      }
+    }
     for (; a + 3 < a_end; a += 4) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
