@@ -142,14 +142,15 @@ def test_training_reduces_loss(ntf):
     net.close()
 
 
-def test_warm_start_judge_in_factor_update(ntf):
+@pytest.mark.parametrize("H", [32, 320])  # the fused inference kernels; the GEMM path (H > 256)
+def test_warm_start_judge_in_factor_update(ntf, H):
     """Warm start of one factor update: every row starts from the network's candidate if it
     has both the smaller row objective and the smaller KKT residual, else from the
     carried-over state (replayed in FP64 with the oracle network and oracle judge); the final
     state is the oracle update from that start."""
     from paper_1409_2383_gb300 import warmstart
     rng = np.random.default_rng(9)
-    dims, R, H = (40, 30, 20), 4, 32
+    dims, R = (40, 30, 20), 4
     X = rng.random(dims).astype(np.float32)
     fs = [rng.random((d, R)).astype(np.float32) for d in dims]
     flat = warmstart.init_params(R, H, seed=2)

@@ -309,14 +309,16 @@ def test_stopping_rule_and_target(ntf):
     assert rs["reached_target"] == 1 and rs["rel_err"] <= 0.2 and rs["iters"] < 400
 
 
-@pytest.mark.parametrize("check_every,rule", [(1, "target"), (3, "target"), (1, "residual"),
-                                               (2, "residual")])
-def test_run_stops_at_the_first_sweep_that_meets_the_rule(ntf, check_every, rule):
+@pytest.mark.parametrize("dims,R,check_every,rule", [
+    ((40, 36, 32), 4, 1, "target"), ((40, 36, 32), 4, 3, "target"),
+    ((40, 36, 32), 4, 1, "residual"), ((40, 36, 32), 4, 2, "residual"),
+    # the last factor's partial sums too many for the rows kernel: separate reduction kernel
+    ((24, 20, 480), 8, 1, "target"), ((24, 20, 480), 8, 3, "target")])
+def test_run_stops_at_the_first_sweep_that_meets_the_rule(ntf, dims, R, check_every, rule):
     """The host enqueues a sweep before it reads the previous sweep's outcome; the sweep after
     the one that met the stopping rule must leave the state untouched.  The stopped run's state
     equals, bit for bit, that of a run of exactly as many sweeps without a rule, and the rule's
     value at that sweep matches."""
-    dims, R = (40, 36, 32), 4
     X, fs, init = synth.workload(dims, R, seed=3, snr_db=20.0)
     eps = 1e-3 if rule == "residual" else 0.0
     p = ntf.default_params(paper_mode=False, eps_abs=eps, eps_rel=eps)
