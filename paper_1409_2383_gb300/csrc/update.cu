@@ -13,6 +13,13 @@
 //  k_update_reduce  fixed-order sums of the partials: the stored Gram of the factor, the
 //                   residuals, the penalty rule (Sec. III-D) and, for the last factor of a
 //                   sweep, the relative error ||X||^2 - 2<M, F> + sum_i f_i^T G f_i.
+//
+// Inside a sweep the reduction and the next factor's coefficient system are one kernel
+// (k_update_reduce_system: its last CTA builds the system); a small set of partials is
+// reduced by the rows kernel's own last CTA instead.  The last factor's reduction also
+// evaluates the run's stopping rules and writes the sweep's outcome; the rows kernel of a
+// factor that alone forms a contraction's Khatri-Rao operand writes that contraction's split
+// table from the new rows.
 #include <cmath>
 
 #include "ntf_internal.cuh"
