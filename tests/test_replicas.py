@@ -67,3 +67,20 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(bench, "_workload", lambda seed: called.append(seed))
     bench.run_reference(Args())
     assert called == [] and capsys.readouterr().out == ""
+
+
+def test_clock_summary_reads_the_samples_of_the_timed_region():
+    bench = _bench()
+    s = bench.ClockSampler(0)
+    s.lines = ["1965, 2070, Not Active, Not Active, Not Active, Not Active",   # before the region
+               "2070, 2070, Not Active, Not Active, Not Active, Active",
+               "2055, 2070, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s.skip = 1
+    got = s.summary()
+    assert got["samples"] == 2 and got["sm_mhz"] == 2062.5 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"]
+    s.lines, s.skip = s.lines[:1], 1           # a region shorter than the sampling period
+    assert s.summary()["samples"] == 1
+    s.lines = []
+    assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
