@@ -172,7 +172,13 @@ ntf_status ntf_fit_from_mttkrp(ntf_ctx* ctx, const float* d_M_last, const float*
  * iterations) or max_outer iterations.  Grams are (re)initialised from the Khatri-Rao
  * source factors first.  rfe_hist (host, may be NULL, length max_outer) receives the error
  * after every checked iteration (NaN elsewhere).  Returns NTF_ERR_NOT_CONVERGED if
- * max_outer was reached without meeting a requested criterion (out is still filled). */
+ * max_outer was reached without meeting a requested criterion (out is still filled).
+ * The stopping rules are evaluated on the device; the call enqueues the next iteration
+ * before it reads the previous one's outcome, so one iteration more may be enqueued than
+ * run: its kernels find the run stopped and leave the state as it is (the state, iteration
+ * count and error are those of stopping at the first checked iteration that met a rule).
+ * The call may return while that iteration's kernels still drain on the context's stream;
+ * work enqueued on that stream afterwards (or ntf_sync) is ordered after them. */
 ntf_status ntf_run(ntf_ctx* ctx, float* const* d_A, float* const* d_At, float* const* d_Y,
                    int max_outer, double target_rfe, int check_every, double* rfe_hist,
                    ntf_run_stats* out);
