@@ -44,7 +44,6 @@ __global__ void k_system(const double* __restrict__ grams, int N, int mode, int 
                          int rho_policy, Ctrl* ctrl, double* __restrict__ H_out,
                          double* __restrict__ L_out) {
   __shared__ double A[kMaxRank * kMaxRank];
-  __shared__ double rho_s;
   __shared__ int fail;
   const int tid = threadIdx.x;
   const int RR = R * R;
@@ -64,7 +63,6 @@ __global__ void k_system(const double* __restrict__ grams, int N, int mode, int 
     } else {
       rho = ctrl->rho[mode];
     }
-    rho_s = rho;
     fail = !(rho > 0.0) || !isfinite(rho);
     for (int i = 0; i < R; ++i) A[i * R + i] += rho;
     ctrl->stats[mode][5] = rho;
