@@ -97,7 +97,6 @@ __global__ void k_system(const double* __restrict__ grams, int N, int mode, int 
     ctrl->bad[mode] = fail;
     if (fail) atomicOr(&ctrl->status, kStNotSpd);
   }
-  (void)rho_s;
 }
 
 constexpr int kFitThreads = 256;
