@@ -375,3 +375,20 @@ def factorize(X: np.ndarray, init: Sequence[np.ndarray], params: Params, max_ite
             converged = True
             break
     return st, hist, converged
+
+
+def factorize_with_restarts(X: np.ndarray, draws: Sequence[Sequence[np.ndarray]],
+                            params: Params, n_max: int):
+    """The restart strategy of Sec. V-A: run ADMoM for up to n_max outer iterations; if the
+    stopping test of Sec. III-C has not held by then, start again from the next random initial
+    point, until it converges.  The random initial points are inputs (draws[attempt], the
+    factors that init_state takes); the paper repeats without bound, here the attempts end
+    with the last draw.  Returns (State, history, converged, restarts) of the last attempt,
+    restarts = the number of attempts before it."""
+    if not draws:
+        raise ValueError("at least one initial point is needed")
+    for attempt, init in enumerate(draws):
+        st, hist, converged = factorize(X, init, params, n_max)
+        if converged:
+            break
+    return st, hist, converged, attempt
