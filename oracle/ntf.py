@@ -32,8 +32,9 @@ Where the paper is silent the readings are (each also listed in the design notes
   inner iterations is rho * (aux after - aux before the update);
 * reported factors are the non-negative auxiliaries.
 
-Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against brute
-force, closed forms, exhaustive NNLS, optimality conditions or the paper's printed values.
+Parity status: every function here is pinned by ``tests/test_oracle_*.py`` (the restart loop
+by ``tests/test_restarts.py``) against brute force, closed forms, exhaustive NNLS, optimality
+conditions or the paper's printed values.
 """
 from __future__ import annotations
 
