@@ -84,3 +84,47 @@ def test_clock_summary_reads_the_samples_of_the_timed_region():
     assert s.summary()["samples"] == 1
     s.lines = []
     assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def _slab_worker(rank, world, port, out):
+    """Sec. IV's block scheme on the oracle: each rank holds a slab of X along mode 1 and the
+    factors; its MTTKRP of modes 2 and 3 over the slab are partial sums, added across ranks by
+    one all-reduce; mode 1's rows are its own slab's."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from oracle import ntf as o
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(0)
+        dims, R = (10, 7, 6), 3
+        X = rng.random(dims)
+        F = [rng.random((d, R)) for d in dims]
+        lo, hi = rank * dims[0] // world, (rank + 1) * dims[0] // world
+        Fs = [F[0][lo:hi], F[1], F[2]]
+        got = []
+        for n in (1, 2):
+            part = torch.as_tensor(o.mttkrp(X[lo:hi], Fs, n))
+            dist.all_reduce(part)
+            got.append(part.numpy())
+        rows0 = o.mttkrp(X[lo:hi], Fs, 0)
+        want = [o.mttkrp(X, F, n) for n in (1, 2)]
+        out.put((rank, all(np.allclose(g, w, rtol=1e-12, atol=0) for g, w in zip(got, want)),
+                 np.allclose(rows0, o.mttkrp(X, F, 0)[lo:hi], rtol=1e-12, atol=0)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_slab_partitioned_mttkrp_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, True, True), (1, True, True)]
