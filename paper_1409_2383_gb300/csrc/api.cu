@@ -1100,6 +1100,12 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
                              cudaMemcpyHostToDevice, c->st));
     c->h_snap[0].sweep = c->h_snap[1].sweep = -1;
   }
+  // however the run ends (an error included), the flags go back to zero on the stream after
+  // its last sweep: kernels launched outside a run must not find it stopped
+  struct StopReset {
+    ntf_ctx* c;
+    ~StopReset() { (void)cudaMemsetAsync(&c->d_ctrl->stop, 0, 3 * sizeof(int), c->st); }
+  } stop_reset{c};
 
   // The sweep is recorded once as a CUDA graph (after one eager sweep has set every kernel
   // attribute) and replayed; it is re-recorded only if the state pointers change.  Sweeps
@@ -1206,8 +1212,6 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
     }
   }
   if (st_run == NTF_OK && unread >= 0) st_run = read_sweep(unread);
-  // the run is over: the sweep kernels must not skip outside it
-  NTF_CUDA(cudaMemsetAsync(&c->d_ctrl->stop, 0, 3 * sizeof(int), c->st));
   if (st_run != NTF_OK) return st_run;
   if (!done && (use_res || use_tgt)) result = NTF_ERR_NOT_CONVERGED;
   if (out) *out = rs;
