@@ -516,7 +516,8 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
 
 // Page-locked, device-mapped control blocks (the host mirror of Ctrl followed by the two
 // sweep-outcome slots): allocating and freeing page-locked memory is slow, so blocks of
-// destroyed contexts are kept for the next ones.
+// destroyed contexts are kept for the next ones (portable: a context on another device of
+// the process may take a block over).
 constexpr size_t kPinnedBytes =
     ((sizeof(Ctrl) + 63) / 64) * 64 + 2 * sizeof(ntf::SweepSnap);
 std::mutex g_pinned_mu;
@@ -531,7 +532,7 @@ cudaError_t pinned_acquire(void** p) {
       return cudaSuccess;
     }
   }
-  return cudaHostAlloc(p, kPinnedBytes, cudaHostAllocMapped);
+  return cudaHostAlloc(p, kPinnedBytes, cudaHostAllocMapped | cudaHostAllocPortable);
 }
 void pinned_release(void* p) {
   std::lock_guard<std::mutex> lock(g_pinned_mu);
