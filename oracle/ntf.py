@@ -14,16 +14,16 @@ or reordering beyond what the definition states:
   remaining mode varies fastest (W^(1) = A (C (.) B)^T);
 * the Khatri-Rao factor of mode n is F_N (.) ... (.) F_{n+1} (.) F_{n-1} (.) ... (.) F_1
   (Sec. II, App. A);
-* MTTKRP = explicit unfolding times explicit Khatri-Rao matrix (Sec. III-A, item 1);
-* the coefficient matrix via the Gram identity (Sec. III-A, item 2) and explicitly;
+* MTTKRP = explicit unfolding times explicit Khatri-Rao matrix (Sec. IV-A, item 1);
+* the coefficient matrix via the Gram identity (Sec. IV-A, item 2) and explicitly;
 * the per-factor update of eq. (ADMM_NTF_ALS_C), solved with LAPACK Cholesky, followed by
   the projection and dual ascent of eq. (ADMoM_NTF);
-* residuals and stopping test of Sec. III-C, penalty rule of Sec. III-D;
-* the relative factorization error of Sec. V-A by explicit reconstruction.
+* residuals and stopping test of Sec. IV-C, penalty rule of Sec. IV-D;
+* the relative factorization error of Sec. VI-A by explicit reconstruction.
 
 Where the paper is silent the readings are (each also listed in the design notes):
 * ``inner_iters`` L repeats the closed-form update / projection / dual step L times per
-  factor with the coefficient matrix fixed (the paper uses L = 1, Sec. III footnote);
+  factor with the coefficient matrix fixed (the paper uses L = 1, Sec. IV footnote);
 * ``kr_source`` chooses which factors feed the Khatri-Rao products: the unconstrained primal
   factors (the paper, eq. ADMM_NTF_ALS_C) or the non-negative auxiliaries;
 * ``rho_policy`` "adaptive" is the rule of eq. (varying_penalty_rule) applied once per outer
@@ -105,13 +105,13 @@ def reconstruct(factors: Sequence[np.ndarray]) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------------
-# Sec. III-A: MTTKRP and the coefficient matrix
+# Sec. IV-A: MTTKRP and the coefficient matrix
 # ----------------------------------------------------------------------------------------
 
 def mttkrp(X: np.ndarray, factors: Sequence[np.ndarray], n: int) -> np.ndarray:
     """M_n = X^(n) (Khatri-Rao of the other factors): explicit unfolding times explicit KR.
 
-    Sec. III-A item 1 (the term X^(1)(C (.) B) of eq. ADMM_NTF_ALS_C).
+    Sec. IV-A item 1 (the term X^(1)(C (.) B) of eq. ADMM_NTF_ALS_C).
     """
     return unfold(np.asarray(X, dtype=np.float64), n) @ kr_others(factors, n)
 
@@ -137,7 +137,7 @@ def coeff_matrix_explicit(factors: Sequence[np.ndarray], n: int) -> np.ndarray:
 
 
 def coeff_matrix(factors: Sequence[np.ndarray], n: int) -> np.ndarray:
-    """(KR)^T (KR) via the Hadamard-of-Grams identity of Sec. III-A item 2."""
+    """(KR)^T (KR) via the Hadamard-of-Grams identity of Sec. IV-A item 2."""
     G = None
     for m, F in enumerate(factors):
         if m == n:
@@ -160,16 +160,48 @@ class UpdateStats:
     rho: float
 
 
+def project_nonneg(V: np.ndarray) -> np.ndarray:
+    """Projection onto the non-negative matrices (eq. ADMoM_NTF): (V)_+."""
+    return np.maximum(V, 0.0)
+
+
+def project_nonneg_sparse(V: np.ndarray, c: int) -> np.ndarray:
+    """Projection onto the non-negative matrices with at most c nonzero entries (Sec. IV-E,
+    eq. g_new_def), by sorting.  Keeping entry v costs (max(v, 0) - v)^2 and zeroing it v^2,
+    so keeping it gains max(v, 0)^2: the projection keeps the c largest positive entries
+    (ties broken by the lower flat index) and zeroes the rest."""
+    if c < 0:
+        raise ValueError("c must be >= 0")
+    P = np.maximum(np.asarray(V, np.float64), 0.0)
+    flat = P.ravel()
+    if np.count_nonzero(flat) <= c:
+        return P
+    keep = np.argsort(-flat, kind="stable")[:c]
+    out = np.zeros_like(flat)
+    out[keep] = flat[keep]
+    return out.reshape(P.shape)
+
+
+def project_box(V: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    """Projection onto the box lo <= entry <= hi (Sec. IV-E, "box or other set
+    constraints"): entrywise clamp."""
+    if not lo <= hi:
+        raise ValueError("lo must be <= hi")
+    return np.clip(np.asarray(V, np.float64), lo, hi)
+
+
 def admm_factor_update(M: np.ndarray, G: np.ndarray, At: np.ndarray, Y: np.ndarray,
-                       rho: float, inner_iters: int = 1):
+                       rho: float, inner_iters: int = 1, project=project_nonneg):
     """Update one factor: L repetitions of
 
         A   = (M + rho At - Y) (G + rho I)^{-1}        (eq. ADMM_NTF_ALS_C)
         At  = (A + Y / rho)_+                          (eq. ADMoM_NTF, auxiliary)
         Y   = Y + rho (A - At)                         (eq. ADMoM_NTF, dual)
 
-    with G + rho I factored once by Cholesky (Sec. III-A item 2) and the common coefficient
-    matrix shared by all rows (App. B).  Returns (A, At, Y, UpdateStats).
+    with G + rho I factored once by Cholesky (Sec. IV-A item 2) and the common coefficient
+    matrix shared by all rows (App. B).  ``project`` replaces (.)_+ for the structural
+    constraints of Sec. IV-E (the only step that changes there).  Returns (A, At, Y,
+    UpdateStats).
     """
     if not rho > 0:
         raise ValueError("rho must be positive")
@@ -185,7 +217,7 @@ def admm_factor_update(M: np.ndarray, G: np.ndarray, At: np.ndarray, Y: np.ndarr
         rhs = M + rho * At_k - Y_k                               # I x R
         Z = scipy.linalg.solve_triangular(Lc, rhs.T, lower=True)
         A = scipy.linalg.solve_triangular(Lc.T, Z, lower=False).T
-        At_k = np.maximum(A + Y_k / rho, 0.0)
+        At_k = project(A + Y_k / rho)
         Y_k = Y_k + rho * (A - At_k)
     st = UpdateStats(
         primal_res=float(np.linalg.norm(A - At_k)),
@@ -205,7 +237,7 @@ def rho_trace(G: np.ndarray) -> float:
 
 def rho_adapt(rho: float, P: float, D: float, mu: float = 8.0, tau_incr: float = 4.0,
               tau_decr: float = 2.0) -> float:
-    """Penalty rule of eq. (varying_penalty_rule), Sec. III-D."""
+    """Penalty rule of eq. (varying_penalty_rule), Sec. IV-D."""
     if P > mu * D:
         return tau_incr * rho
     if D > mu * P:
@@ -221,11 +253,11 @@ def small_residuals(st: UpdateStats, rows: int, R: int, eps_abs: float, eps_rel:
 
 
 # ----------------------------------------------------------------------------------------
-# Sec. V-A: relative factorization error; Sec. III-B: KKT conditions
+# Sec. VI-A: relative factorization error; Sec. IV-B: KKT conditions
 # ----------------------------------------------------------------------------------------
 
 def rfe(X: np.ndarray, factors: Sequence[np.ndarray]) -> float:
-    """||X - [F_1..F_N]||_F / ||X||_F by explicit reconstruction (Sec. V-A)."""
+    """||X - [F_1..F_N]||_F / ||X||_F by explicit reconstruction (Sec. VI-A)."""
     X = np.asarray(X, np.float64)
     return float(np.linalg.norm(X - reconstruct(factors)) / np.linalg.norm(X))
 
@@ -318,7 +350,7 @@ class State:
 
 
 def init_state(init: Sequence[np.ndarray], params: Params) -> State:
-    """Initial point of Sec. V-A (paper mode) or the all-uniform start (aux mode).
+    """Initial point of Sec. VI-A (paper mode) or the all-uniform start (aux mode).
 
     Paper mode: primal factors take the given non-negative random values (only those of
     modes 2..N are used), auxiliaries and duals are zero.  Aux mode: primal = aux = the
@@ -360,7 +392,7 @@ def outer_iteration(X: np.ndarray, st: State, params: Params):
 
 def factorize(X: np.ndarray, init: Sequence[np.ndarray], params: Params, max_iters: int,
               stop_on_residuals: bool = True, record_rfe: bool = True):
-    """Run outer iterations until the stopping test (Sec. III-C) holds for every factor or
+    """Run outer iterations until the stopping test (Sec. IV-C) holds for every factor or
     ``max_iters`` is reached.  Returns (State, history) with history a list of
     (iteration, rfe) pairs and the convergence flag."""
     st = init_state(init, params)
@@ -380,8 +412,8 @@ def factorize(X: np.ndarray, init: Sequence[np.ndarray], params: Params, max_ite
 
 def factorize_with_restarts(X: np.ndarray, draws: Sequence[Sequence[np.ndarray]],
                             params: Params, n_max: int):
-    """The restart strategy of Sec. V-A: run ADMoM for up to n_max outer iterations; if the
-    stopping test of Sec. III-C has not held by then, start again from the next random initial
+    """The restart strategy of Sec. VI-A: run ADMoM for up to n_max outer iterations; if the
+    stopping test of Sec. IV-C has not held by then, start again from the next random initial
     point, until it converges.  The random initial points are inputs (draws[attempt], the
     factors that init_state takes); the paper repeats without bound, here the attempts end
     with the last draw.  Returns (State, history, converged, restarts) of the last attempt,
