@@ -5,13 +5,13 @@
  * via Alternating Direction Method of Multipliers" (arXiv 1409.2383).  For an N-way dense
  * tensor X (N = 3 or 4) and rank R the library computes, per factor n,
  *
- *   M_n = X^(n) (Khatri-Rao of the other factors)               Sec. III-A item 1
- *   G_n = Hadamard product of the other factors' Grams         Sec. III-A item 2
+ *   M_n = X^(n) (Khatri-Rao of the other factors)               Sec. IV-A item 1
+ *   G_n = Hadamard product of the other factors' Grams         Sec. IV-A item 2
  *   A   = (M_n + rho At - Y) (G_n + rho I)^{-1}                 eq. (ADMM_NTF_ALS_C)
  *   At  = (A + Y / rho)_+ ,  Y = Y + rho (A - At)               eq. (ADMoM_NTF)
  *
- * the residuals of Sec. III-C, the penalty rule of Sec. III-D and the relative
- * factorization error of Sec. V-A.
+ * the residuals of Sec. IV-C, the penalty rule of Sec. IV-D and the relative
+ * factorization error of Sec. VI-A.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -82,15 +82,15 @@ typedef struct {
   int kr_source;     /* ntf_kr_source                                                    */
   int rho_policy;    /* ntf_rho_policy                                                   */
   double rho0;       /* initial penalty (paper: 1)                                       */
-  double mu;         /* penalty rule parameters (paper: 8, 4, 2), Sec. V-A               */
+  double mu;         /* penalty rule parameters (paper: 8, 4, 2), Sec. VI-A               */
   double tau_incr;
   double tau_decr;
-  double eps_abs;    /* stopping tolerances of Sec. III-C (paper: 1e-4, 1e-4)            */
+  double eps_abs;    /* stopping tolerances of Sec. IV-C (paper: 1e-4, 1e-4)            */
   double eps_rel;
   int contraction;   /* ntf_contraction (default AUTO)                                   */
 } ntf_params;
 
-/* Per-factor residuals of one update (Sec. III-C), all Frobenius norms. */
+/* Per-factor residuals of one update (Sec. IV-C), all Frobenius norms. */
 typedef struct {
   double primal_res; /* ||A - At||                                   */
   double dual_res;   /* rho ||At_after - At_before||                 */
@@ -126,7 +126,7 @@ ntf_status ntf_destroy(ntf_ctx* ctx);
 /* ||X||_F^2 of the tensor, FP64 accumulation (computed at creation). */
 ntf_status ntf_tensor_norm2(ntf_ctx* ctx, double* out);
 
-/* MTTKRP of Sec. III-A item 1: d_M[I_mode, R] = X^(mode) (Khatri-Rao of d_factors[m],
+/* MTTKRP of Sec. IV-A item 1: d_M[I_mode, R] = X^(mode) (Khatri-Rao of d_factors[m],
  * m != mode).  Streams the tensor from device memory once.  d_factors[mode] is ignored
  * (may be NULL). */
 ntf_status ntf_mttkrp(ntf_ctx* ctx, int mode, const float* const* d_factors, float* d_M);
@@ -136,7 +136,7 @@ ntf_status ntf_mttkrp(ntf_ctx* ctx, int mode, const float* const* d_factors, flo
  * not NULL, also written to d_G [R, R]. */
 ntf_status ntf_gram(ntf_ctx* ctx, int mode, const float* d_F, double* d_G);
 
-/* Coefficient matrix of eq. (ADMM_NTF_ALS_C) from the stored Grams (Sec. III-A item 2):
+/* Coefficient matrix of eq. (ADMM_NTF_ALS_C) from the stored Grams (Sec. IV-A item 2):
  * d_H = Hadamard_{m != mode} Gram_m + rho I and its lower Cholesky factor d_L (each may be
  * NULL), rho chosen by the penalty policy.  Synchronizes and reports NTF_ERR_NOT_SPD. */
 ntf_status ntf_system(ntf_ctx* ctx, int mode, double* d_H, double* d_L, double* rho_out);
@@ -146,7 +146,7 @@ ntf_status ntf_system(ntf_ctx* ctx, int mode, double* d_H, double* d_L, double* 
  * d_A (primal, output only), d_At and d_Y in place, then refreshes the stored Gram of
  * factor `mode` from the Khatri-Rao source (d_A or d_At) and, under the ADAPTIVE policy,
  * applies the penalty rule to this factor's rho.  stats (host, may be NULL): residuals of
- * Sec. III-C; when given, the call synchronizes. */
+ * Sec. IV-C; when given, the call synchronizes. */
 ntf_status ntf_admm_update(ntf_ctx* ctx, int mode, const float* d_M, float* d_A, float* d_At,
                            float* d_Y, ntf_update_stats* stats);
 
@@ -154,7 +154,7 @@ ntf_status ntf_admm_update(ntf_ctx* ctx, int mode, const float* d_M, float* d_A,
 ntf_status ntf_set_rho(ntf_ctx* ctx, int mode, double rho);
 ntf_status ntf_get_rho(ntf_ctx* ctx, int mode, double* rho);
 
-/* Relative factorization error ||X - [F_1..F_N]||_F / ||X||_F of Sec. V-A, evaluated as
+/* Relative factorization error ||X - [F_1..F_N]||_F / ||X||_F of Sec. VI-A, evaluated as
  * sqrt(||X||^2 - 2 <M_N, F_N> + 1^T (Hadamard of all Grams) 1) / ||X|| with one MTTKRP of
  * the last factor (one tensor pass).  Does not touch the stored Grams.  Synchronizes. */
 ntf_status ntf_fit(ntf_ctx* ctx, const float* const* d_factors, double* rel_err);
@@ -167,7 +167,7 @@ ntf_status ntf_fit_from_mttkrp(ntf_ctx* ctx, const float* d_M_last, const float*
 
 /* Whole factorization: outer iterations of eq. (ADMoM_NTF) in Gauss-Seidel order starting
  * from the given state (d_A, d_At, d_Y: host arrays of N device pointers, updated in
- * place), until the residual test of Sec. III-C holds for every factor (if eps_abs or
+ * place), until the residual test of Sec. IV-C holds for every factor (if eps_abs or
  * eps_rel > 0), rel_err <= target_rfe (if target_rfe > 0, checked every check_every
  * iterations) or max_outer iterations.  Grams are (re)initialised from the Khatri-Rao
  * source factors first.  rfe_hist (host, may be NULL, length max_outer) receives the error

@@ -1,5 +1,5 @@
-// Gram, coefficient-matrix and fit kernels of the stand-alone entry points (Sec. III-A item
-// 2, Sec. V-A of Liavas & Sidiropoulos); the fused factor update is in update.cu.
+// Gram, coefficient-matrix and fit kernels of the stand-alone entry points (Sec. IV-A item
+// 2, Sec. VI-A of Liavas & Sidiropoulos); the fused factor update is in update.cu.
 //
 // Precision: Grams, the Hadamard product, rho and the Cholesky factorisation run in FP64
 // (small rho makes G + rho I ill-conditioned); factors and MTTKRP rows are stored in FP32.

@@ -1,4 +1,4 @@
-// MTTKRP building blocks (Sec. III-A item 1 of Liavas & Sidiropoulos).
+// MTTKRP building blocks (Sec. IV-A item 1 of Liavas & Sidiropoulos).
 //
 // The tensor is viewed as a row-major matrix X[P, Q] (P = product of the leading modes,
 // Q = product of the trailing ones).  Every MTTKRP is one of two skinny contractions of such a

@@ -55,7 +55,7 @@ enum : int { kStNotSpd = 1, kStNonFinite = 2, kStTimeout = 4 };
 struct SweepSnap {
   int sweep;       // sweeps finished in the run, this one included
   int status;      // kSt* bits at the end of the sweep
-  int stop;        // 1: fit target reached, 2: residual criteria of Sec. III-C met
+  int stop;        // 1: fit target reached, 2: residual criteria of Sec. IV-C met
   int pad;
   double rel_err;
 };

@@ -7,11 +7,11 @@
 //                   rows (App. B).  Stored as FP64 and FP32.
 //  k_update_rows    one warp per row: x = H^{-1}(m + rho At - Y), At = (x + Y/rho)_+,
 //                   Y += rho (x - At); per-CTA partial sums of the residual norms of
-//                   Sec. III-C, of the new factor's Gram (FP64) and of the fit terms
+//                   Sec. IV-C, of the new factor's Gram (FP64) and of the fit terms
 //                   <M_i, f_i>, f_i^T G f_i.  The row arithmetic is FP32 under the trace
 //                   penalty policy (then cond(H) <= R + 1) and FP64 otherwise.
 //  k_update_reduce  fixed-order sums of the partials: the stored Gram of the factor, the
-//                   residuals, the penalty rule (Sec. III-D) and, for the last factor of a
+//                   residuals, the penalty rule (Sec. IV-D) and, for the last factor of a
 //                   sweep, the relative error ||X||^2 - 2<M, F> + sum_i f_i^T G f_i.
 //
 // Inside a sweep the reduction and the next factor's coefficient system are one kernel
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
   rows_cta_tail(a, part, frow, 64, red);
 }
 
-// Residual norms, penalty rule (Sec. III-D) and, for the last factor of a sweep, the fit,
+// Residual norms, penalty rule (Sec. IV-D) and, for the last factor of a sweep, the fit,
 // from the fixed-order sums of the scalar partials (one thread).
 __device__ void update_finalize(const UpdArgs& a, const double* sum) {
   Ctrl* c = a.ctrl;
@@ -537,7 +537,7 @@ __device__ void update_finalize(const UpdArgs& a, const double* sum) {
   if (!finite) atomicOr(&c->status, kStNonFinite);
   if (a.snap && a.want_fit) {
     // the last factor of a sweep of ntf_run: at a checked sweep, the stopping rules (the fit
-    // target; the residual criteria of Sec. III-C over every factor's norms of this sweep)
+    // target; the residual criteria of Sec. IV-C over every factor's norms of this sweep)
     const int k = c->sweep;
     int stop = 0;
     if ((k + 1) % c->check_every == 0 || k + 1 == c->max_outer) {

@@ -1,7 +1,7 @@
-"""Restarts of the outer driver (Sec. V-A).
+"""Restarts of the outer driver (Sec. VI-A).
 
 The paper runs ADMoM for up to n_max outer iterations (400 in its experiments); if the
-stopping test of Sec. III-C has not held by then, it starts again from another random initial
+stopping test of Sec. IV-C has not held by then, it starts again from another random initial
 point, and repeats until the method converges.  This module is that loop on the host around
 ``Context.run`` (``ntf_run``): every attempt runs on the GPU; the attempts are bounded by
 ``max_restarts`` (the paper's loop has no bound), and the caller supplies the initial points,

@@ -4,7 +4,7 @@ This module only creates workloads; it holds none of the factorization method's
 arithmetic.  Both the FP64 oracle and the CUDA library are fed from here, so the two see
 byte-identical inputs.
 
-Recipe (the experiments of Sec. V-A of Liavas & Sidiropoulos, plus the structured variants
+Recipe (the experiments of Sec. VI-A of Liavas & Sidiropoulos, plus the structured variants
 used for the stress workloads):
 
 * factor entries i.i.d. U[0,1] (``structure="uniform"``);
@@ -106,7 +106,7 @@ def _slab(fs: Sequence[np.ndarray], tail: np.ndarray, i0: int) -> np.ndarray:
 
 def tensor(fs: Sequence[np.ndarray], seed: int, snr_db: Optional[float] = None,
            sigma2: Optional[float] = None, dtype=np.float32) -> np.ndarray:
-    """Observed tensor X = [F_1..F_N] + N with i.i.d. N(0, sigma^2) noise (Sec. V-A).
+    """Observed tensor X = [F_1..F_N] + N with i.i.d. N(0, sigma^2) noise (Sec. VI-A).
 
     Exactly one of ``snr_db`` / ``sigma2`` may be given (neither: noise-free).  Built slab by
     slab over the first mode; the noise of slab i0 comes from its own stream.

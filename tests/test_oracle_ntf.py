@@ -61,7 +61,7 @@ def test_reconstruct_is_sum_of_outer_products(shape):
         assert np.allclose(o.unfold(W, n), fs[n] @ o.kr_others(fs, n).T, rtol=1e-13)
 
 
-# ---------------------------------------------------------------- MTTKRP (Sec. III-A)
+# ---------------------------------------------------------------- MTTKRP (Sec. IV-A)
 
 def test_mttkrp_brute_force_3way():
     I, J, K, R = 3, 4, 5, 2
@@ -117,7 +117,7 @@ def test_mttkrp_all_ones():
 
 @pytest.mark.parametrize("shape", [(6, 5, 4), (3, 4, 5, 2)])
 def test_coeff_matrix_hadamard_identity(shape):
-    """(KR)^T (KR) = Hadamard of Grams (Sec. III-A item 2)."""
+    """(KR)^T (KR) = Hadamard of Grams (Sec. IV-A item 2)."""
     fs = [_rand((s, 4), 40 + i) for i, s in enumerate(shape)]
     for n in range(len(shape)):
         assert np.allclose(o.coeff_matrix(fs, n), o.coeff_matrix_explicit(fs, n), rtol=1e-13)
@@ -256,7 +256,7 @@ def test_partitioned_update_equals_centralized():
 # ---------------------------------------------------------------- whole runs
 
 def test_exact_low_rank_fit_goes_to_zero():
-    """Noise-free non-negative data: the relative error keeps falling (no floor, Sec. V-C)."""
+    """Noise-free non-negative data: the relative error keeps falling (no floor, Sec. VI-C)."""
     dims = (12, 10, 8)
     fs = synth.factors(dims, 3, 0)
     X = synth.tensor(fs, 0, dtype=np.float64)
@@ -279,7 +279,7 @@ def test_noisy_fit_reaches_noise_floor_ao_mode():
 
 
 def test_paper_mode_converges_with_stopping_rule():
-    """Paper settings (Sec. V-A): L = 1, primal Khatri-Rao, rho0 = 1, mu = 8, tau = 4 / 2,
+    """Paper settings (Sec. VI-A): L = 1, primal Khatri-Rao, rho0 = 1, mu = 8, tau = 4 / 2,
     eps = 1e-4, B0, C0 random, other state zero; converges within n_max = 400 and the final
     auxiliaries satisfy the KKT conditions of eq. (KKT_NTF) approximately."""
     dims = (30, 30, 30)

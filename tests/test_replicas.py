@@ -87,7 +87,7 @@ def test_clock_summary_reads_the_samples_of_the_timed_region():
 
 
 def _slab_worker(rank, world, port, out):
-    """Sec. IV's block scheme on the oracle: each rank holds a slab of X along mode 1 and the
+    """Sec. V's block scheme on the oracle: each rank holds a slab of X along mode 1 and the
     factors; its MTTKRP of modes 2 and 3 over the slab are partial sums, added across ranks by
     one all-reduce; mode 1's rows are its own slab's."""
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))

@@ -1,4 +1,4 @@
-"""The restart strategy of Sec. V-A: the oracle's loop on its pins, and the host driver of the
+"""The restart strategy of Sec. VI-A: the oracle's loop on its pins, and the host driver of the
 GPU path on a stand-in context (its runs are the library's ntf_run, covered elsewhere)."""
 import numpy as np
 import pytest
