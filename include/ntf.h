@@ -116,7 +116,11 @@ void ntf_default_params(ntf_params* p, int paper_mode);
 /* Create a context for a tensor of the given order, dims[order] and rank.  d_tensor
  * (dtype NTF_F32 or NTF_BF16, row-major) must stay valid and unchanged until
  * ntf_destroy.  stream: a cudaStream_t (NULL = legacy default stream).  Computes ||X||^2
- * once (synchronizes).  On failure *out is NULL. */
+ * once (synchronizes).  On failure *out is NULL.  Errors: NTF_ERR_INVALID_ARG for an order
+ * outside [3, 4], a rank outside [1, 64], a dim outside [1, 2^30], an unknown dtype, a null
+ * tensor or invalid params; NTF_ERR_UNSUPPORTED if a half of the tensor's matrix views
+ * (I_1 I_2 and the remaining dims; for 3-way tensors also I_1 and I_2 I_3) reaches 2^31
+ * entries; all of these before any CUDA call. */
 ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, int dtype,
                       const void* d_tensor, const ntf_params* p, void* stream);
 

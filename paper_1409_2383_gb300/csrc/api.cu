@@ -672,24 +672,23 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   c->X = d_tensor;
   c->st = static_cast<cudaStream_t>(stream);
   c->prm = *p;
-  c->s_R = order == 3 ? 2 : 2;
+  c->s_R = 2;
   c->s_L = order == 3 ? 1 : 2;
-  c->P_R = c->P_L = 1;
-  c->numel = 1;
+  // each half is a product of at most two dims (<= 2^60), so nothing here overflows; the
+  // tensor's size is formed only once both halves are known to be below 2^31
+  c->P_R = c->P_L = c->Q_R = c->Q_L = 1;
   for (int m = 0; m < order; ++m) {
     c->dims[m] = dims[m];
     c->max_dim = std::max(c->max_dim, dims[m]);
-    c->numel *= dims[m];
-    if (m < c->s_R) c->P_R *= dims[m];
-    if (m < c->s_L) c->P_L *= dims[m];
+    (m < c->s_R ? c->P_R : c->Q_R) *= dims[m];
+    (m < c->s_L ? c->P_L : c->Q_L) *= dims[m];
   }
-  c->Q_R = c->numel / c->P_R;
-  c->Q_L = c->numel / c->P_L;
   if (c->P_R >= (int64_t{1} << 31) || c->Q_R >= (int64_t{1} << 31) ||
       c->P_L >= (int64_t{1} << 31) || c->Q_L >= (int64_t{1} << 31)) {
     delete c;
     return fail(NTF_ERR_UNSUPPORTED, "tensor halves must each have < 2^31 entries");
   }
+  c->numel = c->P_R * c->Q_R;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);

@@ -55,6 +55,20 @@ def test_create_rejects_bad_arguments_before_any_launch(lib, order, rank, dtype,
     assert lib.ntf_last_error()
 
 
+@pytest.mark.parametrize("dims", [(1 << 30, 1 << 30, 1 << 30), (1 << 16, 1 << 16, 2),
+                                  (2, 1 << 16, 1 << 16), (1 << 30,) * 4])
+def test_create_rejects_oversized_halves_before_any_launch(lib, dims):
+    """A half of the tensor's matrix views with 2^31 or more entries is refused as
+    unsupported (without forming the overflowing size of the whole tensor)."""
+    from paper_1409_2383_gb300 import ntf
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    p = ntf.default_params()
+    st = lib.ntf_create(ctypes.byref(h), len(dims), d, 3, 0, 16, ctypes.byref(p), None)
+    assert st == 8 and not h.value
+    assert b"2^31" in lib.ntf_last_error()
+
+
 def test_create_rejects_bad_params(lib):
     from paper_1409_2383_gb300 import ntf
     h = ctypes.c_void_p()
