@@ -310,6 +310,8 @@ ntf_status ntf_attach_warmstart(ntf_ctx* ctx, ntf_mlp* net, int sweeps);
  *   (I_1 I_2 R floats for modes 1-2, I_2 I_3 R floats for mode 3 of a 3-way tensor; I_1 I_2 R
  *   or I_3 I_4 R floats for a 4-way tensor) plus a Khatri-Rao table of the other group.
  *   Partial sums that would not fit beside them are avoided by not splitting the contraction.
+ * - NTF_ERR_UNSUPPORTED, before any CUDA call, under the size limit of ntf_create (a half
+ *   of the tensor's matrix views with 2^31 or more entries).
  * - Never calls cudaMalloc, cudaFree or any allocating routine.  Asynchronous on `stream`. */
 ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int rank, int dtype,
                               const void* d_tensor, int mode, const float* const* d_factors,

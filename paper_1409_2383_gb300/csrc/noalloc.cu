@@ -53,13 +53,12 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
   // The same two contractions as the context path: the leading factors' modes come from
   // X[P_R, Q_R] * KR(trailing factors), the others from X[P_L, Q_L]^T * KR(leading factors).
   const int s_R = 2, s_L = order == 3 ? 1 : 2;
-  int64_t numel = 1, P_R = 1, P_L = 1;
+  // each half is a product of at most two dims (<= 2^60): no overflow before the check
+  int64_t P_R = 1, Q_R = 1, P_L = 1, Q_L = 1;
   for (int m = 0; m < order; ++m) {
-    numel *= dims[m];
-    if (m < s_R) P_R *= dims[m];
-    if (m < s_L) P_L *= dims[m];
+    (m < s_R ? P_R : Q_R) *= dims[m];
+    (m < s_L ? P_L : Q_L) *= dims[m];
   }
-  const int64_t Q_R = numel / P_R, Q_L = numel / P_L;
   if (P_R >= (int64_t{1} << 31) || Q_R >= (int64_t{1} << 31) || P_L >= (int64_t{1} << 31) ||
       Q_L >= (int64_t{1} << 31))
     return NTF_ERR_UNSUPPORTED;

@@ -69,6 +69,15 @@ def test_create_rejects_oversized_halves_before_any_launch(lib, dims):
     assert b"2^31" in lib.ntf_last_error()
 
 
+def test_noalloc_mttkrp_rejects_oversized_halves_before_any_launch(lib):
+    dims = (ctypes.c_int64 * 3)(1 << 30, 1 << 30, 1 << 30)
+    F = (ctypes.c_void_p * 3)(16, 16, 16)
+    assert lib.ntf_mttkrp_noalloc(3, dims, 3, 0, 16, 0, F, 16, None) == 8
+    dims4 = (ctypes.c_int64 * 4)(*(1 << 30,) * 4)
+    F4 = (ctypes.c_void_p * 4)(16, 16, 16, 16)
+    assert lib.ntf_mttkrp_noalloc(4, dims4, 3, 0, 16, 3, F4, 16, None) == 8
+
+
 def test_create_rejects_bad_params(lib):
     from paper_1409_2383_gb300 import ntf
     h = ctypes.c_void_p()
