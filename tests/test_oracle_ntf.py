@@ -224,6 +224,24 @@ def test_stopping_test_scaling():
     assert not o.small_residuals(st, 10, 10, 0.9e-4, 0.0)
 
 
+def test_stopping_test_relative_terms():
+    """eqs. (stopping_cond_prim_A_def), (stopping_cond_dual_A_def) worked by hand: the primal
+    bound takes the larger of ||A||, ||At||, the dual bound takes ||Y||, and both add the
+    absolute term sqrt(I F) eps_abs."""
+    def st(p, d, a, t, y):
+        return o.UpdateStats(primal_res=p, dual_res=d, norm_A=a, norm_At=t, norm_Y=y, rho=1.0)
+    # I F = 4: absolute term 0; relative: primal 0.1 * max(2, 5) = 0.5, dual 0.1 * 1 = 0.1
+    assert o.small_residuals(st(0.5, 0.1, 2.0, 5.0, 1.0), 4, 1, 0.0, 0.1)
+    assert o.small_residuals(st(0.3, 0.05, 2.0, 5.0, 1.0), 4, 1, 0.0, 0.1)      # > 0.1 min(.)
+    assert o.small_residuals(st(0.3, 0.05, 5.0, 2.0, 1.0), 4, 1, 0.0, 0.1)      # either order
+    assert not o.small_residuals(st(0.51, 0.1, 2.0, 5.0, 1.0), 4, 1, 0.0, 0.1)
+    assert not o.small_residuals(st(0.1, 0.3, 2.0, 5.0, 1.0), 4, 1, 0.0, 0.1)   # dual: ||Y||
+    # I F = 36: absolute 6 * 0.01 = 0.06; primal 0.06 + 0.1 * 1 = 0.16, dual 0.06 + 0.1 * 2
+    assert o.small_residuals(st(0.16, 0.26, 1.0, 0.5, 2.0), 9, 4, 0.01, 0.1)
+    assert not o.small_residuals(st(0.161, 0.26, 1.0, 0.5, 2.0), 9, 4, 0.01, 0.1)
+    assert not o.small_residuals(st(0.16, 0.261, 1.0, 0.5, 2.0), 9, 4, 0.01, 0.1)
+
+
 def test_partitioned_update_equals_centralized():
     """App. B / eq. (partitioned_update_Ak): row blocks of A computed from column-blocked
     unfoldings, sum_nC X_{nA,nC} (C_nC (.) B) and sum_nC (C_nC (.) B)^T (C_nC (.) B), equal
