@@ -94,6 +94,25 @@ def test_mttkrp_brute_force_4way():
         assert np.allclose(o.mttkrp(X, fs, n), want, rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("shape", [(3, 4, 5), (2, 3, 4, 5)])
+def test_mttkrp_rows_brute_force(shape):
+    """Selected rows of M_n (unordered, repeated) against the index loops of the MTTKRP
+    definition (the sampled-row check of the full-size GPU parity tests relies on them)."""
+    R = 3
+    X = _rand(shape, 11) - 0.4
+    fs = [_rand((s, R), 40 + i) for i, s in enumerate(shape)]
+    for n in range(len(shape)):
+        full = np.zeros((shape[n], R))
+        for idx in itertools.product(*[range(s) for s in shape]):
+            w = np.ones(R)
+            for m in range(len(shape)):
+                if m != n:
+                    w = w * fs[m][idx[m]]
+            full[idx[n]] += X[idx] * w
+        rows = [shape[n] - 1, 0, shape[n] - 1, shape[n] // 2]
+        assert np.allclose(o.mttkrp_rows(X, fs, n, rows), full[rows], rtol=1e-13, atol=1e-14)
+
+
 @pytest.mark.parametrize("shape", [(6, 5, 4), (3, 4, 5, 2)])
 def test_mttkrp_exact_low_rank_closed_form(shape):
     """X = [F] exactly  =>  M_n = F_n * (Hadamard of the other Grams)."""
@@ -369,3 +388,24 @@ def test_structured_generators():
         C = Fn.T @ Fn
         off = C[~np.eye(6, dtype=bool)]
         assert abs(np.mean(off) - 0.9) < 0.01
+
+
+def test_stored_trajectory_is_the_oracles():
+    """The stored relative-error trajectory of the 400^3 rank-20 workload (written by
+    oracle/trajectory.py; the benchmark takes the oracle's iteration count from it) starts
+    with what the oracle computes now: its first two outer iterations, recomputed."""
+    import json
+    with open(os.path.join(GOLDEN, "trajectory_400x400x400_r20.json")) as f:
+        h = json.load(f)
+    spec = dict(synth.WORKLOADS[h["workload"]])
+    dims, R = spec.pop("dims"), spec.pop("R")
+    X, _, init = synth.workload(dims, R, seed=h["data_seed"], **spec)
+    X64 = X.astype(np.float64)
+    params = o.Params(inner_iters=5, kr_source="aux", rho_policy="trace")
+    st = o.init_state([F.astype(np.float32).astype(np.float64) for F in init], params)
+    for k in range(2):
+        o.outer_iteration(X64, st, params)
+        assert o.rfe(X64, st.aux) == pytest.approx(h["rfe"][k], rel=1e-10)
+    # it ends at its lowest value (the converged error the fit target is measured against)
+    r = np.asarray(h["rfe"])
+    assert len(r) == 200 and r[-1] <= r.min() * (1 + 1e-9)
