@@ -69,6 +69,37 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     assert called == [] and capsys.readouterr().out == ""
 
 
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the keys of the benchmark
+    contract: the oracle's time per iteration times the iterations the oracle needs."""
+    import json
+    bench = _bench()
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+
+    class Args:
+        gpus, steps, warmup = 1, 2, 3
+
+    monkeypatch.setattr(bench, "_workload", lambda seed: (None, None))
+    monkeypatch.setattr(bench, "cpu_oracle_seconds_per_iteration", lambda X, init, n: 0.5)
+    bench.run_reference(Args())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    n_iter, _ = bench._stored_iterations()
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["value"] == pytest.approx(0.5 * n_iter) and d["higher_is_better"] is False
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == bench.WORKLOAD
+    assert 1 <= n_iter <= 200
+
+
 def test_clock_summary_reads_the_samples_of_the_timed_region():
     bench = _bench()
     s = bench.ClockSampler(0)
