@@ -80,3 +80,34 @@ def test_driver_gives_up_after_max_restarts():
     assert drawn == [0, 1, 2, 3] and rs["restarts"] == 3 and rs["converged"] == 0
     with pytest.raises(ValueError):
         restarts.factorize(_Ctx(good=0), A, At, Y, 0, lambda *_: None)
+
+
+class _CtxRho(_Ctx):
+    """Stand-in that also records the penalties it is given."""
+
+    def __init__(self, good, policy):
+        super().__init__(good)
+        from paper_1409_2383_gb300 import ntf
+        self.params = ntf.Params(rho_policy=policy, rho0=1.0)
+        self.rho_calls = []
+
+    def set_rho(self, m, rho):
+        self.rho_calls.append((len(self.calls), m, rho))
+
+
+def test_driver_resets_adaptive_penalties_before_every_attempt():
+    """A restart is a fresh start (Sec. VI-A): rho back to rho0 for every factor before each
+    attempt under the adaptive policy, as the oracle's init_state does; the trace and fixed
+    policies keep the caller's penalties."""
+    import torch
+    from paper_1409_2383_gb300 import ntf, restarts
+    A = [torch.zeros(2) for _ in range(3)]
+    At, Y = [a.clone() for a in A], [a.clone() for a in A]
+    ctx = _CtxRho(good=1, policy=ntf.NTF_RHO_ADAPTIVE)
+    rs = restarts.factorize(ctx, A, At, Y, 10, lambda *_: None, max_restarts=4)
+    assert rs["restarts"] == 1
+    assert ctx.rho_calls == [(k, m, 1.0) for k in range(2) for m in range(3)]
+    for policy in (ntf.NTF_RHO_TRACE, ntf.NTF_RHO_FIXED):
+        ctx = _CtxRho(good=1, policy=policy)
+        restarts.factorize(ctx, A, At, Y, 10, lambda *_: None, max_restarts=4)
+        assert ctx.rho_calls == []
