@@ -17,6 +17,11 @@ host buffers, and the FP64 oracle timed on the host cores.
 
 Multi-GPU: replicas only (each rank factorizes its own tensor of a different seed; no
 collective on the data path); value = max over ranks of the time per factorization.
+
+  python bench.py --study table1 [--realizations R] [--study-cases 0,1,...]
+
+runs the scenarios of the paper's Table 1 in paper mode (restarts included) and prints, per
+scenario, the mean relative error beside the printed one and the time per factorization.
 """
 from __future__ import annotations
 
@@ -530,6 +535,87 @@ def run_sweep_case(args):
                       "rel_err": rs["rel_err"], "trace_last_sweep": trace}))
 
 
+def table_cases(name: str = "table1_rfe.txt"):
+    """Scenarios of the paper's Table 1 (Sec. VI-A) with their printed mean RFE, from the
+    stored fixture: (dims, F, sigma2, printed mean RFE)."""
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                I, J, K, F, s2, v = line.split()
+                rows.append(((int(I), int(J), int(K)), int(F), float(s2), float(v)))
+    return rows
+
+
+def study_case(dims, F, sigma2, realizations, n_max, max_restarts, open_ctx, device,
+               sync=lambda: None):
+    """One scenario of the paper's experiments (Sec. VI-A) in paper mode: for realization r,
+    X = [A, B, C] + N (U[0,1] factors of data seed r, i.i.d. N(0, sigma2) noise) is
+    factorized from B0, C0 i.i.d. U[0,1] (attempt k of realization r: init seed
+    1000 (r + 1) + k), auxiliaries and duals zero, rho0 = 1, until the residual test holds
+    within n_max outer iterations, restarting from a new random point otherwise.
+    `open_ctx(X, F)` opens a context; returns the scenario's statistics."""
+    import torch
+    from paper_1409_2383_gb300 import restarts
+    import synth
+    rfe, secs, nrest, iters, total, conv = [], [], [], [], [], 0
+    for r in range(realizations):
+        X, _, _ = synth.workload(dims, F, seed=r, snr_db=None, sigma2=sigma2)
+        Xd = torch.as_tensor(X).to(device)
+        A = [torch.zeros(d, F, device=device) for d in dims]
+        At = [torch.zeros_like(a) for a in A]
+        Y = [torch.zeros_like(a) for a in A]
+
+        def draw(k, A, At, Y, r=r):
+            init = synth.init_factors(dims, F, seed=1000 * (r + 1) + k)
+            for a, t, y, f in zip(A, At, Y, init):
+                a.copy_(torch.as_tensor(f, dtype=torch.float32))
+                t.zero_()
+                y.zero_()
+
+        with open_ctx(Xd, F) as ctx:
+            sync()
+            t0 = time.perf_counter()
+            rs = restarts.factorize(ctx, A, At, Y, n_max, draw, max_restarts=max_restarts)
+            sync()
+            secs.append(time.perf_counter() - t0)
+            rfe.append(ctx.fit(At))
+        conv += rs["converged"]
+        nrest.append(rs["restarts"])
+        iters.append(rs["iters"])
+        total.append(rs["restarts"] * n_max + rs["iters"])
+    return {"dims": list(dims), "F": F, "sigma2": sigma2, "realizations": realizations,
+            "converged": conv, "mean_rfe": statistics.mean(rfe),
+            "mean_s": statistics.mean(secs),
+            "std_s": statistics.stdev(secs) if len(secs) > 1 else 0.0,
+            "mean_restarts": statistics.mean(nrest), "mean_iters_last_attempt":
+            statistics.mean(iters), "mean_iters_total": statistics.mean(total)}
+
+
+def run_study(args):
+    """The paper's Table 1 scenarios on the GPU in paper mode (L = 1, primal Khatri-Rao,
+    adaptive rho, eps_abs = eps_rel = 1e-4, n_max = 400, restarts): one JSON line per
+    scenario with the mean RFE beside the printed one and the time per factorization."""
+    import torch
+    from paper_1409_2383_gb300 import ntf
+    p = ntf.default_params(paper_mode=True)
+    cases = table_cases()
+    if args.study_cases:
+        keep = {int(i) for i in args.study_cases.split(",")}
+        cases = [c for i, c in enumerate(cases) if i in keep]
+    stream = torch.cuda.Stream()           # a non-default stream: sweeps replay as CUDA graphs
+    for dims, F, s2, printed in cases:
+        with torch.cuda.stream(stream):
+            res = study_case(dims, F, s2, args.realizations, 400, args.max_restarts,
+                             lambda X, R: ntf.Context(X, R, p, stream=stream), "cuda",
+                             torch.cuda.synchronize)
+        res.update({"study": "table1", "printed_mean_rfe": printed,
+                    "rfe_vs_printed": res["mean_rfe"] / printed, "data": "synthetic",
+                    "settings": "L=1, kr_source=primal, adaptive rho (1, 8, 4, 2), "
+                                "eps 1e-4, n_max 400"})
+        print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,9 +644,17 @@ def main():
                     help="run --steps outer iterations of the workload (for ncu launch lists)")
     ap.add_argument("--trace", action="store_true",
                     help="with --sweep-case: print the per-stream timeline of the last sweep")
+    ap.add_argument("--study", choices=["table1"],
+                    help="the paper's Table 1 scenarios in paper mode (one line each)")
+    ap.add_argument("--study-cases", default="",
+                    help="with --study: comma-separated indices of the scenarios to run")
+    ap.add_argument("--realizations", type=int, default=10)
+    ap.add_argument("--max-restarts", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.kernel_case:
+    if args.study:
+        run_study(args)
+    elif args.kernel_case:
         run_kernel_case(args)
     elif args.sweep_case:
         run_sweep_case(args)

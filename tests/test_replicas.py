@@ -1,5 +1,7 @@
-"""The multi-process path of bench.py on CPU (gloo, world size 2): replicas run independently
-and the job's figures are the maximum over ranks; the reference arm runs on rank 0 only."""
+"""Host logic of bench.py on CPU: the multi-process path (gloo, world size 2; replicas run
+independently and the job's figures are the maximum over ranks), the reference arm (rank 0
+only, the contract's keys), the clock summary, the slab partition of the paper's distributed
+scheme on the oracle, and the loop of the Table 1 study on a stand-in context."""
 import importlib.util
 import os
 import socket
@@ -159,3 +161,55 @@ def test_slab_partitioned_mttkrp_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == [(0, True, True), (1, True, True)]
+
+
+def test_table1_study_loop_on_a_stand_in_context():
+    """The Table 1 study of bench.py (paper mode with restarts, Sec. VI-A): the scenarios come
+    from the stored fixture; every attempt starts from its own random B0, C0 with zero
+    auxiliaries and duals; the statistics count restarts and iterations over attempts."""
+    import numpy as np
+    import torch
+    import synth
+    bench = _bench()
+    cases = bench.table_cases()
+    assert len(cases) == 12 and cases[0] == ((3000, 50, 50), 3, 1e-2, 0.2156)
+    assert cases[-1] == ((200, 200, 200), 30, 1e-4, 0.0026)
+
+    seen = []
+
+    class Ctx:
+        def __init__(self, X, R):
+            self.X, self.R, self.k = X, R, 0
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            pass
+
+        def run(self, A, At, Y, n_max, target_rfe=0.0, check_every=1):
+            seen.append(([a.clone() for a in A], [float(t.abs().sum()) for t in At + Y]))
+            self.k += 1
+            ok = self.k >= 2                        # every realization restarts once
+            return {"iters": 17 if ok else n_max, "converged": int(ok),
+                    "reached_target": 0, "rel_err": 0.0}
+
+        def fit(self, F):
+            return float(self.X.abs().mean())
+
+    dims, F = (6, 5, 4), 2
+    res = bench.study_case(dims, F, 1e-2, 2, 30, 5, Ctx, "cpu")
+    assert res["realizations"] == 2 and res["converged"] == 2
+    assert res["mean_restarts"] == 1 and res["mean_iters_last_attempt"] == 17
+    assert res["mean_iters_total"] == 30 + 17
+    assert len(seen) == 4
+    for i, (A, zeros) in enumerate(seen):
+        r, k = divmod(i, 2)
+        want = synth.init_factors(dims, F, seed=1000 * (r + 1) + k)
+        for a, w in zip(A, want):
+            assert np.array_equal(a.numpy(), w.astype(np.float32))
+        assert zeros == [0.0] * 6
+    X0 = synth.workload(dims, F, seed=0, snr_db=None, sigma2=1e-2)[0]
+    X1 = synth.workload(dims, F, seed=1, snr_db=None, sigma2=1e-2)[0]
+    assert res["mean_rfe"] == pytest.approx((np.abs(X0).mean() + np.abs(X1).mean()) / 2,
+                                            rel=1e-6)
