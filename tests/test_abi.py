@@ -1,5 +1,6 @@
 """Host-side checks of the C-ABI library: it builds for sm_103a, loads, exports every entry
-point declared in include/ntf.h, and rejects bad arguments before touching the GPU."""
+point declared in include/ntf.h, the binding's structures match the header's, and it rejects
+bad arguments before touching the GPU."""
 import ctypes
 import os
 import re
@@ -95,3 +96,37 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.ntf_mttkrp(None, 0, None, None) == 1
     assert lib.ntf_to_bf16(None, None, 4, None) == 1
     assert lib.ntf_status_string(4) == b"coefficient matrix not positive definite"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets of the header's
+    structs (compiled with the host C compiler against include/ntf.h)."""
+    import shutil
+    import subprocess
+    from paper_1409_2383_gb300 import ntf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = {"ntf_params": ntf.Params, "ntf_update_stats": ntf.UpdateStats,
+             "ntf_run_stats": ntf.RunStats, "ntf_profile": ntf.Profile,
+             "ntf_trace_entry": ntf.TraceEntry}
+    lines = ["#include <stdio.h>", '#include "ntf.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                             text=True).stdout.splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
