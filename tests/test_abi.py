@@ -130,3 +130,17 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_binding_constants_match_the_header():
+    """Every enum constant of the header has the same value in the binding (status codes in
+    its STATUS table, the others as module constants)."""
+    from paper_1409_2383_gb300 import ntf
+    with open(os.path.join(ROOT, "include", "ntf.h")) as f:
+        consts = {k: int(v) for k, v in re.findall(r"\b(NTF_[A-Z0-9_]+)\s*=\s*(\d+)", f.read())}
+    assert len(consts) >= 19
+    for name, value in consts.items():
+        if name == "NTF_OK" or name.startswith("NTF_ERR_"):
+            assert ntf.STATUS[value] == name
+        else:
+            assert getattr(ntf, name) == value, name
