@@ -217,6 +217,23 @@ def test_inner_loop_converges_to_exhaustive_nnls(R, seed):
     assert k["neg_x"] == 0 and k["dual"] < 1e-9 and k["comp"] < 1e-10 and k["y_gap"] < 1e-9
 
 
+def test_kkt_measures_on_a_hand_worked_problem():
+    """eq. (KKT_NTF) on min_{x >= 0} 1/2 ||x||^2 - m^T x with m = (1, -1): x* = (1, 0),
+    gradient g = x - m.  Each measure is zero at x* and positive exactly where its own
+    condition fails (the scale is s_g = max|G| max|x| + max|m|)."""
+    G, M = np.eye(2), np.array([[1.0, -1.0]])
+    k = o.kkt_nnls(G, M, np.array([[1.0, 0.0]]), np.array([[0.0, -1.0]]))
+    assert k == {"neg_x": 0.0, "dual": 0.0, "comp": 0.0, "y_gap": 0.0}
+    k = o.kkt_nnls(G, M, np.array([[0.5, 0.0]]))           # g = (-0.5, 1): not dual feasible
+    assert k["neg_x"] == 0.0 and k["dual"] == pytest.approx(0.5 / 1.5) and k["comp"] > 0
+    k = o.kkt_nnls(G, M, np.array([[1.0, 0.5]]))           # g = (0, 1.5): x_2 g_2 != 0
+    assert k["dual"] == 0.0 and k["comp"] == pytest.approx(0.75 / (2 * 1.0 * 2.0))
+    k = o.kkt_nnls(G, M, np.array([[1.0, -0.25]]))         # infeasible x
+    assert k["neg_x"] == pytest.approx(0.25)
+    k = o.kkt_nnls(G, M, np.array([[1.0, 0.0]]), np.array([[0.0, -0.5]]))   # Y != M - x G
+    assert k["y_gap"] == pytest.approx(0.5 / (math.sqrt(2) * 2.0))
+
+
 def test_nnls_exhaustive_against_scipy():
     import scipy.optimize
     for seed in range(5):
