@@ -252,6 +252,21 @@ def test_rho_rule_cases():
     assert o.rho_adapt(2.0, 8.0, 1.0) == 2.0          # boundary: strict inequality
 
 
+def test_trace_penalty_bounds_the_condition_number():
+    """rho = trace(G)/R: G = c I gives rho = c, and for any PSD G (rank-deficient included)
+    the eigenvalues of G lie in [0, trace G], so cond(G + rho I) <= (trace G + rho) / rho
+    = R + 1."""
+    assert o.rho_trace(3.5 * np.eye(4)) == 3.5
+    rng = np.random.default_rng(9)
+    for R, rank in ((5, 5), (8, 2), (20, 1)):
+        F = rng.standard_normal((30, rank)) @ rng.standard_normal((rank, R))
+        G = F.T @ F
+        rho = o.rho_trace(G)
+        assert np.linalg.cond(G + rho * np.eye(R)) <= (R + 1) * (1 + 1e-12)
+    G = np.diag([1.0] + [0.0] * 5)                      # the bound is reached
+    assert np.linalg.cond(G + o.rho_trace(G) * np.eye(6)) == pytest.approx(7.0)
+
+
 def test_stopping_test_scaling():
     st = o.UpdateStats(primal_res=1e-3, dual_res=1e-3, norm_A=1.0, norm_At=1.0, norm_Y=1.0,
                        rho=1.0)
