@@ -324,6 +324,19 @@ def test_partitioned_update_equals_centralized():
 
 # ---------------------------------------------------------------- whole runs
 
+def test_rfe_special_cases():
+    """Sec. VI-A's error: 0 for the exact factors of a noise-free tensor, 1 for zero
+    factors, |1 - c| when the factors reproduce c X, and invariant to scaling X and one
+    factor together."""
+    fs = [_rand((s, 3), 60 + i) for i, s in enumerate((5, 4, 6))]
+    X = o.reconstruct(fs)
+    assert o.rfe(X, fs) < 1e-15
+    assert o.rfe(X, [np.zeros_like(F) for F in fs]) == pytest.approx(1.0)
+    assert o.rfe(X, [0.25 * fs[0], fs[1], fs[2]]) == pytest.approx(0.75)
+    Xn = X + 0.01 * _rand(X.shape, 70)
+    assert o.rfe(3.0 * Xn, [3.0 * fs[0], fs[1], fs[2]]) == pytest.approx(o.rfe(Xn, fs))
+
+
 def test_exact_low_rank_fit_goes_to_zero():
     """Noise-free non-negative data: the relative error keeps falling (no floor, Sec. VI-C)."""
     dims = (12, 10, 8)
