@@ -30,6 +30,14 @@ def test_gelu_grad_finite_difference():
     # GELU(z) = z * Phi(z): limits
     assert abs(mlp.gelu(np.array([8.0]))[0] - 8.0) < 1e-12
     assert abs(mlp.gelu(np.array([-8.0]))[0]) < 1e-12
+    # the exact form (not the tanh approximation) at table values of the normal CDF:
+    # Phi(1) = 0.8413447460685429, Phi(2) = 0.9772498680518208, Phi(0.5) = 0.6914624612740131
+    z = np.array([0.0, 1.0, -1.0, 2.0, 0.5])
+    want = z * np.array([0.5, 0.8413447460685429, 1 - 0.8413447460685429,
+                         0.9772498680518208, 0.6914624612740131])
+    assert np.allclose(mlp.gelu(z), want, rtol=1e-14, atol=1e-16)
+    tanh_form = 0.5 * z * (1 + np.tanh(math.sqrt(2 / math.pi) * (z + 0.044715 * z ** 3)))
+    assert not np.allclose(mlp.gelu(z), tanh_form, rtol=1e-6, atol=0)
 
 
 def test_backward_matches_central_differences():
