@@ -73,6 +73,40 @@ def test_adam_first_step_is_lr_times_sign():
     assert np.allclose(p["w"], [0.9, -1.9, 2.9], rtol=1e-12)
 
 
+def test_adam_constant_gradient_steps_are_all_lr():
+    """With a constant gradient the bias-corrected moments are g and g^2 at every step, so
+    every step is lr * sign(g) (eps = 0): a missing or misplaced bias correction makes the
+    early steps differ."""
+    p = {"w": np.array([0.0, 0.0])}
+    g = {"w": np.array([0.3, -7.0])}
+    m = {"w": np.zeros(2)}
+    v = {"w": np.zeros(2)}
+    for t in range(1, 6):
+        mlp.adam_step(p, g, m, v, t, lr=0.01, eps=0.0)
+        assert np.allclose(p["w"], [-0.01 * t, 0.01 * t], rtol=1e-12, atol=0)
+
+
+def test_forward_and_loss_by_hand():
+    """A one-unit network whose pre-activations land on table values of the normal CDF:
+    z1 = 1, h1 = Phi(1); z2 = h1 / Phi(1) = 1, h2 = Phi(1); out = 2 h2 + 1.  The loss is the
+    mean of the squared entries of the error."""
+    phi1 = 0.8413447460685429
+    p = {"W1": np.array([[1.0]]), "b1": np.array([0.0]), "W2": np.array([[1.0 / phi1]]),
+         "b2": np.array([0.0]), "W3": np.array([[2.0]]), "b3": np.array([1.0])}
+    out, _ = mlp.forward(p, np.array([[1.0]]))
+    assert out[0, 0] == pytest.approx(2 * phi1 + 1, rel=1e-14)
+    assert mlp.loss(np.array([[1.0, 2.0]]), np.array([[0.0, 0.0]])) == 2.5
+    assert mlp.loss(np.array([[1.0], [3.0]]), np.array([[1.0], [1.0]])) == 2.0
+
+
+def test_decode_clamps_to_the_kkt_signs():
+    """Network output [x ; y/s] -> (max(0, x), min(0, s y)): a non-negative auxiliary and a
+    non-positive dual, the signs eq. (KKT_NTF) fixes."""
+    out = np.array([[1.5, -0.5, 0.25, -2.0]])
+    aux, dual = mlp.decode(out, 4.0, 2)
+    assert np.array_equal(aux, [[1.5, 0.0]]) and np.array_equal(dual, [[0.0, -8.0]])
+
+
 def test_adam_minimises_quadratic():
     rng = np.random.default_rng(2)
     target = rng.standard_normal(10)
