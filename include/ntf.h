@@ -22,6 +22,8 @@
  *   for the duration of the call (the tensor: for the life of the context).  The context
  *   owns its workspace, allocated in ntf_create and freed in ntf_destroy.  Arrays of
  *   pointers (``const float* const* d_factors``) are host arrays of N device pointers.
+ *   Every array pointer must be a multiple of its element size (FP32: 4, BF16: 2, FP64: 8
+ *   bytes); otherwise the call returns NTF_ERR_INVALID_ARG before any launch.
  * - Streams: every call is enqueued on the stream given to ntf_create and returns without
  *   waiting, except where a host result is returned (stats, rel_err, norms), in which case
  *   the call synchronizes that stream.
@@ -31,7 +33,8 @@
  *   context and returned by the next synchronizing call or by ntf_sync.  ntf_last_error()
  *   gives a message for the calling thread's most recent failure.  A context stays usable
  *   after any error.
- * - Limits: 3 <= N <= 4, 1 <= R <= 64, every I_n >= 1.
+ * - Limits: 3 <= N <= 4, 1 <= R <= 64, 1 <= I_n <= 2^30, and each half of the tensor's
+ *   matrix views below 2^31 entries (ntf_create).
  */
 #ifndef NTF_H
 #define NTF_H

@@ -141,6 +141,10 @@ ntf_status check_mode(const ntf_ctx* c, int mode) {
   return NTF_OK;
 }
 
+// Device arrays are read with loads of their element type (at least): a pointer that is not
+// a multiple of its element size is refused before any launch.
+bool misaligned(const void* p, size_t elem) { return reinterpret_cast<uintptr_t>(p) % elem != 0; }
+
 ntf_status check_params(const ntf_params* p) {
   if (!p) return fail(NTF_ERR_INVALID_ARG, "null params");
   if (p->inner_iters < 1) return fail(NTF_ERR_INVALID_ARG, "inner_iters must be >= 1");
@@ -660,6 +664,8 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     return fail(NTF_ERR_INVALID_ARG, "rank %d not in [1, %d]", rank, ntf::kMaxRank);
   if (dtype != NTF_F32 && dtype != NTF_BF16) return fail(NTF_ERR_INVALID_ARG, "unknown dtype");
   if (!d_tensor) return fail(NTF_ERR_INVALID_ARG, "null tensor");
+  if (misaligned(d_tensor, dtype == NTF_BF16 ? 2 : 4))
+    return fail(NTF_ERR_INVALID_ARG, "tensor pointer not aligned to its element size");
   NTF_TRY(check_params(p));
   for (int m = 0; m < order; ++m)
     if (dims[m] < 1 || dims[m] > (int64_t{1} << 30))
@@ -868,7 +874,9 @@ ntf_status ntf_mttkrp(ntf_ctx* c, int mode, const float* const* F, float* d_M) {
   NTF_TRY(check_mode(c, mode));
   if (!F || !d_M) return fail(NTF_ERR_INVALID_ARG, "null factors or output");
   for (int m = 0; m < c->N; ++m)
-    if (m != mode && !F[m]) return fail(NTF_ERR_INVALID_ARG, "null factor %d", m);
+    if (m != mode && (!F[m] || misaligned(F[m], sizeof(float))))
+      return fail(NTF_ERR_INVALID_ARG, "null or misaligned factor %d", m);
+  if (misaligned(d_M, sizeof(float))) return fail(NTF_ERR_INVALID_ARG, "misaligned output");
   if (mode < c->s_R) {
     float* T = c->s_R == 1 ? d_M : c->TR;
     NTF_TRY(contract_right(c, F, T, c->st));
@@ -884,6 +892,8 @@ ntf_status ntf_gram(ntf_ctx* c, int mode, const float* d_F, double* d_G) {
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's
   NTF_TRY(check_mode(c, mode));
   if (!d_F) return fail(NTF_ERR_INVALID_ARG, "null factor");
+  if (misaligned(d_F, sizeof(float)) || misaligned(d_G, sizeof(double)))
+    return fail(NTF_ERR_INVALID_ARG, "misaligned factor or Gram");
   const int64_t RR = static_cast<int64_t>(c->R) * c->R;
   double* G = c->grams + mode * RR;
   NTF_CUDA(ntf::launch_gram(d_F, c->dims[mode], c->R, G, c->st));
@@ -894,6 +904,8 @@ ntf_status ntf_gram(ntf_ctx* c, int mode, const float* d_F, double* d_G) {
 ntf_status ntf_system(ntf_ctx* c, int mode, double* d_H, double* d_L, double* rho_out) {
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's
   NTF_TRY(check_mode(c, mode));
+  if (misaligned(d_H, sizeof(double)) || misaligned(d_L, sizeof(double)))
+    return fail(NTF_ERR_INVALID_ARG, "misaligned output");
   const int64_t RR = static_cast<int64_t>(c->R) * c->R;
   double* L = c->chol + mode * RR;
   NTF_CUDA(ntf::launch_system(c->grams, c->N, mode, c->R, c->prm.rho_policy, c->d_ctrl, d_H, L,
@@ -909,6 +921,9 @@ ntf_status ntf_admm_update(ntf_ctx* c, int mode, const float* d_M, float* d_A, f
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's
   NTF_TRY(check_mode(c, mode));
   if (!d_M || !d_A || !d_At || !d_Y) return fail(NTF_ERR_INVALID_ARG, "null matrix argument");
+  for (const void* q : {static_cast<const void*>(d_M), static_cast<const void*>(d_A),
+                        static_cast<const void*>(d_At), static_cast<const void*>(d_Y)})
+    if (misaligned(q, sizeof(float))) return fail(NTF_ERR_INVALID_ARG, "misaligned matrix");
   c->ws_now = true;  // a single update consults an attached network
   NTF_TRY(enqueue_update(c, mode, d_M, d_A, d_At, d_Y, false));
   if (!stats) return NTF_OK;
@@ -945,7 +960,8 @@ ntf_status ntf_fit(ntf_ctx* c, const float* const* F, double* rel_err) {
   (void)cudaGetLastError();  // a stale non-sticky error is not this call's
   if (!c || !F || !rel_err) return fail(NTF_ERR_INVALID_ARG, "null argument");
   for (int m = 0; m < c->N; ++m)
-    if (!F[m]) return fail(NTF_ERR_INVALID_ARG, "null factor %d", m);
+    if (!F[m] || misaligned(F[m], sizeof(float)))
+      return fail(NTF_ERR_INVALID_ARG, "null or misaligned factor %d", m);
   const int last = c->N - 1;
   NTF_TRY(ntf_mttkrp(c, last, F, c->Mbuf));
   const int64_t RR = static_cast<int64_t>(c->R) * c->R;
@@ -961,6 +977,8 @@ ntf_status ntf_fit(ntf_ctx* c, const float* const* F, double* rel_err) {
 ntf_status ntf_fit_from_mttkrp(ntf_ctx* c, const float* d_M_last, const float* d_F_last,
                                double* rel_err) {
   if (!c || !d_M_last || !d_F_last || !rel_err) return fail(NTF_ERR_INVALID_ARG, "null argument");
+  if (misaligned(d_M_last, sizeof(float)) || misaligned(d_F_last, sizeof(float)))
+    return fail(NTF_ERR_INVALID_ARG, "misaligned matrix");
   NTF_CUDA(ntf::launch_fit(d_M_last, d_F_last, c->dims[c->N - 1], c->R, c->grams, c->N,
                            c->fit_part, c->d_ctrl, c->st));
   NTF_TRY(read_ctrl(c));
@@ -1066,6 +1084,10 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   if (check_every < 1) check_every = 1;
   for (int m = 0; m < c->N; ++m)
     if (!A[m] || !At[m] || !Y[m]) return fail(NTF_ERR_INVALID_ARG, "null state of factor %d", m);
+  for (int m = 0; m < c->N; ++m)
+    if (misaligned(A[m], sizeof(float)) || misaligned(At[m], sizeof(float)) ||
+        misaligned(Y[m], sizeof(float)))
+      return fail(NTF_ERR_INVALID_ARG, "misaligned state of factor %d", m);
   const bool use_res = c->prm.eps_abs > 0.0 || c->prm.eps_rel > 0.0;
   const bool use_tgt = target_rfe > 0.0;
   if (rfe_hist)
@@ -1221,6 +1243,8 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
 
 ntf_status ntf_to_bf16(const float* d_in, uint16_t* d_out, int64_t n, void* stream) {
   if (!d_in || !d_out || n < 0) return fail(NTF_ERR_INVALID_ARG, "bad argument");
+  if (misaligned(d_in, sizeof(float)) || misaligned(d_out, sizeof(uint16_t)))
+    return fail(NTF_ERR_INVALID_ARG, "input or output not aligned to its element size");
   if (n == 0) return NTF_OK;
   // the input is read through its device address: device memory as it is, page-locked host
   // memory through the address the device maps it at; anything else is refused

@@ -46,9 +46,15 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
       (dtype != NTF_F32 && dtype != NTF_BF16) || !d_tensor || !d_factors || !d_M || mode < 0 ||
       mode >= order)
     return NTF_ERR_INVALID_ARG;
+  // device arrays are read with loads of their element type: pointers must be multiples of it
+  const auto misaligned = [](const void* p, uintptr_t elem) {
+    return reinterpret_cast<uintptr_t>(p) % elem != 0;
+  };
+  if (misaligned(d_tensor, dtype == NTF_BF16 ? 2 : 4) || misaligned(d_M, 4))
+    return NTF_ERR_INVALID_ARG;
   for (int m = 0; m < order; ++m) {
     if (dims[m] < 1 || dims[m] > (int64_t{1} << 30)) return NTF_ERR_INVALID_ARG;
-    if (m != mode && !d_factors[m]) return NTF_ERR_INVALID_ARG;
+    if (m != mode && (!d_factors[m] || misaligned(d_factors[m], 4))) return NTF_ERR_INVALID_ARG;
   }
   // The same two contractions as the context path: the leading factors' modes come from
   // X[P_R, Q_R] * KR(trailing factors), the others from X[P_L, Q_L]^T * KR(leading factors).

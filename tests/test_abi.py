@@ -144,3 +144,22 @@ def test_binding_constants_match_the_header():
             assert ntf.STATUS[value] == name
         else:
             assert getattr(ntf, name) == value, name
+
+
+def test_misaligned_pointers_are_refused_before_any_launch(lib):
+    """Pointers that are not multiples of their element size are invalid arguments (the
+    kernels read every array with loads of its element type at least)."""
+    from paper_1409_2383_gb300 import ntf
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    p = ntf.default_params()
+    for dtype, ptr in ((0, 18), (0, 17), (1, 17)):
+        st = lib.ntf_create(ctypes.byref(h), 3, dims, 3, dtype, ptr, ctypes.byref(p), None)
+        assert st == 1 and not h.value and b"aligned" in lib.ntf_last_error()
+    assert lib.ntf_to_bf16(18, 16, 4, None) == 1
+    assert lib.ntf_to_bf16(16, 17, 4, None) == 1
+    ok = (ctypes.c_void_p * 3)(16, 16, 16)
+    bad = (ctypes.c_void_p * 3)(16, 18, 16)
+    assert lib.ntf_mttkrp_noalloc(3, dims, 3, 0, 18, 0, ok, 16, None) == 1   # tensor
+    assert lib.ntf_mttkrp_noalloc(3, dims, 3, 0, 16, 0, bad, 16, None) == 1  # factor 1
+    assert lib.ntf_mttkrp_noalloc(3, dims, 3, 0, 16, 0, ok, 18, None) == 1   # output
