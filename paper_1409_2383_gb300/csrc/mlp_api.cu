@@ -60,6 +60,9 @@ void mlp_free(ntf_mlp* n) {
   delete n;
 }
 
+// Device arrays are read with loads of their element type (4 bytes here) at least.
+bool misaligned4(const void* p) { return reinterpret_cast<uintptr_t>(p) % 4 != 0; }
+
 ntf_status check_batch(const ntf_mlp* n, int groups, int rows) {
   if (!n) return mfail(NTF_ERR_INVALID_ARG, "null network");
   if (groups < 1 || groups > n->max_groups || rows < 1 || rows > n->max_rows)
@@ -180,6 +183,8 @@ ntf_status ntf_mlp_forward(ntf_mlp* n, const float* d_Gn, const int* d_offsets, 
   ntf_status s = check_batch(n, groups, rows);
   if (s != NTF_OK) return s;
   if (!d_Gn || !d_offsets || !d_mrows || !d_out) return mfail(NTF_ERR_INVALID_ARG, "null pointer");
+  if (misaligned4(d_Gn) || misaligned4(d_offsets) || misaligned4(d_mrows) || misaligned4(d_out))
+    return mfail(NTF_ERR_INVALID_ARG, "pointer not aligned to its element size");
   s = forward_batch(n, d_Gn, d_offsets, groups, d_mrows, rows, n->st);
   if (s != NTF_OK) return s;
   MLP_CUDA(cudaMemcpyAsync(d_out, n->out, static_cast<size_t>(rows) * n->s.Dout * 4,
@@ -193,6 +198,9 @@ ntf_status ntf_mlp_train_step(ntf_mlp* n, const float* d_Gn, const int* d_offset
   ntf_status s = check_batch(n, groups, rows);
   if (s != NTF_OK) return s;
   if (!d_Gn || !d_offsets || !d_mrows || !d_targets) return mfail(NTF_ERR_INVALID_ARG, "null pointer");
+  if (misaligned4(d_Gn) || misaligned4(d_offsets) || misaligned4(d_mrows) ||
+      misaligned4(d_targets) || misaligned4(d_grad_out))
+    return mfail(NTF_ERR_INVALID_ARG, "pointer not aligned to its element size");
   s = forward_batch(n, d_Gn, d_offsets, groups, d_mrows, rows, n->st);
   if (s != NTF_OK) return s;
   const int offs_h[2] = {0, rows};
