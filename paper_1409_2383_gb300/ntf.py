@@ -162,9 +162,12 @@ def _ptr_array(ts: Sequence[Optional[torch.Tensor]]):
     return arr
 
 
-def _mat(t: torch.Tensor, rows: int, R: int, name: str, dtype=torch.float32) -> None:
+def _mat(t: torch.Tensor, rows: int, R: int, name: str, dtype=torch.float32,
+         device: Optional[torch.device] = None) -> None:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the tensor on {device}")
     if t.dtype != dtype or tuple(t.shape) != (rows, R) or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape ({rows}, {R}); "
                          f"got {t.dtype} {tuple(t.shape)}")
@@ -198,10 +201,10 @@ def mttkrp_noalloc(X: torch.Tensor, mode: int, F: Sequence[Optional[torch.Tensor
     R = next(int(t.shape[1]) for m, t in enumerate(F) if m != mode)
     for m, t in enumerate(F):
         if m != mode:
-            _mat(t, dims[m], R, f"factor {m}")
+            _mat(t, dims[m], R, f"factor {m}", device=X.device)
     if out is None:
         out = torch.empty(dims[mode], R, device=X.device)
-    _mat(out, dims[mode], R, "out")
+    _mat(out, dims[mode], R, "out", device=X.device)
     cdims = (_I64 * len(dims))(*dims)
     dtype = NTF_F32 if X.dtype == torch.float32 else NTF_BF16
     _check(lib().ntf_mttkrp_noalloc(len(dims), cdims, R, dtype, _ptr(X), mode, _ptr_array(F),
@@ -262,21 +265,21 @@ class Context:
             raise ValueError(f"need {self.N} factors")
         for m, t in enumerate(F):
             if m != skip:
-                _mat(t, self.dims[m], self.R, f"factor {m}")
+                _mat(t, self.dims[m], self.R, f"factor {m}", device=self.X.device)
         return _ptr_array(F)
 
     def mttkrp(self, mode: int, F: Sequence[Optional[torch.Tensor]],
                out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
             out = torch.empty(self.dims[mode], self.R, device=self.X.device)
-        _mat(out, self.dims[mode], self.R, "out")
+        _mat(out, self.dims[mode], self.R, "out", device=self.X.device)
         _check(lib().ntf_mttkrp(self._h, mode, self._factors(F, skip=mode), _ptr(out)))
         return out
 
     def gram(self, mode: int, F: torch.Tensor, out: Optional[torch.Tensor] = None):
-        _mat(F, self.dims[mode], self.R, "F")
+        _mat(F, self.dims[mode], self.R, "F", device=self.X.device)
         if out is not None:
-            _mat(out, self.R, self.R, "out", torch.float64)
+            _mat(out, self.R, self.R, "out", torch.float64, self.X.device)
         _check(lib().ntf_gram(self._h, mode, _ptr(F), _ptr(out)))
         return out
 
@@ -284,7 +287,7 @@ class Context:
                L: Optional[torch.Tensor] = None) -> float:
         for t, n in ((H, "H"), (L, "L")):
             if t is not None:
-                _mat(t, self.R, self.R, n, torch.float64)
+                _mat(t, self.R, self.R, n, torch.float64, self.X.device)
         rho = ctypes.c_double()
         _check(lib().ntf_system(self._h, mode, _ptr(H), _ptr(L), ctypes.byref(rho)))
         return rho.value
@@ -292,7 +295,7 @@ class Context:
     def admm_update(self, mode: int, M: torch.Tensor, A: torch.Tensor, At: torch.Tensor,
                     Y: torch.Tensor, stats: bool = True):
         for t, n in ((M, "M"), (A, "A"), (At, "At"), (Y, "Y")):
-            _mat(t, self.dims[mode], self.R, n)
+            _mat(t, self.dims[mode], self.R, n, device=self.X.device)
         st = UpdateStats() if stats else None
         _check(lib().ntf_admm_update(self._h, mode, _ptr(M), _ptr(A), _ptr(At), _ptr(Y),
                                      ctypes.byref(st) if st is not None else None))
@@ -314,8 +317,8 @@ class Context:
         return v.value
 
     def fit_from_mttkrp(self, M_last: torch.Tensor, F_last: torch.Tensor) -> float:
-        _mat(M_last, self.dims[-1], self.R, "M_last")
-        _mat(F_last, self.dims[-1], self.R, "F_last")
+        _mat(M_last, self.dims[-1], self.R, "M_last", device=self.X.device)
+        _mat(F_last, self.dims[-1], self.R, "F_last", device=self.X.device)
         v = ctypes.c_double()
         _check(lib().ntf_fit_from_mttkrp(self._h, _ptr(M_last), _ptr(F_last), ctypes.byref(v)))
         return v.value
