@@ -154,6 +154,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cores() -> int:
+    """Cores this process may run on (its CPU affinity; the whole host's count as fallback):
+    the threads the oracle's BLAS calls spread over."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -209,7 +218,7 @@ def run_reference(args):
     n_iter, _ = _stored_iterations()
     sec = cpu_oracle_seconds_per_iteration(X, init, args.warmup + args.steps)
     value = sec * n_iter
-    cores = os.cpu_count()
+    cores = host_cores()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1000.0,
@@ -439,7 +448,7 @@ def run_ntf(args):
         n_cpu = 2
         sec = cpu_oracle_seconds_per_iteration(X, init, n_cpu)
         n_it, _ = _stored_iterations()
-        cpu = {"value": sec * n_it, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": sec * n_it, "unit": "s", "cores": host_cores(), "kind": "oracle",
                "sample": f"{n_cpu} FP64 oracle outer iterations of {WORKLOAD} (median "
                          f"{sec:.2f} s) x the {n_it} iterations the oracle needs to reach the "
                          "fit (stored oracle trajectory)"}
