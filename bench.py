@@ -601,10 +601,12 @@ def study_case(dims, F, sigma2, realizations, n_max, max_restarts, open_ctx, dev
             statistics.mean(iters), "mean_iters_total": statistics.mean(total)}
 
 
-def run_study(args):
+def run_study(args, open_ctx=None, device="cuda"):
     """The paper's Table 1 scenarios on the GPU in paper mode (L = 1, primal Khatri-Rao,
     adaptive rho, eps_abs = eps_rel = 1e-4, n_max = 400, restarts): one JSON line per
-    scenario with the mean RFE beside the printed one and the time per factorization."""
+    scenario with the mean RFE beside the printed one and the time per factorization.
+    (open_ctx / device: a stand-in context on the host, for tests of the loop.)"""
+    import contextlib
     import torch
     from paper_1409_2383_gb300 import ntf
     p = ntf.default_params(paper_mode=True)
@@ -612,12 +614,17 @@ def run_study(args):
     if args.study_cases:
         keep = {int(i) for i in args.study_cases.split(",")}
         cases = [c for i, c in enumerate(cases) if i in keep]
-    stream = torch.cuda.Stream()           # a non-default stream: sweeps replay as CUDA graphs
+    if device == "cuda":
+        stream = torch.cuda.Stream()       # a non-default stream: sweeps replay as CUDA graphs
+        scope, sync = (lambda: torch.cuda.stream(stream)), torch.cuda.synchronize
+        if open_ctx is None:
+            open_ctx = lambda X, R: ntf.Context(X, R, p, stream=stream)  # noqa: E731
+    else:
+        scope, sync = contextlib.nullcontext, (lambda: None)
     for dims, F, s2, printed in cases:
-        with torch.cuda.stream(stream):
+        with scope():
             res = study_case(dims, F, s2, args.realizations, 400, args.max_restarts,
-                             lambda X, R: ntf.Context(X, R, p, stream=stream), "cuda",
-                             torch.cuda.synchronize)
+                             open_ctx, device, sync)
         res.update({"study": "table1", "printed_mean_rfe": printed,
                     "rfe_vs_printed": res["mean_rfe"] / printed, "data": "synthetic",
                     "settings": "L=1, kr_source=primal, adaptive rho (1, 8, 4, 2), "

@@ -213,3 +213,38 @@ def test_table1_study_loop_on_a_stand_in_context():
     X1 = synth.workload(dims, F, seed=1, snr_db=None, sigma2=1e-2)[0]
     assert res["mean_rfe"] == pytest.approx((np.abs(X0).mean() + np.abs(X1).mean()) / 2,
                                             rel=1e-6)
+
+
+def test_table1_study_lines(capsys):
+    """run_study prints one JSON line per chosen scenario, the mean error beside the printed
+    one (stand-in context on the host whose error is the printed value)."""
+    import json
+    bench = _bench()
+
+    class Args:
+        study_cases, realizations, max_restarts = "8", 2, 0
+
+    class Ctx:
+        def __init__(self, X, R):
+            pass
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            pass
+
+        def run(self, A, At, Y, n_max, target_rfe=0.0, check_every=1):
+            return {"iters": 40, "converged": 1, "reached_target": 0, "rel_err": 0.0}
+
+        def fit(self, F):
+            return 0.14
+
+    bench.run_study(Args(), open_ctx=Ctx, device="cpu")
+    lines = [json.loads(ln) for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["study"] == "table1" and d["dims"] == [200, 200, 200] and d["F"] == 5
+    assert d["sigma2"] == 1e-2 and d["printed_mean_rfe"] == 0.14
+    assert d["rfe_vs_printed"] == pytest.approx(1.0) and d["converged"] == 2
+    assert d["mean_iters_total"] == 40 and d["mean_restarts"] == 0
