@@ -222,7 +222,7 @@ def test_table1_study_lines(capsys):
     bench = _bench()
 
     class Args:
-        study_cases, realizations, max_restarts = "8", 2, 0
+        study, study_cases, realizations, max_restarts = "table1", "8", 2, 0
 
     class Ctx:
         def __init__(self, X, R):
