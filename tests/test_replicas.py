@@ -163,6 +163,69 @@ def test_slab_partitioned_mttkrp_two_gloo_ranks():
     assert res == [(0, True, True), (1, True, True)]
 
 
+def _slab_iteration_worker(rank, world, port, out):
+    """Sec. V-B on the oracle: whole outer iterations with the tensor and the first factor's
+    rows split into slabs over the ranks.  The first factor's update is row-local (its
+    coefficient matrix needs only the replicated factors); the others take their MTTKRP and
+    the first factor's Gram as sums over the slabs (one all-reduce each) and are then updated
+    identically on every rank.  The result equals the centralized iteration."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    from oracle import ntf as o
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dims, R, L = (11, 7, 6), 3, 5
+        X = synth.workload(dims, R, seed=3, snr_db=20.0)[0].astype(np.float64)
+        init = synth.init_factors(dims, R, 4)
+        ref = o.init_state(init, o.AO)
+        lo, hi = rank * dims[0] // world, (rank + 1) * dims[0] // world
+        At = [init[0][lo:hi].copy(), init[1].copy(), init[2].copy()]
+        Y = [np.zeros_like(F) for F in At]
+
+        def allsum(a):
+            t = torch.as_tensor(np.ascontiguousarray(a))
+            dist.all_reduce(t)
+            return t.numpy()
+
+        for _ in range(2):
+            o.outer_iteration(X, ref, o.AO)
+            Xs = X[lo:hi]
+            # factor 1: rows of this slab, coefficient matrix from the replicated factors
+            G = o.gram(At[1]) * o.gram(At[2])
+            _, At[0], Y[0], _ = o.admm_factor_update(o.mttkrp(Xs, At, 0), G, At[0], Y[0],
+                                                     o.rho_trace(G), L)
+            GA = allsum(o.gram(At[0]))       # Gram of the split factor: a sum over slabs
+            for n in (1, 2):
+                M = allsum(o.mttkrp(Xs, At, n))
+                G = GA * o.gram(At[3 - n])
+                _, At[n], Y[n], _ = o.admm_factor_update(M, G, At[n], Y[n], o.rho_trace(G), L)
+        ok = (np.allclose(At[0], ref.aux[0][lo:hi], rtol=1e-10, atol=1e-13)
+              and np.allclose(Y[0], ref.dual[0][lo:hi], rtol=1e-10, atol=1e-13)
+              and all(np.allclose(At[n], ref.aux[n], rtol=1e-10, atol=1e-13) and
+                      np.allclose(Y[n], ref.dual[n], rtol=1e-10, atol=1e-13) for n in (1, 2)))
+        out.put((rank, ok))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_slab_partitioned_outer_iterations_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_iteration_worker, args=(r, 2, port, out))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, True), (1, True)]
+
+
 def test_table1_study_loop_on_a_stand_in_context():
     """The Table 1 study of bench.py (paper mode with restarts, Sec. VI-A): the scenarios come
     from the stored fixture; every attempt starts from its own random B0, C0 with zero
