@@ -36,25 +36,43 @@ ntf_status scratch_on_current_device(float** out) {
   return NTF_OK;
 }
 
+// The device that `p` lives on, if it is device (or managed) memory of that device; -1 for
+// host memory, memory of no CUDA allocation, or a failed query.  cudaPointerGetAttributes
+// allocates nothing.
+int device_of(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return -1;
+  return at.device;
+}
+
 }  // namespace
 
 extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int rank, int dtype,
                                          const void* d_tensor, int mode,
                                          const float* const* d_factors, float* d_M,
                                          void* stream) {
+  using ntf::record_error;
   if (order < 3 || order > ntf::kMaxOrder || !dims || rank < 1 || rank > ntf::kMaxRank ||
       (dtype != NTF_F32 && dtype != NTF_BF16) || !d_tensor || !d_factors || !d_M || mode < 0 ||
       mode >= order)
-    return NTF_ERR_INVALID_ARG;
+    return record_error(NTF_ERR_INVALID_ARG,
+                        "ntf_mttkrp_noalloc: invalid order, rank, dtype, mode or null pointer");
   // device arrays are read with loads of their element type: pointers must be multiples of it
   const auto misaligned = [](const void* p, uintptr_t elem) {
     return reinterpret_cast<uintptr_t>(p) % elem != 0;
   };
   if (misaligned(d_tensor, dtype == NTF_BF16 ? 2 : 4) || misaligned(d_M, 4))
-    return NTF_ERR_INVALID_ARG;
+    return record_error(NTF_ERR_INVALID_ARG, "ntf_mttkrp_noalloc: misaligned tensor or output");
   for (int m = 0; m < order; ++m) {
-    if (dims[m] < 1 || dims[m] > (int64_t{1} << 30)) return NTF_ERR_INVALID_ARG;
-    if (m != mode && (!d_factors[m] || misaligned(d_factors[m], 4))) return NTF_ERR_INVALID_ARG;
+    if (dims[m] < 1 || dims[m] > (int64_t{1} << 30))
+      return record_error(NTF_ERR_INVALID_ARG, "ntf_mttkrp_noalloc: dims[%d] out of range", m);
+    if (m != mode && (!d_factors[m] || misaligned(d_factors[m], 4)))
+      return record_error(NTF_ERR_INVALID_ARG,
+                          "ntf_mttkrp_noalloc: factor %d is null or misaligned", m);
   }
   // The same two contractions as the context path: the leading factors' modes come from
   // X[P_R, Q_R] * KR(trailing factors), the others from X[P_L, Q_L]^T * KR(leading factors).
@@ -67,7 +85,9 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
   }
   if (P_R >= (int64_t{1} << 31) || Q_R >= (int64_t{1} << 31) || P_L >= (int64_t{1} << 31) ||
       Q_L >= (int64_t{1} << 31))
-    return NTF_ERR_UNSUPPORTED;
+    return record_error(NTF_ERR_UNSUPPORTED,
+                        "ntf_mttkrp_noalloc: a matrix view of the tensor has 2^31 or more "
+                        "entries");
   const int R = rank;
   const bool left = mode < s_R;
   const int first = left ? 0 : s_L;
@@ -79,12 +99,30 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
   // otherwise it is an intermediate in scratch, after the Khatri-Rao table.
   const int64_t t_floats = count == 1 ? 0 : rows * R;
   const int64_t room = kScratchFloats - w_floats - t_floats;
-  if (room < 0) return NTF_ERR_INVALID_ARG;
+  if (room < 0)
+    return record_error(NTF_ERR_INVALID_ARG,
+                        "ntf_mttkrp_noalloc: mode %d needs %lld scratch floats (Khatri-Rao "
+                        "table %lld + intermediate %lld), more than the %lld of the static "
+                        "scratch array",
+                        mode, static_cast<long long>(w_floats + t_floats),
+                        static_cast<long long>(w_floats), static_cast<long long>(t_floats),
+                        static_cast<long long>(kScratchFloats));
 
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return NTF_ERR_CUDA;
+  if (e != cudaSuccess)
+    return record_error(NTF_ERR_CUDA, "ntf_mttkrp_noalloc: %s", cudaGetErrorString(e));
+  // every array the kernels touch must be memory of the current device: the kernels run there
+  if (device_of(d_tensor) != dev || device_of(d_M) != dev)
+    return record_error(NTF_ERR_INVALID_ARG,
+                        "ntf_mttkrp_noalloc: the tensor and the output must be device memory "
+                        "of the current device (%d)", dev);
+  for (int m = 0; m < order; ++m)
+    if (m != mode && device_of(d_factors[m]) != dev)
+      return record_error(NTF_ERR_INVALID_ARG,
+                          "ntf_mttkrp_noalloc: factor %d is not device memory of the current "
+                          "device (%d)", m, dev);
   ntf::GemmPlan plan = left ? ntf::plan_gemm_n(P_R, Q_R, dtype, d_tensor, sms)
                             : ntf::plan_gemm_t(P_L, Q_L, dtype, d_tensor, sms);
   // Partial sums of a split contraction range use what is left of the scratch; when they do
@@ -103,7 +141,9 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
 
   float* scratch = nullptr;
   ntf_status st = scratch_on_current_device(&scratch);
-  if (st != NTF_OK) return st;
+  if (st != NTF_OK)
+    return record_error(st, "ntf_mttkrp_noalloc: the scratch array's device address was not "
+                            "found on device %d", dev);
   float* W = scratch;
   float* T = count == 1 ? d_M : scratch + w_floats;
   float* part = scratch + w_floats + t_floats;
@@ -132,6 +172,8 @@ extern "C" ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int ran
     else
       e = ntf::launch_post_slow(T, Ia, Ib, R, d_factors[first], post_splits, part, d_M, cs);
   }
-  if (e != cudaSuccess) return NTF_ERR_CUDA;
+  if (e != cudaSuccess)
+    return record_error(NTF_ERR_CUDA, "ntf_mttkrp_noalloc: launch failed: %s",
+                        cudaGetErrorString(e));
   return NTF_OK;
 }
