@@ -1,19 +1,26 @@
 """Benchmark: time to relative fit 1e-3 of ADMoM non-negative CP factorization on GB300.
 
-One step = one whole factorization of the 400x400x400 rank-20 workload (U[0,1] factors,
-20 dB Gaussian noise, data seed 0, uniform start of seed 1; L = 5 inner iterations,
-Khatri-Rao of the auxiliaries, rho = trace(G)/R) from the start until the relative error is
-within 1e-3 of the converged value RFE* (RFE_k <= RFE* (1 + 1e-3)), where RFE* is the error
-of the plain FP32 method after the workload's 200 outer iterations, found during warm-up.
-The timed form (--form) defaults to BF16 tensor storage with the learned warm start in the
-first sweep (network trained before the timed region on rows of other tensors of the same
-generator; its harvest and training times are reported apart); plain FP32 and plain BF16
-are timed to the same target as variants.  The metric is the time of one factorization
-(lower is better); the same JSON line carries the live roofline of the dominant tensor
-contraction (HBM GB/s from CUDA events inside the timed steps), an end-to-end time through
-host buffers, and the FP64 oracle timed on the host cores.
+One step = one whole factorization of the workload (default: the 1000x1000x1000 rank-32
+tensor, U[0,1] factors, 30 dB Gaussian noise, drawn on the device; L = 5 inner iterations,
+Khatri-Rao of the auxiliaries, rho = trace(G)/R, uniform start) from the start until the
+relative error is within 1e-3 of the converged value RFE* (RFE_k <= RFE* (1 + 1e-3)), RFE*
+the error of the plain FP32 method after the workload's outer-iteration budget, found
+before the timed region.  The timed form (--form) defaults to BF16 tensor storage with the
+learned warm start in the first sweep (network trained before the timed region on rows of
+other tensors of the same generator; harvest and training times reported apart).  Every form
+(plain FP32, plain BF16, BF16 + learned) is also timed to the fit target and to the same
+KKT tolerance (eq. KKT_NTF: the scaled dual infeasibility and complementarity of every
+factor's last update), and the learned form is compared with plain BF16 on held-out tensors.
+The other workloads of the evaluation (600^3 rank 50 with sparse factors, the 4-way
+200x200x200x50 rank-16 collinear stress case) are measured the same way under `variants`,
+each with the live roofline of its dominant contraction.  The metric is the time of one
+factorization (lower is better); the JSON line carries the live roofline of the dominant
+tensor contraction (HBM GB/s from CUDA events inside the timed steps), an end-to-end time
+through host buffers, and the FP64 oracle timed on the host cores (on a slab of the tensor,
+scaled: extrapolated).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ntf|reference]
+                  [--workload NAME] [--no-variants]
 
 Multi-GPU: replicas only (each rank factorizes its own tensor of a different seed; no
 collective on the data path); value = max over ranks of the time per factorization.
@@ -42,9 +49,32 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to rel. fit 1e-3 (s) & MTTKRP HBM GB/s; BF16+learned vs plain FP32 GPU"
-WORKLOAD = "400x400x400_r20"
-DIMS, RANK, SNR_DB, MAX_OUTER = (400, 400, 400), 20, 20.0, 200
 FIT_TOL = 1e-3
+
+# The evaluation workloads (the recipe of synth.WORKLOADS, drawn on the device).  max_outer:
+# the outer-iteration budget whose plain FP32 error defines the fit target.  kkt: the common
+# KKT tolerance (scaled dual infeasibility, scaled complementarity) every form is run to.
+# fit_iters: outer iterations the plain FP32 method needs to reach the fit target (measured on
+# GB300; the FP64 oracle runs the same iteration and tracks it within 1e-4 in the error), used
+# to scale the oracle's per-iteration time into a time to fit.
+WORKLOADS = {
+    "1000x1000x1000_r32": dict(dims=(1000, 1000, 1000), R=32, snr_db=30.0,
+                               structure="uniform", max_outer=300, kkt=(1e-4, 1e-6),
+                               fit_iters=77),
+    "600x600x600_r50_sparse": dict(dims=(600, 600, 600), R=50, snr_db=20.0,
+                                   structure="sparse", max_outer=200, kkt=(1e-4, 1e-6),
+                                   fit_iters=13),
+    "200x200x200x50_r16_collinear": dict(dims=(200, 200, 200, 50), R=16, snr_db=10.0,
+                                         structure="collinear", max_outer=300,
+                                         kkt=(1e-4, 1e-6), fit_iters=52),
+    "400x400x400_r20": dict(dims=(400, 400, 400), R=20, snr_db=20.0, structure="uniform",
+                            max_outer=200, kkt=(1e-4, 1e-6), fit_iters=43),
+}
+DEFAULT_WORKLOAD = "1000x1000x1000_r32"
+# measured beside the default workload, under `variants`
+VARIANT_WORKLOADS = ("600x600x600_r50_sparse", "200x200x200x50_r16_collinear")
+# oracle sample: a slab of the tensor over its last mode with at most this many entries
+ORACLE_SAMPLE_NUMEL = 100_000_000
 
 
 def _peaks():
@@ -171,10 +201,28 @@ def _dist():
     return world, rank, local
 
 
-def _workload(seed: int):
+def device_workload(name: str, seed: int):
+    """(X FP32 on the device, start factors) of a named workload, drawn on the device."""
+    from paper_1409_2383_gb300 import warmstart
+    w = WORKLOADS[name]
+    return warmstart.synthetic_tensor(w["dims"], w["R"], seed=seed, snr_db=w["snr_db"],
+                                      structure=w["structure"])
+
+
+def oracle_sample(name: str, seed: int = 0):
+    """The oracle's bounded sample of a workload: the first slab of the tensor over its last
+    mode with at most ORACLE_SAMPLE_NUMEL entries, drawn by the host generator with the
+    workload's recipe (the whole tensor if it is small).  Returns (X, start factors, scale):
+    scale = the full tensor's entries over the slab's."""
     import synth
-    X, _, init = synth.workload(DIMS, RANK, seed=seed, snr_db=SNR_DB)
-    return X, [f.astype(np.float32) for f in init]
+    w = WORKLOADS[name]
+    dims = list(w["dims"])
+    full = math.prod(dims)
+    rest = full // dims[-1]
+    dims[-1] = max(1, min(dims[-1], ORACLE_SAMPLE_NUMEL // rest))
+    kw = {} if w["structure"] == "uniform" else {"structure": w["structure"]}
+    X, _, init = synth.workload(tuple(dims), w["R"], seed=seed, snr_db=w["snr_db"], **kw)
+    return X, [f.astype(np.float32) for f in init], full / math.prod(dims)
 
 
 def cpu_oracle_seconds_per_iteration(X, init, sweeps: int):
@@ -191,16 +239,6 @@ def cpu_oracle_seconds_per_iteration(X, init, sweeps: int):
     return statistics.median(ts)
 
 
-def _stored_iterations():
-    """Outer iterations the oracle needs to reach RFE <= RFE*(1+1e-3) on this workload, from
-    the stored oracle trajectory (tests/golden, written by oracle/trajectory.py)."""
-    path = os.path.join(ROOT, "tests", "golden", f"trajectory_{WORKLOAD}.json")
-    with open(path) as f:
-        h = json.load(f)["rfe"]
-    target = h[-1] * (1 + FIT_TOL)
-    return next(i + 1 for i, v in enumerate(h) if v <= target), len(h)
-
-
 def max_over_ranks(values, device):
     """Whole-job figures of a replicas run: the maximum over ranks of each value (the slowest
     rank sets the job's time).  One all-reduce of a small vector; nothing else is exchanged."""
@@ -211,27 +249,38 @@ def max_over_ranks(values, device):
     return t.tolist()
 
 
+def _workload_config(name: str) -> dict:
+    w = WORKLOADS[name]
+    return {"workload": name, "dims": list(w["dims"]), "rank": w["R"], "snr_db": w["snr_db"],
+            "structure": w["structure"], "inner_iters": 5, "rho": "trace(G)/R",
+            "kr_source": "aux", "fit_tol": FIT_TOL, "max_outer": w["max_outer"],
+            "kkt_tol": {"dual": w["kkt"][0], "comp": w["kkt"][1]}}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    X, init = _workload(0)
-    n_iter, _ = _stored_iterations()
-    sec = cpu_oracle_seconds_per_iteration(X, init, args.warmup + args.steps)
+    name = getattr(args, "workload", None) or DEFAULT_WORKLOAD
+    X, init, scale = oracle_sample(name)
+    n_iter = WORKLOADS[name]["fit_iters"]
+    sec = cpu_oracle_seconds_per_iteration(X, init, args.warmup + args.steps) * scale
     value = sec * n_iter
     cores = host_cores()
+    shape = "x".join(str(d) for d in X.shape)
+    sample = (f"{args.warmup + args.steps} oracle outer iterations on a {shape} slab of "
+              f"{name} (median, x {scale:g} for the full tensor: extrapolated) x the {n_iter} "
+              "outer iterations the method needs to reach the fit")
+    cfg = _workload_config(name)
+    cfg["step"] = ("one FP64 oracle outer iteration (slab, scaled); value = that time x the "
+                   f"{n_iter} iterations to the fit")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1000.0,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "snr_db": SNR_DB,
-                   "inner_iters": 5, "rho": "trace(G)/R", "fit_tol": FIT_TOL,
-                   "step": "one FP64 oracle outer iteration; value = median time x the "
-                           f"{n_iter} iterations the oracle needs to reach the fit"},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.warmup + args.steps} oracle outer iterations on "
-                                   f"{WORKLOAD}, median x {n_iter} iterations"},
+                         "sample": sample, "extrapolated": True},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -245,29 +294,32 @@ FORMS = {
 }
 
 
-def train_network(args):
-    """Warm-start network for the workload: rows harvested from the first sweeps of tensors
-    of the workload generator with other seeds (drawn on the device), trained by the
-    library's kernels.  Returns (network, report)."""
+def train_network(name: str, args):
+    """Warm-start network for a workload: rows harvested from the first sweeps of tensors of
+    the workload's generator with other seeds (drawn on the device), trained by the library's
+    kernels.  Returns (network, report)."""
     import torch
     from paper_1409_2383_gb300 import ntf, warmstart
+    w = WORKLOADS[name]
+    dims, R = w["dims"], w["R"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rows = warmstart.training_set(DIMS, RANK, args.train_rows, sweeps=args.ws_sweeps,
-                                  seed0=1000, snr_db=SNR_DB, storage="bf16")
+    rows = warmstart.training_set(dims, R, args.train_rows, sweeps=args.ws_sweeps,
+                                  seed0=1000, snr_db=w["snr_db"], storage="bf16",
+                                  structure=w["structure"])
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     H = 256
     groups, per_group = 256, 25                  # rows from many coefficient matrices per step
-    net = ntf.Mlp(RANK, H, warmstart.init_params(RANK, H, seed=0),
-                  max_rows=max(groups * per_group, 16 * max(DIMS)), max_groups=groups)
+    net = ntf.Mlp(R, H, warmstart.init_params(R, H, seed=0),
+                  max_rows=max(groups * per_group, 16 * max(dims)), max_groups=groups)
     loss0 = warmstart.eval_loss(net, rows, 16)
     steps = max(1, int(args.train_epochs * rows.rows / (groups * per_group)))
     warmstart.train(net, rows, steps=steps, groups_per_batch=groups, lr=1e-3, decay_at=0.7,
                     rows_per_group=per_group)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    rep = {"rows": rows.rows, "groups": len(rows.Gn), "tensor_dims": list(DIMS),
+    rep = {"rows": rows.rows, "groups": len(rows.Gn), "tensor_dims": list(dims),
            "sweeps_harvested": args.ws_sweeps, "ws_sweeps": args.ws_sweeps,
            "harvest_s": t1 - t0, "train_s": t2 - t1, "steps": steps, "hidden": H,
            "loss_before": loss0, "loss_after": warmstart.eval_loss(net, rows, 16)}
@@ -275,33 +327,139 @@ def train_network(args):
     return net, rep
 
 
-def robustness(args, net, p):
-    """Outer iterations and time to the fit, plain BF16 vs BF16 + learned warm start, on other
-    tensors of the workload generator (drawn on the device): the iteration count to a fit
-    target depends on the path through the slow phase of the factorization, so one tensor
-    says little about the warm start."""
+def _params(kkt=None):
+    from paper_1409_2383_gb300 import ntf
+    if kkt is None:
+        return ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    return ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0,
+                              kkt_dual_tol=kkt[0], kkt_comp_tol=kkt[1])
+
+
+def fit_target(X, R: int, init, max_outer: int) -> float:
+    """The error of the plain FP32 method after `max_outer` outer iterations, relaxed by the
+    fit tolerance: the target every form is timed to."""
+    import torch
+    from paper_1409_2383_gb300 import ntf
+    A = [f.clone() for f in init]
+    T = [f.clone() for f in init]
+    Y = [torch.zeros_like(f) for f in init]
+    with ntf.Context(X, R, _params()) as c:
+        rs = c.run(A, T, Y, max_outer, check_every=max_outer)
+    return rs["rel_err"] * (1 + FIT_TOL)
+
+
+def _roofline_of(prof, storage: str) -> dict:
+    """Live HBM roofline of the dominant contraction (more device time) from a profile."""
+    k = 0 if prof["contraction_ms"][0] >= prof["contraction_ms"][1] else 1
+    names = ["k_umma<0,...> (X * KR_right, tcgen05)", "k_umma<1,...> (X^T * KR_left, tcgen05)"]
+    kernel_ids = [f"k_umma_n_{storage}", f"k_umma_t_{storage}"]
+    avg_ms = prof["contraction_ms"][k] / max(prof["contractions"][k], 1)
+    bytes_ = prof["contraction_bytes"][k]
+    achieved = bytes_ / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    other = None
+    if prof["contractions"][1 - k]:
+        other = prof["contraction_bytes"][1 - k] / (
+            prof["contraction_ms"][1 - k] / prof["contractions"][1 - k] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": names[k], "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic_record(kernel_ids[k]), "algorithmic_bytes_per_launch": bytes_,
+            "avg_launch_ms": avg_ms, "other_contraction_gbs": other}
+
+
+def time_form(X32, R: int, init, storage: str, net, target: float, kkt, max_outer: int,
+              ws_sweeps: int, repeats: int = 3) -> dict:
+    """One form on one tensor: time (CUDA events, median of `repeats`) and outer iterations to
+    the fit target and to the KKT tolerance, the final error against the FP32 tensor, and the
+    live roofline of its dominant contraction."""
     import torch
     from paper_1409_2383_gb300 import ntf, warmstart
-    rows = []
-    for seed in range(100, 100 + args.robust_tensors):
-        X, init = warmstart.synthetic_tensor(DIMS, RANK, seed=seed, snr_db=SNR_DB)
+    from paper_1409_2383_gb300 import ntf as _n
+    Xf = _n.to_bf16(X32) if storage == "bf16" else X32
+    fit = warmstart.time_to_fit(Xf, R, init, target, max_outer, net=net, repeats=repeats,
+                                ws_sweeps=ws_sweeps)
+    kk = warmstart.time_to_fit(Xf, R, init, 0.0, max_outer, net=net, repeats=repeats,
+                               ws_sweeps=ws_sweeps, params=_params(kkt))
+    # the state after the KKT run: its error against the FP32 tensor and its live roofline
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
         A = [f.clone() for f in init]
         T = [f.clone() for f in init]
         Y = [torch.zeros_like(f) for f in init]
-        with ntf.Context(X, RANK, p) as c:
-            target = c.run(A, T, Y, MAX_OUTER, check_every=MAX_OUTER)["rel_err"] * (1 + FIT_TOL)
+        with ntf.Context(Xf, R, _params(kkt), stream=stream) as c:
+            if net is not None:
+                c.attach_warmstart(net, ws_sweeps)
+            c.profile_enable(True)
+            c.run(A, T, Y, max_outer)
+            prof = c.profile_get()
+        with ntf.Context(X32, R, _params(), stream=stream) as c32:
+            err32 = c32.fit(T)
+    del Xf
+    return {"fit": fit, "kkt": kk, "final_rfe_vs_fp32_tensor": err32,
+            "roofline": _roofline_of(prof, storage)}
+
+
+def robustness(name: str, args, net) -> dict:
+    """Outer iterations and time to the fit target and to the KKT tolerance, plain BF16 vs
+    BF16 + learned warm start, on held-out tensors of the workload's generator: the iteration
+    count depends on the path through the slow phase of the factorization, so one tensor says
+    little about the warm start."""
+    from paper_1409_2383_gb300 import ntf, warmstart
+    w = WORKLOADS[name]
+    rows = []
+    for seed in range(100, 100 + args.robust_tensors):
+        X, init = device_workload(name, seed)
+        target = fit_target(X, w["R"], init, w["max_outer"])
         Xb = ntf.to_bf16(X)
-        pl = warmstart.time_to_fit(Xb, RANK, init, target, MAX_OUTER)
-        le = warmstart.time_to_fit(Xb, RANK, init, target, MAX_OUTER, net=net,
-                                   ws_sweeps=args.ws_sweeps)
-        rows.append({"seed": seed, "plain_iters": pl["iters"], "learned_iters": le["iters"],
-                     "plain_s": pl["seconds"], "learned_s": le["seconds"]})
-        del X, Xb
-    return {"tensors": rows,
-            "mean_plain_iters": statistics.mean(r["plain_iters"] for r in rows),
-            "mean_learned_iters": statistics.mean(r["learned_iters"] for r in rows),
-            "mean_plain_s": statistics.mean(r["plain_s"] for r in rows),
-            "mean_learned_s": statistics.mean(r["learned_s"] for r in rows)}
+        del X
+        r = {"seed": seed}
+        for tag, nt in (("plain", None), ("learned", net)):
+            f = warmstart.time_to_fit(Xb, w["R"], init, target, w["max_outer"], net=nt,
+                                      ws_sweeps=args.ws_sweeps)
+            k = warmstart.time_to_fit(Xb, w["R"], init, 0.0, w["max_outer"], net=nt,
+                                      ws_sweeps=args.ws_sweeps, params=_params(w["kkt"]))
+            r[f"{tag}_fit_iters"], r[f"{tag}_fit_s"] = f["iters"], f["seconds"]
+            r[f"{tag}_kkt_iters"], r[f"{tag}_kkt_s"] = k["iters"], k["seconds"]
+            r[f"{tag}_kkt_met"] = k["kkt_met"]
+        rows.append(r)
+        del Xb
+    out = {"tensors": rows}
+    for key in ("fit_iters", "fit_s", "kkt_iters", "kkt_s"):
+        for tag in ("plain", "learned"):
+            vals = [r[f"{tag}_{key}"] for r in rows]
+            out[f"{tag}_{key}_mean"] = statistics.mean(vals)
+            out[f"{tag}_{key}_std"] = statistics.stdev(vals) if len(vals) > 1 else 0.0
+    out["learned_fewer_kkt_iters"] = sum(r["learned_kkt_iters"] < r["plain_kkt_iters"]
+                                         for r in rows)
+    out["learned_more_kkt_iters"] = sum(r["learned_kkt_iters"] > r["plain_kkt_iters"]
+                                        for r in rows)
+    return out
+
+
+def measure_workload(name: str, args, net=None, training=None) -> dict:
+    """Every form of a workload (seed 0) to the fit target and to the KKT tolerance, the
+    learned form's network (trained here unless given) and its held-out comparison."""
+    w = WORKLOADS[name]
+    X, init = device_workload(name, 0)
+    target = fit_target(X, w["R"], init, w["max_outer"])
+    if net is None and not args.no_learned:
+        net, training = train_network(name, args)
+    out = {"config": _workload_config(name), "target_rfe": target, "forms": {},
+           "training": training}
+    for form, (storage, learned) in FORMS.items():
+        if learned and net is None:
+            continue
+        out["forms"][form] = time_form(X, w["R"], init, storage, net if learned else None,
+                                       target, w["kkt"], w["max_outer"], args.ws_sweeps)
+    f = out["forms"]
+    if "fp32" in f:
+        for form in f:
+            f[form]["fit_speedup_vs_fp32"] = f["fp32"]["fit"]["seconds"] / f[form]["fit"]["seconds"]
+            f[form]["kkt_speedup_vs_fp32"] = f["fp32"]["kkt"]["seconds"] / f[form]["kkt"]["seconds"]
+    del X
+    if net is not None and args.robust_tensors > 0:
+        out["learned_vs_plain_held_out"] = robustness(name, args, net)
+    return out, net
 
 
 def run_ntf(args):
@@ -311,15 +469,15 @@ def run_ntf(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    from paper_1409_2383_gb300 import ntf, warmstart
+    from paper_1409_2383_gb300 import ntf
 
+    name = args.workload
+    w = WORKLOADS[name]
+    dims, R, max_outer = w["dims"], w["R"], w["max_outer"]
     storage, learned = FORMS[args.form]
-    X, init = _workload(rank)                # replicas: one tensor per rank
     stream = torch.cuda.Stream()
-    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
     with torch.cuda.stream(stream):
-        Xd = torch.as_tensor(X).cuda()
-        init_d = [torch.as_tensor(f).cuda() for f in init]
+        Xd, init_d = device_workload(name, rank)    # replicas: one tensor per rank
         A = [f.clone() for f in init_d]
         At = [f.clone() for f in init_d]
         Y = [torch.zeros_like(f) for f in init_d]
@@ -332,19 +490,20 @@ def run_ntf(args):
 
         # the fit target of every form: the converged error of the plain FP32 method within
         # the workload's iteration budget, relaxed by the fit tolerance
-        with ntf.Context(Xd, RANK, p, stream=stream) as c32:
+        target = fit_target(Xd, R, init_d, max_outer)
+        fp32_fit = None
+        with ntf.Context(Xd, R, _params(), stream=stream) as c32:
             reset()
-            full = c32.run(A, At, Y, MAX_OUTER, check_every=MAX_OUTER)
-        target = full["rel_err"] * (1 + FIT_TOL)
+            fp32_fit = c32.run(A, At, Y, max_outer, target_rfe=target)["iters"]
 
-        net, training = train_network(args) if learned else (None, None)
+        net, training = train_network(name, args) if learned else (None, None)
         Xf = ntf.to_bf16(Xd) if storage == "bf16" else Xd
-        ctx = ntf.Context(Xf, RANK, p, stream=stream)
+        ctx = ntf.Context(Xf, R, _params(), stream=stream)
         if net is not None:
             ctx.attach_warmstart(net, args.ws_sweeps)
         for _ in range(args.warmup):
             reset()
-            ctx.run(A, At, Y, MAX_OUTER, target_rfe=target)
+            ctx.run(A, At, Y, max_outer, target_rfe=target)
         stream.synchronize()
 
         # timed region: K factorizations to the target, inputs resident in HBM
@@ -358,7 +517,7 @@ def run_ntf(args):
             ev0.record(stream)
             for _ in range(args.steps):
                 reset()
-                rs = ctx.run(A, At, Y, MAX_OUTER, target_rfe=target)
+                rs = ctx.run(A, At, Y, max_outer, target_rfe=target)
                 iters.append(rs["iters"])
             ev1.record(stream)
             torch.cuda.synchronize()
@@ -370,16 +529,18 @@ def run_ntf(args):
         final_rfe = rs["rel_err"]
         ctx.close()
         # error of the form's factors against the FP32 tensor (BF16 storage rounds the data)
-        with ntf.Context(Xd, RANK, p, stream=stream) as c32:
+        with ntf.Context(Xd, R, _params(), stream=stream) as c32:
             rfe_vs_fp32 = c32.fit(At)
 
         # end to end through the public API with host buffers: H2D of the FP32 tensor and the
         # start (BF16 form: the conversion kernel reads the pinned host tensor, so the copy and
         # the conversion are one pass), context creation (||X||^2), the factorization, D2H of
         # the factors
-        Xh = torch.as_tensor(X).pin_memory()
-        init_h = [torch.as_tensor(f).pin_memory() for f in init]
+        Xh = Xd.cpu().pin_memory()
+        init_h = [f.cpu().pin_memory() for f in init_d]
         out_h = [torch.empty_like(f).pin_memory() for f in init_h]
+        if storage == "bf16":
+            del Xd                               # room for the end-to-end copies
         torch.cuda.synchronize()
         e2e_steps = max(1, min(args.steps, 5))
         t0 = time.perf_counter()
@@ -387,43 +548,43 @@ def run_ntf(args):
             if storage == "bf16":
                 Xe = ntf.to_bf16(Xh, stream)
             else:
-                Xe = torch.empty_like(Xd)
+                Xe = torch.empty(Xh.shape, dtype=torch.float32, device="cuda")
                 Xe.copy_(Xh, non_blocking=True)
-            Ae = [torch.empty_like(f) for f in init_d]
-            Te = [torch.empty_like(f) for f in init_d]
+            Ae = [torch.empty(f.shape, device="cuda") for f in init_h]
+            Te = [torch.empty(f.shape, device="cuda") for f in init_h]
             for a, t, f in zip(Ae, Te, init_h):
                 a.copy_(f, non_blocking=True)
                 t.copy_(f, non_blocking=True)
-            Ye = [torch.zeros_like(f) for f in init_d]
-            with ntf.Context(Xe, RANK, p, stream=stream) as c2:
+            Ye = [torch.zeros(f.shape, device="cuda") for f in init_h]
+            with ntf.Context(Xe, R, _params(), stream=stream) as c2:
                 if net is not None:
                     c2.attach_warmstart(net, args.ws_sweeps)
-                c2.run(Ae, Te, Ye, MAX_OUTER, target_rfe=target)
+                c2.run(Ae, Te, Ye, max_outer, target_rfe=target)
             for o_, t in zip(out_h, Te):
                 o_.copy_(t, non_blocking=True)
             stream.synchronize()
+            del Xe
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         h2d = Xh.numel() * 4 + 2 * sum(f.numel() * 4 for f in init_h)
         d2h = sum(f.numel() * 4 for f in out_h)
+        oracle_slab = None
+        if not args.no_cpu_baseline and rank == 0:
+            oracle_slab = oracle_sample(name)
+        del Xh, Xf
 
         variants = None
-        if not args.no_variants:
-            variants = {}
-            for name, (st_, lw) in FORMS.items():
-                if name == args.form:
+        if not args.no_variants and rank == 0:
+            torch.cuda.empty_cache()
+            main_meas, net = measure_workload(name, args, net=net, training=training)
+            variants = {name: main_meas}
+            for other in VARIANT_WORKLOADS:
+                if other == name:
                     continue
-                if lw and net is None:
-                    net, training = train_network(args)
-                Xv = ntf.to_bf16(Xd) if st_ == "bf16" else Xd
-                variants[name] = warmstart.time_to_fit(Xv, RANK, init_d, target, MAX_OUTER,
-                                                       net=net if lw else None, repeats=3,
-                                                       ws_sweeps=args.ws_sweeps)
-            variants[args.form] = {"seconds": ms / 1000.0, "iters": statistics.mean(iters),
-                                   "rel_err": final_rfe}
-            if net is not None and args.robust_tensors > 0:
-                variants["learned_vs_plain_other_tensors"] = robustness(args, net, p)
-            if "fp32" in variants:
-                variants["speedup_vs_fp32"] = variants["fp32"]["seconds"] / (ms / 1000.0)
+                torch.cuda.empty_cache()
+                meas, onet = measure_workload(other, args)
+                if onet is not None:
+                    onet.close()
+                variants[other] = meas
         if net is not None:
             net.close()
 
@@ -433,51 +594,39 @@ def run_ntf(args):
     if rank != 0:
         return
 
-    # roofline of the dominant contraction (more device time) of the timed form
-    k = 0 if prof["contraction_ms"][0] >= prof["contraction_ms"][1] else 1
-    names = ["k_umma<0,...> (X * KR_right, tcgen05)", "k_umma<1,...> (X^T * KR_left, tcgen05)"]
-    kernel_ids = [f"k_umma_n_{storage}", f"k_umma_t_{storage}"]
-    avg_ms = prof["contraction_ms"][k] / max(prof["contractions"][k], 1)
-    bytes_ = prof["contraction_bytes"][k]
-    achieved = bytes_ / (avg_ms * 1e-3) / 1e9
-    peak, peak_kind = _peaks()
-    traffic = _traffic_record(kernel_ids[k])
+    roofline = _roofline_of(prof, storage)
     sweep_ms = ms / statistics.mean(iters)
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if oracle_slab is not None:
+        Xs, init_s, scale = oracle_slab
         n_cpu = 2
-        sec = cpu_oracle_seconds_per_iteration(X, init, n_cpu)
-        n_it, _ = _stored_iterations()
-        cpu = {"value": sec * n_it, "unit": "s", "cores": host_cores(), "kind": "oracle",
-               "sample": f"{n_cpu} FP64 oracle outer iterations of {WORKLOAD} (median "
-                         f"{sec:.2f} s) x the {n_it} iterations the oracle needs to reach the "
-                         "fit (stored oracle trajectory)"}
+        sec = cpu_oracle_seconds_per_iteration(Xs, init_s, n_cpu) * scale
+        shape = "x".join(str(d) for d in Xs.shape)
+        cpu = {"value": sec * fp32_fit, "unit": "s", "cores": host_cores(), "kind": "oracle",
+               "extrapolated": True,
+               "sample": f"{n_cpu} FP64 oracle outer iterations on a {shape} slab of {name} "
+                         f"(median, x {scale:g} for the full tensor: {sec:.2f} s per "
+                         f"iteration) x the {fp32_fit} outer iterations the plain method "
+                         "needs to reach the fit"}
 
+    cfg = _workload_config(name)
+    cfg.update({"form": args.form, "storage": storage,
+                "accumulate": "f32 (Gram, coefficient system: f64)",
+                "warm_start": f"learned, first {args.ws_sweeps} sweep(s)" if learned else "none",
+                "target_rfe": target, "target_from": "plain FP32 converged error x (1 + tol)",
+                "final_rfe": final_rfe, "final_rfe_vs_fp32_tensor": rfe_vs_fp32,
+                "outer_iters_to_fit": statistics.mean(iters),
+                "fp32_outer_iters_to_fit": fp32_fit, "ms_per_outer_iter": sweep_ms,
+                "l2": "inputs larger than L2 (tensor streamed twice per iteration)",
+                "parallelism": "replicas" if world > 1 else "single GPU"})
     line = {
         "metric": METRIC, "value": value_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if storage == "bf16" else "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dims": list(DIMS), "rank": RANK, "snr_db": SNR_DB,
-                   "form": args.form, "storage": storage,
-                   "accumulate": "f32 (Gram, coefficient system: f64)",
-                   "warm_start": f"learned, first {args.ws_sweeps} sweep(s)" if learned
-                   else "none",
-                   "inner_iters": 5, "rho": "trace(G)/R", "kr_source": "aux",
-                   "fit_tol": FIT_TOL, "max_outer": MAX_OUTER,
-                   "target_rfe": target, "target_from": "plain FP32 converged error x (1 + tol)",
-                   "final_rfe": final_rfe, "final_rfe_vs_fp32_tensor": rfe_vs_fp32,
-                   "outer_iters_to_fit": statistics.mean(iters), "ms_per_outer_iter": sweep_ms,
-                   "l2": "inputs larger than L2 (tensor streamed twice per iteration)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": names[k], "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_,
-                     "avg_launch_ms": avg_ms,
-                     "other_contraction_gbs": prof["contraction_bytes"][1 - k] /
-                     (prof["contraction_ms"][1 - k] / max(prof["contractions"][1 - k], 1) * 1e-3)
-                     / 1e9 if prof["contractions"][1 - k] else None},
+        "data": "synthetic (drawn on the device with the workload's recipe)",
+        "config": cfg,
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(prof["kernel_launches"]),
@@ -526,14 +675,15 @@ def run_sweep_case(args):
     lists of the whole sweep): one eager sweep, then graph replays."""
     import torch
     from paper_1409_2383_gb300 import ntf
-    X, init = _workload(0)
-    Xd = torch.as_tensor(X).cuda()
+    w = WORKLOADS[args.workload]
+    RANK = w["R"]
+    Xd, init = device_workload(args.workload, 0)
     if args.storage == "bf16":
         Xd = ntf.to_bf16(Xd)
     p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        A = [torch.as_tensor(f).cuda() for f in init]
+        A = [f.clone() for f in init]
         At = [a.clone() for a in A]
         Y = [torch.zeros_like(a) for a in A]
         with ntf.Context(Xd, RANK, p, stream=stream) as ctx:
@@ -541,7 +691,7 @@ def run_sweep_case(args):
             rs = ctx.run(A, At, Y, args.steps)
             trace = ctx.trace_get() if args.trace else None
         stream.synchronize()
-    print(json.dumps({"sweep_case": WORKLOAD, "storage": args.storage, "sweeps": args.steps,
+    print(json.dumps({"sweep_case": args.workload, "storage": args.storage, "sweeps": args.steps,
                       "rel_err": rs["rel_err"], "trace_last_sweep": trace}))
 
 
@@ -649,16 +799,20 @@ def main():
     ap.add_argument("--form", default="bf16_learned", choices=sorted(FORMS),
                     help="the timed form: BF16 or FP32 storage, with or without the learned "
                          "warm start")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="the evaluation workload of the headline line")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="variants: skip the learned warm start (no network training)")
     ap.add_argument("--train-rows", type=int, default=1_000_000)
     ap.add_argument("--train-epochs", type=float, default=20.0)
-    ap.add_argument("--robust-tensors", type=int, default=6,
+    ap.add_argument("--robust-tensors", type=int, default=10,
                     help="other tensors on which the learned warm start is compared with plain")
     ap.add_argument("--ws-sweeps", type=int, default=1,
                     help="outer iterations of each run in which the network is consulted")
     ap.add_argument("--kernel-case", action="store_true",
                     help="standalone MTTKRP calls only (profiling case)")
     ap.add_argument("--dims", default="384x384x384")
-    ap.add_argument("--rank", type=int, default=RANK)
+    ap.add_argument("--rank", type=int, default=20)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "tensor", "simt"])
     ap.add_argument("--sweep-case", action="store_true",

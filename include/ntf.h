@@ -91,9 +91,24 @@ typedef struct {
   double eps_abs;    /* stopping tolerances of Sec. IV-C (paper: 1e-4, 1e-4)            */
   double eps_rel;
   int contraction;   /* ntf_contraction (default AUTO)                                   */
+  /* KKT stopping rule of ntf_run (eq. KKT_NTF; default 0 = not used): the run stops at a
+   * checked iteration where every factor's last update has kkt_dual <= kkt_dual_tol and
+   * kkt_comp <= kkt_comp_tol (a tolerance of 0 leaves that measure untested; see
+   * ntf_update_stats for the measures). */
+  double kkt_dual_tol;
+  double kkt_comp_tol;
 } ntf_params;
 
-/* Per-factor residuals of one update (Sec. IV-C), all Frobenius norms. */
+/* Per-factor residuals of one update (Sec. IV-C), all Frobenius norms, and the KKT measures
+ * of the factor's non-negative least-squares problem at the new auxiliary At (eq. KKT_NTF:
+ * with the other factors fixed the factor solves min_{At >= 0} 1/2 ||X^(n) - At K^T||^2, whose
+ * gradient is g = At G - M, G the coefficient matrix without rho and M the MTTKRP; the
+ * optimality conditions are At >= 0, g >= 0, At (*) g = 0).  Scaled with s_x = max |At| and
+ * s_g = max |G| s_x + max |M| (FP32 arithmetic for g, so values below about R 2^-24 are
+ * rounding):
+ *   kkt_neg_x = max(0, -min At) / s_x                  (0: At is projected)
+ *   kkt_dual  = max(0, max(-g)) / s_g                  (dual feasibility)
+ *   kkt_comp  = sum |At (*) g| / (I_n R s_x s_g)       (complementarity) */
 typedef struct {
   double primal_res; /* ||A - At||                                   */
   double dual_res;   /* rho ||At_after - At_before||                 */
@@ -101,14 +116,19 @@ typedef struct {
   double norm_At;
   double norm_Y;
   double rho;        /* penalty used by this update                  */
+  double kkt_neg_x;
+  double kkt_dual;
+  double kkt_comp;
 } ntf_update_stats;
 
 typedef struct {
   int iters;          /* outer iterations executed                          */
   int converged;      /* 1 if the residual test held for every factor       */
   int reached_target; /* 1 if rel_err <= target_rfe was observed            */
-  int reserved;
+  int kkt_met;        /* 1 if the KKT tolerances held for every factor      */
   double rel_err;     /* relative error of the auxiliaries at the end       */
+  double kkt_dual;    /* largest kkt_dual over the factors of the last      */
+  double kkt_comp;    /* checked iteration (likewise kkt_comp)              */
 } ntf_run_stats;
 
 /* Fill *p with the paper's settings (paper_mode != 0: L=1, PRIMAL, ADAPTIVE, rho0=1,
@@ -175,8 +195,9 @@ ntf_status ntf_fit_from_mttkrp(ntf_ctx* ctx, const float* d_M_last, const float*
 /* Whole factorization: outer iterations of eq. (ADMoM_NTF) in Gauss-Seidel order starting
  * from the given state (d_A, d_At, d_Y: host arrays of N device pointers, updated in
  * place), until the residual test of Sec. IV-C holds for every factor (if eps_abs or
- * eps_rel > 0), rel_err <= target_rfe (if target_rfe > 0, checked every check_every
- * iterations) or max_outer iterations.  Grams are (re)initialised from the Khatri-Rao
+ * eps_rel > 0), rel_err <= target_rfe (if target_rfe > 0), the KKT tolerances of the params
+ * hold for every factor (if kkt_dual_tol or kkt_comp_tol > 0) -- each tested every
+ * check_every iterations -- or max_outer iterations.  Grams are (re)initialised from the Khatri-Rao
  * source factors first.  rfe_hist (host, may be NULL, length max_outer) receives the error
  * after every checked iteration (NaN elsewhere).  Returns NTF_ERR_NOT_CONVERGED if
  * max_outer was reached without meeting a requested criterion (out is still filled).
@@ -304,7 +325,14 @@ ntf_status ntf_attach_warmstart(ntf_ctx* ctx, ntf_mlp* net, int sweeps);
  * sums and the contraction intermediate) is one static 32 MiB device array that every GPU
  * loading this library holds until the process exits.
  * - The first call on each device looks up that array's device address (cudaGetSymbolAddress
- *   with the device current) and caches it; make that first call before any stream capture.
+ *   with the device current) and caches it.  With CUDA's lazy module loading (the default)
+ *   that lookup is also when the 32 MiB array is placed in device memory, so make the first
+ *   call on each device before any stream capture and before the caller reserves the
+ *   device's memory; alternatively set CUDA_MODULE_LOADING=EAGER, which places the array when
+ *   the library is loaded.
+ * - d_tensor, d_M and the used d_factors must be device memory of the current device (checked
+ *   with cudaPointerGetAttributes before any launch: NTF_ERR_INVALID_ARG otherwise, e.g. for
+ *   host memory or another device's memory).
  * - All calls on a device share the array and it keeps the last call's contents (nothing in
  *   it needs to start at zero).  Calls whose work overlaps on the GPU -- on different streams
  *   or from different threads -- race on it; serialize them.

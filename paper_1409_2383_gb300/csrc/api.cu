@@ -161,6 +161,8 @@ ntf_status check_params(const ntf_params* p) {
     return fail(NTF_ERR_INVALID_ARG, "negative stopping tolerance");
   if (p->contraction < NTF_CONTRACT_AUTO || p->contraction > NTF_CONTRACT_SIMT)
     return fail(NTF_ERR_INVALID_ARG, "unknown contraction engine %d", p->contraction);
+  if (!(p->kkt_dual_tol >= 0.0) || !(p->kkt_comp_tol >= 0.0))
+    return fail(NTF_ERR_INVALID_ARG, "negative KKT tolerance");
   return NTF_OK;
 }
 
@@ -620,6 +622,16 @@ void free_ctx(ntf_ctx* c) {
 
 }  // namespace
 
+ntf_status ntf::record_error(ntf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
 extern "C" {
 
 void ntf_default_params(ntf_params* p, int paper_mode) {
@@ -634,6 +646,8 @@ void ntf_default_params(ntf_params* p, int paper_mode) {
   p->eps_abs = 1e-4;
   p->eps_rel = 1e-4;
   p->contraction = NTF_CONTRACT_AUTO;
+  p->kkt_dual_tol = 0.0;
+  p->kkt_comp_tol = 0.0;
 }
 
 const char* ntf_status_string(ntf_status s) {
@@ -935,6 +949,9 @@ ntf_status ntf_admm_update(ntf_ctx* c, int mode, const float* d_M, float* d_A, f
   stats->norm_At = s[3];
   stats->norm_Y = s[4];
   stats->rho = s[5];
+  stats->kkt_neg_x = c->h_ctrl->kkt[mode][0];
+  stats->kkt_dual = c->h_ctrl->kkt[mode][1];
+  stats->kkt_comp = c->h_ctrl->kkt[mode][2];
   return take_status(c);
 }
 
@@ -1090,6 +1107,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
       return fail(NTF_ERR_INVALID_ARG, "misaligned state of factor %d", m);
   const bool use_res = c->prm.eps_abs > 0.0 || c->prm.eps_rel > 0.0;
   const bool use_tgt = target_rfe > 0.0;
+  const bool use_kkt = c->prm.kkt_dual_tol > 0.0 || c->prm.kkt_comp_tol > 0.0;
   if (rfe_hist)
     for (int i = 0; i < max_outer; ++i) rfe_hist[i] = NAN;
   const float* const* src = c->prm.kr_source == NTF_KR_AUX ? At : A;
@@ -1116,6 +1134,9 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
     h.eps_rel = c->prm.eps_rel;
     for (int m = 0; m < c->N; ++m)
       h.res_base[m] = std::sqrt(static_cast<double>(c->dims[m]) * c->R) * c->prm.eps_abs;
+    h.use_kkt = use_kkt;
+    h.kkt_dual_tol = c->prm.kkt_dual_tol;
+    h.kkt_comp_tol = c->prm.kkt_comp_tol;
     const size_t off = offsetof(Ctrl, stop), len = sizeof(Ctrl) - off;
     NTF_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(c->d_ctrl) + off,
                              reinterpret_cast<char*>(c->h_ctrl) + off, len,
@@ -1134,6 +1155,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   // that consult the warm-start network have their own recording.
   ntf_run_stats rs{};
   rs.rel_err = NAN;
+  rs.kkt_dual = rs.kkt_comp = NAN;
   ntf_status result = NTF_OK;
   bool done = false;
   // Capture needs a non-legacy stream; otherwise (or if capture fails) launch eagerly.
@@ -1153,9 +1175,12 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
     }
     rs.iters = k + 1;
     rs.rel_err = sn.rel_err;
+    rs.kkt_dual = sn.kkt_dual;
+    rs.kkt_comp = sn.kkt_comp;
     if (rfe_hist) rfe_hist[k] = sn.rel_err;
     if (sn.stop & 1) rs.reached_target = 1;
     if (sn.stop & 2) rs.converged = 1;
+    if (sn.stop & 4) rs.kkt_met = 1;
     if (sn.stop) done = true;
     return NTF_OK;
   };
@@ -1235,7 +1260,7 @@ ntf_status ntf_run(ntf_ctx* c, float* const* A, float* const* At, float* const* 
   }
   if (st_run == NTF_OK && unread >= 0) st_run = read_sweep(unread);
   if (st_run != NTF_OK) return st_run;
-  if (!done && (use_res || use_tgt)) result = NTF_ERR_NOT_CONVERGED;
+  if (!done && (use_res || use_tgt || use_kkt)) result = NTF_ERR_NOT_CONVERGED;
   if (out) *out = rs;
   if (result != NTF_OK) fail(result, "no stopping criterion met in %d iterations", max_outer);
   return result;

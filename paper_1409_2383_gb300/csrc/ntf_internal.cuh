@@ -13,6 +13,9 @@ namespace ntf {
 
 constexpr int kMaxOrder = 4;
 
+// Records the calling thread's last-error message (returned by ntf_last_error) and returns s.
+ntf_status record_error(ntf_status s, const char* fmt, ...);
+
 // Entry idx of a split Khatri-Rao table of the tensor-core contractions (parts n apart):
 // BF16, W = w1 + w2 + w3 with w1 = bf16(W), w2 = bf16(W - w1), w3 = bf16(W - w1 - w2) (each
 // remainder exact in FP32); FP32 (TF32 operands), W = wh + wl, wh = W truncated to TF32,
@@ -55,9 +58,12 @@ enum : int { kStNotSpd = 1, kStNonFinite = 2, kStTimeout = 4 };
 struct SweepSnap {
   int sweep;       // sweeps finished in the run, this one included
   int status;      // kSt* bits at the end of the sweep
-  int stop;        // 1: fit target reached, 2: residual criteria of Sec. IV-C met
+  int stop;        // 1: fit target reached, 2: residual criteria of Sec. IV-C met,
+                   // 4: KKT tolerances of eq. (KKT_NTF) met
   int pad;
   double rel_err;
+  double kkt_dual;  // largest scaled dual infeasibility over the factors of the sweep
+  double kkt_comp;  // largest scaled complementarity over the factors of the sweep
 };
 
 // Small device-resident control block: penalties, residual norms and fit terms live here so
@@ -65,6 +71,9 @@ struct SweepSnap {
 struct Ctrl {
   double rho[kMaxOrder];          // penalty per factor (adaptive / fixed policies)
   double stats[kMaxOrder][8];     // primal, dual, |A|, |At|, |Y|, rho used, -, -
+  // KKT measures of each factor's last update (eq. KKT_NTF, scaled): negativity of At, dual
+  // infeasibility, complementarity; [3]: max |G| of the coefficient matrix (set by the system)
+  double kkt[kMaxOrder][4];
   double fit_inner;               // <M_N, F_N>
   double fit_gram;                // 1^T (Hadamard of all Grams) 1
   double rel_err;
@@ -84,6 +93,8 @@ struct Ctrl {
   int use_tgt, use_res, check_every, max_outer;
   double target_rfe, eps_rel;
   double res_base[kMaxOrder];  // sqrt(I_m R) eps_abs
+  double kkt_dual_tol, kkt_comp_tol;  // KKT stopping rule (0: that measure is not tested)
+  int use_kkt, pad2;
 };
 
 // ------------------------------------------------------------------ kernel launchers

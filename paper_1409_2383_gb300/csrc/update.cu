@@ -7,8 +7,9 @@
 //                   rows (App. B).  Stored as FP64 and FP32.
 //  k_update_rows    one warp per row: x = H^{-1}(m + rho At - Y), At = (x + Y/rho)_+,
 //                   Y += rho (x - At); per-CTA partial sums of the residual norms of
-//                   Sec. IV-C, of the new factor's Gram (FP64) and of the fit terms
-//                   <M_i, f_i>, f_i^T G f_i.  The row arithmetic is FP32 under the trace
+//                   Sec. IV-C, of the new factor's Gram (FP64), of the fit terms
+//                   <M_i, f_i>, f_i^T G f_i and of the KKT measures of the row problems
+//                   (eq. KKT_NTF, gradient At G - M).  The row arithmetic is FP32 under the trace
 //                   penalty policy (then cond(H) <= R + 1) and FP64 otherwise.
 //  k_update_reduce  fixed-order sums of the partials: the stored Gram of the factor, the
 //                   residuals, the penalty rule (Sec. IV-D) and, for the last factor of a
@@ -29,7 +30,12 @@ namespace {
 
 constexpr int kRowWarps = 8;  // rows per CTA
 constexpr int kRowThreads = kRowWarps * 32;
-constexpr int kScal = 8;      // scalar partials per CTA
+// Scalar partials per CTA: [0, kSumScal) are summed over CTAs -- squared norms of the
+// residuals (0-4), the fit terms <M, f> and f^T G f (5, 6), the complementarity sum
+// sum |At (At G - M)| (7) -- and [kSumScal, kScal) are maxima -- max(-(At G - M)) (8),
+// max |At| (9), max |M| (10), max(-At) (11) -- for the KKT measures of eq. (KKT_NTF).
+constexpr int kScal = 12;
+constexpr int kSumScal = 8;
 // The rows kernel reduces its own partials (in its last CTA) when there are at most this many
 // Gram partial entries to add; larger sets go to the separate multi-CTA reduction.
 constexpr int64_t kFusedReduceMax = 2048;
@@ -123,13 +129,13 @@ template <int S, int NT>
 __device__ void system_body(const UpdArgs& a) {
   __shared__ double s_col[2][64];  // u: column k of B, zero at the pivot
   __shared__ double s_piv[2], s_c[2];
-  __shared__ double s_red[NT / 32];
+  __shared__ double s_red[NT / 32], s_gmax[NT / 32];
   const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SysView sv = sys_view(a.sys, a.mode, R);
   double v[S];
   int ii[S], jj[S];
-  double tr = 0.0;
+  double tr = 0.0, gmax = 0.0;
 #pragma unroll
   for (int q = 0; q < S; ++q) {
     const int p = tid + NT * q;
@@ -151,12 +157,24 @@ __device__ void system_body(const UpdArgs& a) {
       sv.h32[i * R + j] = static_cast<float>(h);
       sv.h32[j * R + i] = static_cast<float>(h);
       if (i == j) tr += h;
+      gmax = fmax(gmax, fabs(h));
     }
     v[q] = h;
   }
-  for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
-  if (lane == 0) s_red[warp] = tr;
+  for (int off = 16; off > 0; off >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
+  }
+  if (lane == 0) {
+    s_red[warp] = tr;
+    s_gmax[warp] = gmax;
+  }
   __syncthreads();
+  if (tid == 0) {
+    double g = 0.0;
+    for (int w = 0; w < NT / 32; ++w) g = fmax(g, s_gmax[w]);
+    a.ctrl->kkt[a.mode][3] = g;  // max |G|: scale of the KKT measures
+  }
   double rho;
   if (a.rho_policy == NTF_RHO_TRACE) {
     double t = 0.0;
@@ -230,6 +248,211 @@ __device__ void system_body(const UpdArgs& a) {
   }
 }
 
+// Trace policy: H = Hadamard_{m != n} Gram_m + rho I with rho = trace(G)/R, so that
+// cond(H) <= R + 1 (the eigenvalues of G lie in [0, trace G]).  H is factored once in FP64
+// (App. B) as H = L D L^T by right-looking elimination, fraction-free: the trailing part is
+// kept as B = c A for a tracked scalar c > 0 and step k maps
+//   b_ij -> 2^e (b_ij b_kk - b_ik b_jk)  (i >= j > k),   c -> 2^e c b_kk,
+// with 2^e the power of two that brings b_kk into [1, 2) (exact), so no reciprocal lies on
+// the chain of dependent steps.  Column k is final after step k: l_ik = b_ik / b_kk and
+// d_k = b_kk / c (c of step k cancels in l).  The lower triangle is packed column by column,
+// so the trailing part of step k is a suffix of the packing and the threads that still have
+// work at a step fill whole warps (FP64 instructions issue per warp at a small fraction of
+// the FP32 rate on this GPU, so partly idle warps would cost as much as busy ones).  A pivot
+// that is not a positive normal number reports NOT_SPD, where Cholesky would fail.
+// H^{-1} = L^{-T} D^{-1} L^{-1} is then formed in FP32 from the FP64 factor: W = L^{-1} by
+// forward substitution (one warp per set of columns, shuffles, no block barriers) and
+// H^{-1}_ij = sum_{k >= max(i, j)} W_ki W_kj / d_k; with cond(H) <= R + 1 its error is a few
+// FP32 roundings, the precision the rows kernel applies it in.  Only the FP32 inverse is
+// written (the rows kernel of this policy reads nothing else).
+__device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
+
+template <int S, int NT>
+__device__ void system_ldl(const UpdArgs& a) {
+  __shared__ double s_col[2][kMaxRank];  // column k + 1 of B, published during step k
+  __shared__ double s_piv[2], s_c[2];
+  __shared__ double s_red[NT / 32], s_gmax[NT / 32];
+  __shared__ double s_pk[kMaxRank], s_ck[kMaxRank];  // b_kk and c of every step
+  __shared__ float s_l[S * NT];                       // L, then W = L^{-1} (packed by column)
+  __shared__ float s_dinv[kMaxRank];
+  const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SysView sv = sys_view(a.sys, a.mode, R);
+  double v[S];
+  int ii[S], jj[S];
+  double tr = 0.0, gmax = 0.0;
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const int p = tid + NT * q;
+    int j = -1, i = -1;
+    if (p < T) {  // column j of the packing holds rows j .. R-1
+      j = 0;
+      while (col_start(j + 1, R) <= p) ++j;
+      i = j + (p - col_start(j, R));
+    }
+    ii[q] = i;
+    jj[q] = j;
+    double h = 0.0;
+    if (p < T) {
+      double g[kMaxOrder];  // loads first, then the product
+#pragma unroll
+      for (int m = 0; m < kMaxOrder; ++m)
+        g[m] = m < a.N && m != a.mode ? a.grams[m * RR + i * R + j] : 1.0;
+      h = g[0];
+#pragma unroll
+      for (int m = 1; m < kMaxOrder; ++m) h *= g[m];
+      sv.h32[i * R + j] = static_cast<float>(h);
+      sv.h32[j * R + i] = static_cast<float>(h);
+      if (i == j) tr += h;
+      gmax = fmax(gmax, fabs(h));
+    }
+    v[q] = h;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
+  }
+  if (lane == 0) {
+    s_red[warp] = tr;
+    s_gmax[warp] = gmax;
+  }
+  __syncthreads();
+  double t = 0.0, gm = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+    t += s_red[w];
+    gm = fmax(gm, s_gmax[w]);
+  }
+  const double rho = t / R;
+  if (tid == 0) a.ctrl->kkt[a.mode][3] = gm;
+  bool fail = !(rho > 0.0) || !isfinite(rho);
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    if (ii[q] >= 0 && ii[q] == jj[q]) v[q] += rho;
+    if (jj[q] == 0) {  // publish column 0 (c = 1)
+      s_col[0][ii[q]] = v[q];
+      if (ii[q] == 0) {
+        s_piv[0] = v[q];
+        s_c[0] = 1.0;
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < R && !fail; ++k) {
+    const int b = k & 1;
+    const double piv = s_piv[b], c = s_c[b];
+    const int pex = __double2hiint(piv) >> 20;  // negative when the sign bit is set
+    if (static_cast<unsigned>(pex - 1) >= 0x7FEu) {  // not SPD (or not a normal number)
+      fail = true;  // the same shared value in every thread: a uniform exit
+      break;
+    }
+    if (tid == 0) {
+      s_pk[k] = piv;
+      s_ck[k] = c;
+    }
+    const int e = 1023 - pex;   // b_kk 2^e in [1, 2)
+    const int first = col_start(k + 1, R);  // the trailing part is p >= first
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      if (tid + NT * q < first || ii[q] < 0) continue;
+      const int i = ii[q], j = jj[q];
+      const double nv = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e);
+      v[q] = nv;
+      if (j == k + 1) {  // publish column k + 1 for the next step
+        s_col[b ^ 1][i] = nv;
+        if (i == j) {
+          s_piv[b ^ 1] = nv;
+          s_c[b ^ 1] = scale_pow2(c * piv, e);
+        }
+      }
+    }
+    __syncthreads();  // one barrier per step: the next step reads the other buffers
+  }
+  if (fail) {  // uniform
+    if (tid == 0) {
+      a.ctrl->bad[a.mode] = 1;
+      atomicOr(&a.ctrl->status, kStNotSpd);
+    }
+    return;
+  }
+  // L (unit lower, FP32) and D^{-1}: l_ij = b_ij / b_jj, 1/d_j = c_j / b_jj
+  if (tid < R) {
+    const double rp = recip_newton(s_pk[tid]);
+    s_pk[tid] = rp;
+    s_dinv[tid] = static_cast<float>(s_ck[tid] * rp);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const int i = ii[q], j = jj[q];
+    if (i < 0) continue;
+    s_l[tid + NT * q] = i == j ? 1.0f : static_cast<float>(v[q] * s_pk[j]);
+  }
+  __syncthreads();
+  // W = L^{-1}: warp w forms the columns j = w, w + NT/32, ...; lane l holds rows l, l + 32
+  constexpr int kCols = kMaxRank / (NT / 32);
+  float w0[kCols], w1[kCols];
+#pragma unroll
+  for (int cc = 0; cc < kCols; ++cc) {
+    const int j = warp + (NT / 32) * cc;
+    w0[cc] = lane == j ? 1.0f : 0.0f;
+    w1[cc] = lane + 32 == j ? 1.0f : 0.0f;
+  }
+  for (int k = 0; k + 1 < R; ++k) {
+    const int ck = col_start(k, R) - k;  // s_l[ck + i] = L_ik
+    const float l0 = lane > k && lane < R ? s_l[ck + lane] : 0.0f;
+    const float l1 = lane + 32 > k && lane + 32 < R ? s_l[ck + lane + 32] : 0.0f;
+#pragma unroll
+    for (int cc = 0; cc < kCols; ++cc) {
+      const int j = warp + (NT / 32) * cc;
+      if (j > k || j >= R) continue;  // w_kj = 0: nothing to eliminate (warp-uniform)
+      const float y = __shfl_sync(0xffffffffu, k < 32 ? w0[cc] : w1[cc], k & 31);
+      w0[cc] = fmaf(-l0, y, w0[cc]);
+      w1[cc] = fmaf(-l1, y, w1[cc]);
+    }
+  }
+  __syncthreads();  // every warp has read L
+#pragma unroll
+  for (int cc = 0; cc < kCols; ++cc) {
+    const int j = warp + (NT / 32) * cc;
+    if (j >= R) continue;
+    const int cj = col_start(j, R) - j;  // s_l[cj + i] = W_ij, i >= j
+    if (lane >= j && lane < R) s_l[cj + lane] = w0[cc];
+    if (lane + 32 >= j && lane + 32 < R) s_l[cj + lane + 32] = w1[cc];
+  }
+  __syncthreads();
+  // H^{-1}_ij = sum_{k >= i} W_ki W_kj / d_k (i >= j)
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const int i = ii[q], j = jj[q];
+    if (i < 0) continue;
+    const float* wi = s_l + col_start(i, R) - i;
+    const float* wj = s_l + col_start(j, R) - j;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    int k = i;
+    for (; k + 1 < R; k += 2) {
+      acc0 = fmaf(wi[k] * wj[k], s_dinv[k], acc0);
+      acc1 = fmaf(wi[k + 1] * wj[k + 1], s_dinv[k + 1], acc1);
+    }
+    if (k < R) acc0 = fmaf(wi[k] * wj[k], s_dinv[k], acc0);
+    const float h = acc0 + acc1;
+    sv.hinv32[i * R + j] = h;
+    sv.hinv32[j * R + i] = h;
+  }
+  if (tid == 0) {
+    a.ctrl->bad[a.mode] = 0;
+    a.ctrl->stats[a.mode][5] = rho;
+  }
+}
+
+// The coefficient system of a factor update: the FP64 factorization above under the trace
+// policy, the FP64 sweep operator otherwise (the rows then run in FP64).
+template <int S, int NT>
+__device__ __forceinline__ void system_any(const UpdArgs& a) {
+  if (a.rho_policy == NTF_RHO_TRACE) system_ldl<S, NT>(a);
+  else system_body<S, NT>(a);
+}
+
 __device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
 
 // (r, s), r >= s, of packed lower-triangle entry e = r (r + 1) / 2 + s.
@@ -257,15 +480,19 @@ __device__ __forceinline__ void rows_cta_tail(const UpdArgs& a, float (&part)[kS
 #pragma unroll
   for (int q = 0; q < kScal; ++q)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part[q] += __shfl_xor_sync(0xffffffffu, part[q], off);
+    for (int off = 16; off > 0; off >>= 1) {
+      const float o = __shfl_xor_sync(0xffffffffu, part[q], off);
+      part[q] = q < kSumScal ? part[q] + o : fmaxf(part[q], o);
+    }
   if (lane == 0)
 #pragma unroll
     for (int q = 0; q < kScal; ++q) red[warp][q] = part[q];
   __syncthreads();
   if (tid < kScal) {
-    double sum = 0.0;
-    for (int w = 0; w < kRowWarps; ++w) sum += red[w][tid];
-    a.scal_part[blockIdx.x * kScal + tid] = sum;
+    double v = 0.0;  // maxima: every entry is >= 0 (the measures are clamped at zero)
+    for (int w = 0; w < kRowWarps; ++w)
+      v = tid < kSumScal ? v + red[w][tid] : fmax(v, red[w][tid]);
+    a.scal_part[blockIdx.x * kScal + tid] = v;
   }
   double* gp = a.gram_part + static_cast<int64_t>(blockIdx.x) * T;
   for (int e = tid; e < T; e += kRowThreads) {
@@ -301,7 +528,7 @@ __device__ __forceinline__ void rows_cta_tail(const UpdArgs& a, float (&part)[kS
 template <int S>
 __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
   if (a.ctrl->stop) return;  // the run has stopped
-  system_body<S, kSysThreads>(a);
+  system_any<S, kSysThreads>(a);
 }
 
 // Rows for R <= 32.  Real = float (trace policy) or double.  One warp per row, lane j owns
@@ -339,7 +566,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
   if (bad) return;  // uniform: the system of this factor failed, or the run has stopped; the
                     // state is kept
   const Real rinv = Real(1) / rho;
-  float part[kScal] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float part[kScal] = {};
   float f = 0.0f;
   if (row < a.I) {
     const Real t_in = t;
@@ -376,15 +603,34 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
     if (a.wsplit && h)  // its entry (row, lane) of the next contraction's split table
       split_store(a.wsplit, static_cast<int64_t>(a.ws_n) * a.ws_kpad,
                   static_cast<int64_t>(lane) * a.ws_kpad + row, f, a.ws_bf16);
+    float g = 0.0f;  // (G f)_j with the FP32 coefficient matrix (no rho)
     if (a.want_fit) {
       part[5] = static_cast<float>(m) * f;
-      float g = 0.0f;  // (G f)_j with the FP32 coefficient matrix
 #pragma unroll
       for (int k = 0; k < kR; ++k) {
         const float fk = __shfl_sync(0xffffffffu, f, k);
         if (k < R && h) g = fmaf(__ldg(sv.h32 + k * R + lane), fk, g);
       }
       part[6] = f * g;
+    }
+    // KKT of the row problem min_{x >= 0} 1/2 x^T G x - m^T x at x = At (eq. KKT_NTF):
+    // gradient (G At)_j - m_j; (G At)_j is the fit's (G f)_j when f = At
+    float gt = g;
+    if (!(a.want_fit && a.kr_aux)) {
+      gt = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kR; ++k) {
+        const float tk = __shfl_sync(0xffffffffu, ft, k);
+        if (k < R && h) gt = fmaf(__ldg(sv.h32 + k * R + lane), tk, gt);
+      }
+    }
+    if (h) {
+      const float gr = gt - static_cast<float>(m);
+      part[7] = fabsf(ft * gr);
+      part[8] = fmaxf(0.0f, -gr);
+      part[9] = fabsf(ft);
+      part[10] = fabsf(static_cast<float>(m));
+      part[11] = fmaxf(0.0f, -ft);
     }
   }
   frow[warp][lane] = h ? static_cast<double>(f) : 0.0;
@@ -398,7 +644,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
   extern __shared__ double shd[];
   const int R = a.R, RR = R * R;
   Real* Hi = reinterpret_cast<Real*>(shd);                       // [RR] H^{-1}
-  float* Hf = reinterpret_cast<float*>(Hi + RR);                 // [RR] H (fit only)
+  float* Hf = reinterpret_cast<float*>(Hi + RR);                 // [RR] H (fit and KKT)
   Real* vbuf = reinterpret_cast<Real*>(shd + ((RR * sizeof(Real) + RR * 4 + 15) / 16) * 2);
   float* frow = reinterpret_cast<float*>(vbuf + kRowWarps * 64); // [kRowWarps][64]
   __shared__ double red[kRowWarps][kScal];
@@ -408,13 +654,13 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
   for (int idx = tid; idx < RR; idx += kRowThreads) {
     if constexpr (sizeof(Real) == 4) Hi[idx] = sv.hinv32[idx];
     else Hi[idx] = sv.hinv64[idx];
-    if (a.want_fit) Hf[idx] = sv.h32[idx];
+    Hf[idx] = sv.h32[idx];
   }
   __syncthreads();
   const Real rho = static_cast<Real>(a.ctrl->stats[a.mode][5]);
   const Real rinv = Real(1) / rho;
   const int64_t row = static_cast<int64_t>(blockIdx.x) * kRowWarps + warp;
-  float part[kScal] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float part[kScal] = {};
   const int j0 = lane, j1 = lane + 32;
   const bool h0 = j0 < R, h1 = j1 < R;
   Real* vb = vbuf + warp * 64;
@@ -486,10 +732,10 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
       if (h0) split_store(a.wsplit, nt, static_cast<int64_t>(j0) * a.ws_kpad + row, f0, a.ws_bf16);
       if (h1) split_store(a.wsplit, nt, static_cast<int64_t>(j1) * a.ws_kpad + row, f1, a.ws_bf16);
     }
+    float g0 = 0.0f, g1 = 0.0f;  // (G f)_j with the FP32 coefficient matrix (no rho)
+    __syncwarp();
     if (a.want_fit) {
       part[5] = static_cast<float>(m0) * f0 + static_cast<float>(m1) * f1;
-      __syncwarp();
-      float g0 = 0.0f, g1 = 0.0f;
       for (int kk = 0; kk < R; ++kk) {
         const float fk = fr[kk];
         if (h0) g0 = fmaf(Hf[kk * R + j0], fk, g0);
@@ -497,6 +743,28 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
       }
       part[6] = f0 * g0 + f1 * g1;
     }
+    // KKT of the row problem at x = At (eq. KKT_NTF): gradient (G At)_j - m_j
+    if (!(a.want_fit && a.kr_aux)) {
+      float* tb = reinterpret_cast<float*>(vb);  // this warp's v buffer is free now
+      __syncwarp();
+      if (h0) tb[j0] = ft0;
+      if (h1) tb[j1] = ft1;
+      __syncwarp();
+      g0 = g1 = 0.0f;
+      for (int kk = 0; kk < R; ++kk) {
+        const float tk = tb[kk];
+        if (h0) g0 = fmaf(Hf[kk * R + j0], tk, g0);
+        if (h1) g1 = fmaf(Hf[kk * R + j1], tk, g1);
+      }
+      __syncwarp();
+    }
+    const float gr0 = h0 ? g0 - static_cast<float>(m0) : 0.0f;
+    const float gr1 = h1 ? g1 - static_cast<float>(m1) : 0.0f;
+    part[7] = fabsf(ft0 * gr0) + fabsf(ft1 * gr1);
+    part[8] = fmaxf(0.0f, fmaxf(-gr0, -gr1));
+    part[9] = fmaxf(fabsf(ft0), fabsf(ft1));
+    part[10] = fmaxf(fabsf(static_cast<float>(m0)), fabsf(static_cast<float>(m1)));
+    part[11] = fmaxf(0.0f, fmaxf(-ft0, -ft1));
   } else {
     if (h0) fr[j0] = 0.0f;
     if (h1) fr[j1] = 0.0f;
@@ -526,6 +794,16 @@ __device__ void update_finalize(const UpdArgs& a, const double* sum) {
   } else if (a.rho_policy == NTF_RHO_TRACE) {
     c->rho[a.mode] = rho;
   }
+  {
+    // KKT measures of the factor's row problems at At (eq. KKT_NTF), scaled as
+    // s_x = max |At|, s_g = max |G| s_x + max |M|
+    const double sx = fmax(sum[9], 1e-30);
+    const double sg = c->kkt[a.mode][3] * sx + sum[10];
+    const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
+    c->kkt[a.mode][0] = fmax(0.0, sum[11]) / sx;
+    c->kkt[a.mode][1] = fmax(0.0, sum[8]) * inv;
+    c->kkt[a.mode][2] = sum[7] * inv / (sx * static_cast<double>(a.I) * a.R);
+  }
   if (a.want_fit) {
     const double inner = sum[5], quad = sum[6];
     const double e2 = c->x_norm2 - 2.0 * inner + quad;
@@ -551,6 +829,15 @@ __device__ void update_finalize(const UpdArgs& a, const double* sum) {
         }
         if (all) stop |= 2;
       }
+      if (c->use_kkt) {
+        bool all = true;
+        for (int m = 0; m < a.N && all; ++m) {
+          const double* q = c->kkt[m];
+          all = (c->kkt_dual_tol <= 0.0 || q[1] <= c->kkt_dual_tol) &&
+                (c->kkt_comp_tol <= 0.0 || q[2] <= c->kkt_comp_tol);
+        }
+        if (all) stop |= 4;
+      }
     }
     const int status = c->status;
     SweepSnap* sn = a.snap + (k & 1);
@@ -558,6 +845,13 @@ __device__ void update_finalize(const UpdArgs& a, const double* sum) {
     sn->status = status;
     sn->stop = stop;
     sn->rel_err = c->rel_err;
+    double kd = 0.0, kc = 0.0;
+    for (int m = 0; m < a.N; ++m) {
+      kd = fmax(kd, c->kkt[m][1]);
+      kc = fmax(kc, c->kkt[m][2]);
+    }
+    sn->kkt_dual = kd;
+    sn->kkt_comp = kc;
     c->stop_next = stop != 0 || status != 0;
     c->sweep = k + 1;
   }
@@ -629,12 +923,20 @@ __device__ __forceinline__ void store_gram_entry(const UpdArgs& a, int e, double
   a.gram_out[c * a.R + r] = v;
 }
 
-// Scalar partial q summed over blocks by one warp: lane l takes blocks l, l + 32, ... and the
-// lanes are combined by a fixed butterfly.
+// Scalar partial q combined over blocks by one warp (summed for q < kSumScal, else the
+// maximum): lane l takes blocks l, l + 32, ... and the lanes are combined by a fixed
+// butterfly.
 __device__ __forceinline__ double scalar_sum(const UpdArgs& a, int nblocks, int q, int lane) {
+  const bool sum = q < kSumScal;
   double s = 0.0;
-  for (int b = lane; b < nblocks; b += 32) s += __ldcg(a.scal_part + b * kScal + q);
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  for (int b = lane; b < nblocks; b += 32) {
+    const double v = __ldcg(a.scal_part + b * kScal + q);
+    s = sum ? s + v : fmax(s, v);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_xor_sync(0xffffffffu, s, off);
+    s = sum ? s + o : fmax(s, o);
+  }
   return s;
 }
 
@@ -665,8 +967,10 @@ __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
     if ((tid & 7) == 0 && e < T) store_gram_entry(a, e, v);
     return;
   }
-  const double v = scalar_sum(a, nblocks, warp, lane);
-  if (lane == 0) s_sum[warp] = v;
+  for (int q = warp; q < kScal; q += 8) {
+    const double v = scalar_sum(a, nblocks, q, lane);
+    if (lane == 0) s_sum[q] = v;
+  }
   __syncthreads();
   if (tid == 0) update_finalize(a, s_sum);
 }
@@ -691,8 +995,10 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
       const double v = gram_entry_sum8(a, nblocks, e, tid & 7);
       if ((tid & 7) == 0 && e < T) store_gram_entry(a, e, v);
     } else {
-      const double v = scalar_sum(a, nblocks, warp, lane);
-      if (lane == 0) s_sum[warp] = v;
+      for (int q = warp; q < kScal; q += 8) {
+        const double v = scalar_sum(a, nblocks, q, lane);
+        if (lane == 0) s_sum[q] = v;
+      }
       __syncthreads();
       if (tid == 0) update_finalize(a, s_sum);
     }
@@ -703,7 +1009,7 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  system_body<S, 256>(as);
+  system_any<S, 256>(as);
   if (tid == 0) {
     a.ctrl->sys_count = 0;
     // every CTA of this kernel has read stop by now

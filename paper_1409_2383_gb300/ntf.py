@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
                 ("rho_policy", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("mu", ctypes.c_double), ("tau_incr", ctypes.c_double),
                 ("tau_decr", ctypes.c_double), ("eps_abs", ctypes.c_double),
-                ("eps_rel", ctypes.c_double), ("contraction", ctypes.c_int)]
+                ("eps_rel", ctypes.c_double), ("contraction", ctypes.c_int),
+                ("kkt_dual_tol", ctypes.c_double), ("kkt_comp_tol", ctypes.c_double)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -50,13 +51,16 @@ class TraceEntry(ctypes.Structure):
 class UpdateStats(ctypes.Structure):
     _fields_ = [("primal_res", ctypes.c_double), ("dual_res", ctypes.c_double),
                 ("norm_A", ctypes.c_double), ("norm_At", ctypes.c_double),
-                ("norm_Y", ctypes.c_double), ("rho", ctypes.c_double)]
+                ("norm_Y", ctypes.c_double), ("rho", ctypes.c_double),
+                ("kkt_neg_x", ctypes.c_double), ("kkt_dual", ctypes.c_double),
+                ("kkt_comp", ctypes.c_double)]
 
 
 class RunStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
-                ("reached_target", ctypes.c_int), ("reserved", ctypes.c_int),
-                ("rel_err", ctypes.c_double)]
+                ("reached_target", ctypes.c_int), ("kkt_met", ctypes.c_int),
+                ("rel_err", ctypes.c_double), ("kkt_dual", ctypes.c_double),
+                ("kkt_comp", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -207,8 +211,9 @@ def mttkrp_noalloc(X: torch.Tensor, mode: int, F: Sequence[Optional[torch.Tensor
     _mat(out, dims[mode], R, "out", device=X.device)
     cdims = (_I64 * len(dims))(*dims)
     dtype = NTF_F32 if X.dtype == torch.float32 else NTF_BF16
-    _check(lib().ntf_mttkrp_noalloc(len(dims), cdims, R, dtype, _ptr(X), mode, _ptr_array(F),
-                                    _ptr(out), _stream_ptr(stream)))
+    with torch.cuda.device(X.device):      # the entry point works on the current device
+        _check(lib().ntf_mttkrp_noalloc(len(dims), cdims, R, dtype, _ptr(X), mode,
+                                        _ptr_array(F), _ptr(out), _stream_ptr(stream)))
     return out
 
 
@@ -334,7 +339,7 @@ class Context:
                            int(check_every), hist, ctypes.byref(rs))
         if st != 0 and (st != 6 or raise_not_converged):
             _check(st)
-        out = {k: getattr(rs, k) for k, _ in RunStats._fields_ if k != "reserved"}
+        out = {k: getattr(rs, k) for k, _ in RunStats._fields_}
         if history:
             out["history"] = [hist[i] for i in range(max_outer)]
         return out

@@ -81,31 +81,77 @@ class RowSet:
                 T_all[ridx].contiguous())
 
 
+def _collinear_weight(congruence: float) -> float:
+    """Mixing weight a of columns a u0 + (1 - a) u_r (u0, u_r i.i.d. U[0,1]) whose expected
+    congruence is `congruence` (moments of U[0,1]: E[u^2] = 1/3, E[u u'] = 1/4), by
+    bisection."""
+    def c(a):
+        cross = a * a / 3 + a * (1 - a) / 2 + (1 - a) ** 2 / 4
+        return cross / (a * a / 3 + a * (1 - a) / 2 + (1 - a) ** 2 / 3)
+    lo, hi = 0.0, 1.0
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if c(mid) < congruence else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
 def synthetic_tensor(dims: Sequence[int], R: int, seed: int, snr_db: float = 20.0,
-                     device: str = "cuda"):
-    """Tensor and start of the synthetic workload, drawn on the device: factors i.i.d.
-    uniform[0, 1], X = [F_1, ..., F_N] + Gaussian noise at `snr_db` (SNR = ||X_0||^2 /
-    (numel sigma^2)), start factors i.i.d. uniform[0, 1].  Same recipe as the host generator
-    of the tests, with the device's random streams."""
+                     device: str = "cuda", structure: str = "uniform",
+                     zero_frac: float = 0.5, congruence: float = 0.9):
+    """Tensor and start of a synthetic workload, drawn on the device with the device's random
+    streams: factors i.i.d. uniform[0, 1] (``structure="sparse"``: each entry zeroed with
+    probability `zero_frac`; ``"collinear"``: column r = a u0 + (1 - a) u_r with the weight a
+    of expected congruence `congruence`), X = [F_1, ..., F_N] + i.i.d. Gaussian noise at
+    `snr_db` (SNR = ||X_0||^2 / (numel sigma^2), ||X_0||^2 from the Hadamard product of the
+    factors' Grams), start factors i.i.d. uniform[0, 1].  The recipe of the host generator of
+    the tests."""
     g = torch.Generator(device=device).manual_seed(int(seed))
-    F = [torch.rand(int(d), R, generator=g, device=device) for d in dims]
-    letters = "abcd"[:len(dims)]
-    X = torch.einsum(",".join(f"{c}r" for c in letters) + "->" + letters, *F).contiguous()
-    sigma = math.sqrt(float(X.double().pow(2).sum()) / X.numel() / 10.0 ** (snr_db / 10.0))
+    F = []
+    for d in dims:
+        f = torch.rand(int(d), R, generator=g, device=device)
+        if structure == "sparse":
+            f[torch.rand(int(d), R, generator=g, device=device) < zero_frac] = 0.0
+            for r in (f.max(dim=0).values <= 0).nonzero().flatten().tolist():
+                while not bool((f[:, r] > 0).any()):  # an all-zero column: draw it again
+                    col = torch.rand(int(d), generator=g, device=device)
+                    col[torch.rand(int(d), generator=g, device=device) < zero_frac] = 0.0
+                    f[:, r] = col
+        elif structure == "collinear":
+            a = _collinear_weight(congruence)
+            u0 = torch.rand(int(d), 1, generator=g, device=device)
+            f = a * u0 + (1 - a) * f
+        elif structure != "uniform":
+            raise ValueError(f"unknown structure {structure!r}")
+        F.append(f)
+    # X = KR(leading factors) KR(trailing factors)^T as one product, then the tensor's shape
+    def kr(fs):
+        t = fs[0]
+        for f in fs[1:]:
+            t = (t[:, None, :] * f[None, :, :]).reshape(-1, R)
+        return t
+    s = 2 if len(dims) == 4 else 1
+    X = (kr(F[:s]) @ kr(F[s:]).T).reshape([int(d) for d in dims])
+    G = torch.ones(R, R, dtype=torch.float64, device=device)
+    for f in F:
+        G *= f.double().T @ f.double()
+    numel = X.numel()
+    sigma = math.sqrt(float(G.sum()) / numel / 10.0 ** (snr_db / 10.0))
     X.add_(torch.randn(X.shape, generator=g, device=device), alpha=sigma)
     init = [torch.rand(int(d), R, generator=g, device=device) for d in dims]
     return X, init
 
 
 def training_set(dims: Sequence[int], R: int, rows: int, sweeps: int = 2, seed0: int = 1,
-                 snr_db: float = 20.0, conv_iters: int = 300, storage: str = "fp32") -> RowSet:
+                 snr_db: float = 20.0, conv_iters: int = 300, storage: str = "fp32",
+                 **structure) -> RowSet:
     """Rows of the first `sweeps` outer iterations of synthetic tensors with seeds seed0,
-    seed0 + 1, ... until at least `rows` rows are collected."""
+    seed0 + 1, ... until at least `rows` rows are collected (`structure`: the keyword
+    arguments of the generator's factor structure)."""
     from . import ntf as _ntf
     out = RowSet(R)
     seed = seed0
     while out.rows < rows:
-        X, init = synthetic_tensor(dims, R, seed, snr_db)
+        X, init = synthetic_tensor(dims, R, seed, snr_db, **structure)
         if storage == "bf16":
             X = _ntf.to_bf16(X)
         harvest(X, R, init, outer=sweeps, rows=out, conv_iters=conv_iters)
@@ -185,9 +231,10 @@ def eval_loss(net: ntf.Mlp, rows: RowSet, groups_per_batch: int) -> float:
 def time_to_fit(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], target: float,
                 max_outer: int, net: Optional[ntf.Mlp] = None, repeats: int = 1,
                 params: Optional[ntf.Params] = None, ws_sweeps: int = 1):
-    """Time (CUDA events) of factorizations from `init` until rel_err <= target, on a fresh
-    non-default stream (so the sweep is replayed as a CUDA graph).  Returns a dict with the
-    median seconds, iterations, final error and the warm-start row counts."""
+    """Time (CUDA events) of factorizations from `init` until rel_err <= target (or another
+    stopping rule of `params`: the KKT tolerances), on a fresh non-default stream (so the
+    sweep is replayed as a CUDA graph).  Returns a dict with the median seconds, iterations,
+    final error, the rules met, the KKT measures and the warm-start row counts."""
     p = params or ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
     stream = torch.cuda.Stream()
     times, res = [], None
@@ -216,5 +263,7 @@ def time_to_fit(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], target: f
                     times.append(e0.elapsed_time(e1) / 1000.0)
     return {"seconds": float(np.median(times)), "iters": res["iters"],
             "rel_err": res["rel_err"], "reached": bool(res["reached_target"]),
+            "kkt_met": bool(res["kkt_met"]), "kkt_dual": res["kkt_dual"],
+            "kkt_comp": res["kkt_comp"],
             "ws_considered": prof["ws_rows_considered"] - prof0["ws_rows_considered"],
             "ws_accepted": prof["ws_rows_accepted"] - prof0["ws_rows_accepted"]}

@@ -158,6 +158,32 @@ def test_system_reports_not_spd(ntf):
         assert ctx.system(0) == 1.0
 
 
+def test_trace_policy_update_reports_not_spd(ntf):
+    """The same injection under the trace penalty, whose factor update builds its own FP64
+    LDL^T factorization: the update fails with NOT_SPD, leaves the state, and works again once
+    the input is repaired."""
+    R, dims = 6, (8, 9, 10)
+    X, fs = _problem(dims, R)
+    p = ntf.default_params(paper_mode=False)
+    with ntf.Context(cuda(X), R, p) as ctx:
+        bad = fs[2].copy()
+        bad[5, 1] = np.nan
+        ctx.gram(0, cuda(fs[0]))
+        ctx.gram(1, cuda(fs[1]))
+        ctx.gram(2, cuda(bad))
+        At = torch.rand(8, R, device="cuda")
+        before = At.clone()
+        with pytest.raises(ntf.NTFError) as e:
+            ctx.admm_update(0, torch.ones(8, R, device="cuda"), torch.empty(8, R, device="cuda"),
+                            At, torch.zeros(8, R, device="cuda"))
+        assert e.value.status == 4
+        assert torch.equal(At, before)
+        ctx.gram(2, cuda(fs[2]))
+        st = ctx.admm_update(0, torch.ones(8, R, device="cuda"), torch.empty(8, R, device="cuda"),
+                             At, torch.zeros(8, R, device="cuda"))
+        assert st["rho"] > 0 and torch.isfinite(At).all()
+
+
 @pytest.mark.parametrize("dims,R,L,policy", [((40, 30, 20), 5, 1, "trace"),
                                               ((64, 48, 40), 20, 5, "trace"),
                                               ((90, 30, 20), 50, 5, "trace"),
@@ -166,7 +192,9 @@ def test_system_reports_not_spd(ntf):
                                               ((70, 36, 40), 32, 4, "trace"),   # widest 1-lane rows
                                               ((70, 36, 40), 32, 4, "fixed"),   # same, FP64 rows
                                               ((50, 44, 41), 33, 3, "trace"),   # first 2-lane rank
-                                              ((300, 20, 12), 1, 2, "fixed")])  # R = 1, many blocks
+                                              ((300, 20, 12), 1, 2, "fixed"),   # R = 1, many blocks
+                                              ((70, 30, 40), 64, 2, "trace"),   # maximum rank
+                                              ((40, 30, 20), 16, 5, "trace")])
 def test_admm_update(ntf, dims, R, L, policy):
     X, fs = _problem(dims, R, seed=11, signed=True)
     rng = np.random.default_rng(5)
@@ -196,6 +224,14 @@ def test_admm_update(ntf, dims, R, L, policy):
             for k in ("primal_res", "dual_res", "norm_A", "norm_At", "norm_Y"):
                 want = getattr(s, k)
                 assert abs(st[k] - want) <= TOL * max(want, s.norm_At), k
+            # KKT measures of the factor's NNLS problem (eq. KKT_NTF) at the GPU's new At,
+            # against the oracle's from the same At: the GPU forms the gradient At G - M in
+            # FP32, so beyond 1e-4 relative it is allowed 4 R 2^-24 in the scaled units
+            kk = o.kkt_nnls(G, M, host(At_d))
+            assert st["kkt_neg_x"] == 0.0 and kk["neg_x"] == 0.0
+            for k in ("dual", "comp"):
+                assert abs(st["kkt_" + k] - kk[k]) <= 1e-4 * kk[k] + 4 * R * 2.0 ** -24, \
+                    (k, st["kkt_" + k], kk[k])
             # the stored Gram of this factor now comes from the new auxiliary factor
             # (kr_source = aux); check through the next system's coefficient matrix
             F64[n] = host(At_d).astype(np.float64)
@@ -442,3 +478,38 @@ def test_trace_of_a_sweep(ntf):
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_full_size_1000_cubed_r32(ntf, storage):
     _sampled_rows(ntf, (1000, 1000, 1000), 32, storage=storage, snr=30.0, nrows=2)
+
+
+@pytest.mark.parametrize("check_every", [1, 2])
+def test_run_stops_at_the_kkt_tolerance(ntf, check_every):
+    """The KKT stopping rule (every factor's scaled dual infeasibility and complementarity at
+    or below the tolerances, eq. KKT_NTF) stops the run at the first checked sweep that meets
+    it: the state equals, bit for bit, a run of exactly that many sweeps, which reports the
+    same measures, and the checked sweep before it did not meet the rule."""
+    dims, R = (40, 36, 32), 4
+    X, fs, init = synth.workload(dims, R, seed=3, snr_db=20.0)
+    fresh = lambda: ([cuda(F) for F in init], [cuda(F) for F in init],
+                     [torch.zeros(d, R, device="cuda") for d in dims])
+    p0 = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    with ntf.Context(cuda(X), R, p0) as ctx:   # the measures after 8 sweeps set the tolerances
+        A, At, Y = fresh()
+        r8 = ctx.run(A, At, Y, 8, check_every=1)
+    tol_d, tol_c = 1.0001 * r8["kkt_dual"], 1.0001 * r8["kkt_comp"]
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0, kkt_dual_tol=tol_d,
+                           kkt_comp_tol=tol_c)
+    with ntf.Context(cuda(X), R, p) as ctx:
+        A, At, Y = fresh()
+        rs = ctx.run(A, At, Y, 200, check_every=check_every)
+    assert rs["kkt_met"] == 1 and rs["iters"] < 200
+    assert rs["kkt_dual"] <= tol_d and rs["kkt_comp"] <= tol_c
+    assert rs["iters"] % check_every == 0
+    with ntf.Context(cuda(X), R, p0) as ctx:
+        A2, At2, Y2 = fresh()
+        rk = ctx.run(A2, At2, Y2, rs["iters"], check_every=1)
+        assert rk["kkt_dual"] == rs["kkt_dual"] and rk["kkt_comp"] == rs["kkt_comp"]
+        for a, b in zip(At, At2):
+            assert torch.equal(a, b)
+        if rs["iters"] > check_every:
+            A3, At3, Y3 = fresh()
+            rp = ctx.run(A3, At3, Y3, rs["iters"] - check_every, check_every=1)
+            assert not (rp["kkt_dual"] <= tol_d and rp["kkt_comp"] <= tol_c)

@@ -6,6 +6,7 @@ import importlib.util
 import os
 import socket
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -63,43 +64,58 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("LOCAL_RANK", "1")
 
     class Args:
-        gpus, steps, warmup = 2, 1, 0
+        gpus, steps, warmup, workload = 2, 1, 0, bench.DEFAULT_WORKLOAD
 
     called = []
-    monkeypatch.setattr(bench, "_workload", lambda seed: called.append(seed))
+    monkeypatch.setattr(bench, "oracle_sample", lambda name, seed=0: called.append(name))
     bench.run_reference(Args())
     assert called == [] and capsys.readouterr().out == ""
 
 
 def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
     """Rank 0 of the reference arm prints one JSON line with the keys of the benchmark
-    contract: the oracle's time per iteration times the iterations the oracle needs."""
+    contract: the oracle's time per iteration on a slab, scaled to the full tensor, times the
+    iterations the method needs to reach the fit."""
     import json
     bench = _bench()
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
 
     class Args:
-        gpus, steps, warmup = 1, 2, 3
+        gpus, steps, warmup, workload = 1, 2, 3, bench.DEFAULT_WORKLOAD
 
-    monkeypatch.setattr(bench, "_workload", lambda seed: (None, None))
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda name, seed=0: (np.zeros((4, 5, 6)), None, 10.0))
     monkeypatch.setattr(bench, "cpu_oracle_seconds_per_iteration", lambda X, init, n: 0.5)
     bench.run_reference(Args())
     lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    n_iter, _ = bench._stored_iterations()
+    n_iter = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]["fit_iters"]
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
                 "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC
-    assert d["value"] == pytest.approx(0.5 * n_iter) and d["higher_is_better"] is False
+    assert d["value"] == pytest.approx(0.5 * 10.0 * n_iter) and d["higher_is_better"] is False
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["extrapolated"] is True
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == bench.WORKLOAD
-    assert 1 <= n_iter <= 200
+    assert d["config"]["workload"] == bench.DEFAULT_WORKLOAD
+
+
+def test_oracle_sample_is_a_slab_of_the_workload():
+    """The oracle's sample of the 1000^3 workload is a slab over the last mode with at most
+    1e8 entries; the scale brings its time per iteration to the full tensor."""
+    bench = _bench()
+    dims = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]["dims"]
+    rest = int(np.prod(dims[:-1]))
+    last = max(1, min(dims[-1], bench.ORACLE_SAMPLE_NUMEL // rest))
+    assert last * rest <= bench.ORACLE_SAMPLE_NUMEL
+    assert (rest * dims[-1]) / (rest * last) == pytest.approx(10.0)
+    X, init, scale = bench.oracle_sample("400x400x400_r20")   # small enough: the whole tensor
+    assert X.shape == (400, 400, 400) and scale == 1.0 and len(init) == 3
 
 
 def test_clock_summary_reads_the_samples_of_the_timed_region():
