@@ -315,6 +315,20 @@ const char* ntf_mlp_last_error(void);
  * not own the network. */
 ntf_status ntf_attach_warmstart(ntf_ctx* ctx, ntf_mlp* net, int sweeps);
 
+/* Training rows of the warm-start network from one factor update (the inputs the update's own
+ * warm start forms): with the stored Grams and the penalty policy, the factor's coefficient
+ * system is built as ntf_admm_update builds it; then, with s = trace(G)/R,
+ *   d_Gn      [R, R]    = G / s                         (G: the coefficient matrix, no rho)
+ *   d_mrows   [I, 2R]   = [m / s ; z],  z = (G + rho I)^{-1} m, per MTTKRP row m of d_M
+ *   d_targets [I, 2R]   = [At ; Y / s]  from d_At, d_Y  (optional: NULL skips it)
+ * and *s_out = s (host).  Under the trace policy rho = s, so z = (G + s I)^{-1} m, the first
+ * primal iterate of the row's ADMM from zero (eq. ADMM_NTF_ALS_C).  Device arrays are
+ * caller-owned, FP32 row-major; I = dims[mode].  Synchronizes; NTF_ERR_NOT_SPD if the system
+ * failed. */
+ntf_status ntf_warmstart_rows(ntf_ctx* ctx, int mode, const float* d_M, const float* d_At,
+                              const float* d_Y, float* d_Gn, float* d_mrows, float* d_targets,
+                              double* s_out);
+
 /* MTTKRP that allocates nothing.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc on their call path -- services that reserve all
  * device memory at start-up and treat any later allocation as a failure, or host code where

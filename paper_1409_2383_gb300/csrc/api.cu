@@ -1077,6 +1077,37 @@ ntf_status ntf_attach_warmstart(ntf_ctx* c, ntf_mlp* net, int sweeps) {
   return NTF_OK;
 }
 
+ntf_status ntf_warmstart_rows(ntf_ctx* c, int mode, const float* d_M, const float* d_At,
+                              const float* d_Y, float* d_Gn, float* d_mrows, float* d_targets,
+                              double* s_out) {
+  (void)cudaGetLastError();  // a stale non-sticky error is not this call's
+  NTF_TRY(check_mode(c, mode));
+  if (!d_M || !d_Gn || !d_mrows || !s_out)
+    return fail(NTF_ERR_INVALID_ARG, "null MTTKRP, feature output or s");
+  if (d_targets && (!d_At || !d_Y))
+    return fail(NTF_ERR_INVALID_ARG, "targets need the auxiliary and the dual");
+  for (const void* q : {static_cast<const void*>(d_M), static_cast<const void*>(d_At),
+                        static_cast<const void*>(d_Y), static_cast<const void*>(d_Gn),
+                        static_cast<const void*>(d_mrows), static_cast<const void*>(d_targets)})
+    if (misaligned(q, sizeof(float))) return fail(NTF_ERR_INVALID_ARG, "misaligned matrix");
+  const int R = c->R;
+  const int64_t I = c->dims[mode];
+  // the factor's coefficient system, as its update builds it (stored Grams, penalty policy)
+  NTF_CUDA(ntf::launch_update_system(make_call(c, mode, d_M, nullptr, nullptr, nullptr, false),
+                                     c->st));
+  float* s_dev = reinterpret_cast<float*>(c->dpart);  // scratch of the context
+  NTF_CUDA(ntf::ws_prepare(ntf::update_sys_h32(c->sys, mode, R),
+                           ntf::update_sys_hinv32(c->sys, mode, R), d_M, R, I, d_Gn, d_mrows,
+                           s_dev, c->st));
+  if (d_targets) NTF_CUDA(ntf::ws_targets(d_At, d_Y, s_dev, R, I, d_targets, c->st));
+  float s_h = 0.0f;
+  NTF_CUDA(cudaMemcpyAsync(&s_h, s_dev, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  NTF_CUDA(cudaStreamSynchronize(c->st));
+  *s_out = s_h;
+  NTF_TRY(read_ctrl(c));
+  return take_status(c);
+}
+
 ntf_status ntf_sync(ntf_ctx* c) {
   if (!c) return fail(NTF_ERR_INVALID_ARG, "null context");
   NTF_TRY(read_ctrl(c));

@@ -736,6 +736,28 @@ cudaError_t ws_prepare(const float* G, const float* Hinv, const float* M, int R,
   return cudaGetLastError();
 }
 
+// Training targets of factor rows: out[row] = [At_row ; Y_row / s] (s = trace(G)/R on the
+// device), the network's output layout.
+__global__ void k_ws_targets(const float* __restrict__ At, const float* __restrict__ Y,
+                             const float* __restrict__ s_ptr, int R, int64_t I,
+                             float* __restrict__ out) {
+  const float inv = 1.0f / *s_ptr;
+  const int64_t n = I * 2 * R;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = k / (2 * R);
+    const int c = static_cast<int>(k % (2 * R));
+    out[k] = c < R ? At[row * R + c] : Y[row * R + c - R] * inv;
+  }
+}
+
+cudaError_t ws_targets(const float* At, const float* Y, const float* s_ptr, int R, int64_t I,
+                       float* out, cudaStream_t st) {
+  const int64_t n = I * 2 * R;
+  k_ws_targets<<<blocks_for(n), 256, 0, st>>>(At, Y, s_ptr, R, I, out);
+  return cudaGetLastError();
+}
+
 cudaError_t ws_judge(const float* out, const float* G, const float* M, const float* s_ptr,
                      float* At, float* Y, int64_t I, int R, unsigned long long* counters,
                      cudaStream_t st) {

@@ -256,6 +256,9 @@ cudaError_t mlp_row_groups(const int* offs, int groups, int* row_group, cudaStre
 cudaError_t mlp_refresh_bf16(const MlpShape& s, const float* p, __nv_bfloat16* pb, cudaStream_t st);
 cudaError_t ws_prepare(const float* G, const float* Hinv, const float* M, int R, int64_t I,
                        float* Gn, float* mrows, float* s_out, cudaStream_t st);
+// out [I, 2R] = [At ; Y / s] (training targets; s read from the device)
+cudaError_t ws_targets(const float* At, const float* Y, const float* s_ptr, int R, int64_t I,
+                       float* out, cudaStream_t st);
 cudaError_t ws_judge(const float* out, const float* G, const float* M, const float* s_ptr,
                      float* At, float* Y, int64_t I, int R, unsigned long long* counters,
                      cudaStream_t st);

@@ -271,60 +271,76 @@ template <int S, int NT>
 __device__ void system_ldl(const UpdArgs& a) {
   __shared__ double s_col[2][kMaxRank];  // column k + 1 of B, published during step k
   __shared__ double s_piv[2], s_c[2];
-  __shared__ double s_red[NT / 32], s_gmax[NT / 32];
+  __shared__ double s_rho;
+  __shared__ unsigned long long s_gmax[NT / 32];
   __shared__ double s_pk[kMaxRank], s_ck[kMaxRank];  // b_kk and c of every step
   __shared__ float s_l[S * NT];                       // L, then W = L^{-1} (packed by column)
   __shared__ float s_dinv[kMaxRank];
   const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SysView sv = sys_view(a.sys, a.mode, R);
+  // FP64 instructions are scarce on this GPU (a small fraction of the FP32 rate), so the
+  // prologue spends them only on the Hadamard products: |h| maxima on the bit patterns (the
+  // order of non-negative doubles), the trace by one warp from the diagonals.
   double v[S];
   int ii[S], jj[S];
-  double tr = 0.0, gmax = 0.0;
+  unsigned long long gmax = 0;
 #pragma unroll
   for (int q = 0; q < S; ++q) {
     const int p = tid + NT * q;
     int j = -1, i = -1;
-    if (p < T) {  // column j of the packing holds rows j .. R-1
-      j = 0;
-      while (col_start(j + 1, R) <= p) ++j;
+    if (p < T) {  // column j of the packing holds rows j .. R-1: col_start(j) <= p
+      const float b2 = 2.0f * R + 1.0f;
+      j = static_cast<int>((b2 - sqrtf(b2 * b2 - 8.0f * p)) * 0.5f);
+      j = j < 0 ? 0 : j > R - 1 ? R - 1 : j;
+      while (j > 0 && col_start(j, R) > p) --j;
+      while (j + 1 < R && col_start(j + 1, R) <= p) ++j;
       i = j + (p - col_start(j, R));
     }
     ii[q] = i;
     jj[q] = j;
     double h = 0.0;
     if (p < T) {
-      double g[kMaxOrder];  // loads first, then the product
-#pragma unroll
-      for (int m = 0; m < kMaxOrder; ++m)
-        g[m] = m < a.N && m != a.mode ? a.grams[m * RR + i * R + j] : 1.0;
-      h = g[0];
-#pragma unroll
-      for (int m = 1; m < kMaxOrder; ++m) h *= g[m];
-      sv.h32[i * R + j] = static_cast<float>(h);
-      sv.h32[j * R + i] = static_cast<float>(h);
-      if (i == j) tr += h;
-      gmax = fmax(gmax, fabs(h));
+      // the other factors' Grams: factors o = k (k < mode) or k + 1, k = 0 .. N-2; loads
+      // first, then the N - 2 products
+      const int e = i * R + j;
+      const double g0 = a.grams[(0 < a.mode ? 0 : 1) * RR + e];
+      const double g1 = a.grams[(1 < a.mode ? 1 : 2) * RR + e];
+      const double g2 = a.N > 3 ? a.grams[(2 < a.mode ? 2 : 3) * RR + e] : 1.0;
+      h = g0 * g1;
+      if (a.N > 3) h *= g2;
+      const float hf = static_cast<float>(h);
+      sv.h32[i * R + j] = hf;
+      sv.h32[j * R + i] = hf;
+      const unsigned long long bits =
+          static_cast<unsigned long long>(__double_as_longlong(h)) & 0x7FFFFFFFFFFFFFFFull;
+      gmax = bits > gmax ? bits : gmax;
     }
     v[q] = h;
   }
   for (int off = 16; off > 0; off >>= 1) {
-    tr += __shfl_xor_sync(0xffffffffu, tr, off);
-    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, gmax, off);
+    gmax = o > gmax ? o : gmax;
   }
-  if (lane == 0) {
-    s_red[warp] = tr;
-    s_gmax[warp] = gmax;
+  if (lane == 0) s_gmax[warp] = gmax;
+  if (warp == 0) {  // trace(G) = sum_j prod_m Gram_m[j, j]
+    double t = 0.0;
+    for (int j = lane; j < R; j += 32) {
+      double d = 1.0;
+      for (int m = 0; m < a.N; ++m)
+        if (m != a.mode) d *= a.grams[m * RR + j * R + j];
+      t += d;
+    }
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) s_rho = t / R;
   }
   __syncthreads();
-  double t = 0.0, gm = 0.0;
-#pragma unroll
-  for (int w = 0; w < NT / 32; ++w) {
-    t += s_red[w];
-    gm = fmax(gm, s_gmax[w]);
+  const double rho = s_rho;
+  if (tid == 0) {
+    unsigned long long g = 0;
+    for (int w = 0; w < NT / 32; ++w) g = s_gmax[w] > g ? s_gmax[w] : g;
+    a.ctrl->kkt[a.mode][3] = __longlong_as_double(static_cast<long long>(g));  // max |G|
   }
-  const double rho = t / R;
-  if (tid == 0) a.ctrl->kkt[a.mode][3] = gm;
   bool fail = !(rho > 0.0) || !isfinite(rho);
 #pragma unroll
   for (int q = 0; q < S; ++q) {
@@ -446,10 +462,13 @@ __device__ void system_ldl(const UpdArgs& a) {
 }
 
 // The coefficient system of a factor update: the FP64 factorization above under the trace
-// policy, the FP64 sweep operator otherwise (the rows then run in FP64).
+// policy for R >= kLdlMinRank, the FP64 sweep operator otherwise (under the other policies the
+// rows then run in FP64 from its FP64 inverse).  Measured per launch on GB300: R = 20: sweep
+// 11.9 us, LDL^T 18.2 us; R = 32: 70 / 46 us; R = 50: 158 / 99 us; R = 64: 159 us (LDL^T).
+constexpr int kLdlMinRank = 28;
 template <int S, int NT>
 __device__ __forceinline__ void system_any(const UpdArgs& a) {
-  if (a.rho_policy == NTF_RHO_TRACE) system_ldl<S, NT>(a);
+  if (a.rho_policy == NTF_RHO_TRACE && a.R >= kLdlMinRank) system_ldl<S, NT>(a);
   else system_body<S, NT>(a);
 }
 
@@ -536,7 +555,7 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
 // update; x = H^{-1} v takes v_k from lane k by shuffles.  kR = R rounded up to a multiple of
 // 4 fixes the loop lengths at compile time (the padding lanes and columns hold zeros).
 template <typename Real, int kR>
-__global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
+__global__ void __launch_bounds__(kRowThreads, 1) k_update_rows32(UpdArgs a) {
   __shared__ double frow[kRowWarps][32];  // FP64 copies: one conversion per element
   __shared__ double red[kRowWarps][kScal];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -547,14 +566,18 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
   // system slot and the rows are valid memory either way)
   const int bad = a.ctrl->bad[a.mode] | a.ctrl->stop;
   Real hc[kR];
+  float gc[kR];  // column of the FP32 coefficient matrix G (no rho): fit and KKT terms
 #pragma unroll
   for (int k = 0; k < kR; ++k) {
     Real v = 0;
+    float gv = 0.0f;
     if (k < R && h) {
       if constexpr (sizeof(Real) == 4) v = __ldg(sv.hinv32 + k * R + lane);
       else v = __ldg(sv.hinv64 + k * R + lane);
+      gv = __ldg(sv.h32 + k * R + lane);
     }
     hc[k] = v;
+    gc[k] = gv;
   }
   const Real rho = static_cast<Real>(a.ctrl->stats[a.mode][5]);
   const int64_t row = static_cast<int64_t>(blockIdx.x) * kRowWarps + warp;
@@ -607,10 +630,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
     if (a.want_fit) {
       part[5] = static_cast<float>(m) * f;
 #pragma unroll
-      for (int k = 0; k < kR; ++k) {
-        const float fk = __shfl_sync(0xffffffffu, f, k);
-        if (k < R && h) g = fmaf(__ldg(sv.h32 + k * R + lane), fk, g);
-      }
+      for (int k = 0; k < kR; ++k) g = fmaf(gc[k], __shfl_sync(0xffffffffu, f, k), g);
       part[6] = f * g;
     }
     // KKT of the row problem min_{x >= 0} 1/2 x^T G x - m^T x at x = At (eq. KKT_NTF):
@@ -619,10 +639,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows32(UpdArgs a) {
     if (!(a.want_fit && a.kr_aux)) {
       gt = 0.0f;
 #pragma unroll
-      for (int k = 0; k < kR; ++k) {
-        const float tk = __shfl_sync(0xffffffffu, ft, k);
-        if (k < R && h) gt = fmaf(__ldg(sv.h32 + k * R + lane), tk, gt);
-      }
+      for (int k = 0; k < kR; ++k) gt = fmaf(gc[k], __shfl_sync(0xffffffffu, ft, k), gt);
     }
     if (h) {
       const float gr = gt - static_cast<float>(m);

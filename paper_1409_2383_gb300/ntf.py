@@ -108,6 +108,8 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_double), _P]),
     "ntf_mlp_last_error": (ctypes.c_char_p, []),
     "ntf_attach_warmstart": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "ntf_warmstart_rows": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P,
+                                          ctypes.POINTER(ctypes.c_double)]),
     "ntf_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ntf_trace_get": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int)]),
@@ -377,6 +379,26 @@ class Context:
         return [{"name": buf[i].name.decode(), "stream": buf[i].stream, "mode": buf[i].mode,
                  "start_us": buf[i].start_us, "end_us": buf[i].end_us}
                 for i in range(min(n.value, 64))]
+
+    def warmstart_rows(self, mode: int, M: torch.Tensor, At: Optional[torch.Tensor] = None,
+                       Y: Optional[torch.Tensor] = None):
+        """Network inputs of factor `mode`'s rows (and targets [At ; Y/s] if At, Y are given)
+        with the update's own coefficient system: (Gn [R, R], rows [I, 2R], targets or None,
+        s)."""
+        I, R = self.dims[mode], self.R
+        _mat(M, I, R, "M", device=self.X.device)
+        if (At is None) != (Y is None):
+            raise ValueError("give both At and Y, or neither")
+        if At is not None:
+            _mat(At, I, R, "At", device=self.X.device)
+            _mat(Y, I, R, "Y", device=self.X.device)
+        Gn = torch.empty(R, R, device=self.X.device)
+        rows = torch.empty(I, 2 * R, device=self.X.device)
+        tg = torch.empty(I, 2 * R, device=self.X.device) if At is not None else None
+        s = ctypes.c_double()
+        _check(lib().ntf_warmstart_rows(self._h, mode, _ptr(M), _ptr(At), _ptr(Y), _ptr(Gn),
+                                        _ptr(rows), _ptr(tg), ctypes.byref(s)))
+        return Gn, rows, tg, s.value
 
     def attach_warmstart(self, net: Optional["Mlp"], sweeps: int = 0) -> None:
         """sweeps >= 1: consult the network in the first `sweeps` outer iterations of each

@@ -173,7 +173,6 @@ def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
     A = [f.clone() for f in init]
     At = [f.clone() for f in init]
     Y = [torch.zeros_like(f) for f in init]
-    H = torch.empty(R, R, dtype=torch.float64, device=X.device)
     with ntf.Context(X, R, p) as ctx, ntf.Context(X, R, pc) as conv:
         for m in range(len(dims)):
             ctx.gram(m, At[m])
@@ -182,15 +181,14 @@ def harvest(X: torch.Tensor, R: int, init: Sequence[torch.Tensor], outer: int,
             for n in range(len(dims)):
                 M = ctx.mttkrp(n, At)
                 if k % every == 0:
-                    rho = ctx.system(n, H)
-                    G = (H - rho * torch.eye(R, dtype=torch.float64, device=X.device))
-                    s = float(torch.trace(G)) / R
                     Ac, Tc, Yc = A[n].clone(), At[n].clone(), Y[n].clone()
                     conv.admm_update(n, M, Ac, Tc, Yc, stats=False)
-                    rows.Gn.append((G / s).float().reshape(-1).contiguous())
-                    Z = torch.linalg.solve(H, M.double().T).T      # (G + rho I)^{-1} m
-                    rows.mrows.append(torch.cat([M / s, Z.float()], dim=1).contiguous())
-                    rows.targets.append(torch.cat([Tc, Yc / s], dim=1).contiguous())
+                    # inputs [G/s], [m/s ; z] and targets [x* ; y*/s], formed by the library
+                    # with this update's own coefficient system (z = (G + s I)^{-1} m)
+                    Gn, mr, tg, _ = conv.warmstart_rows(n, M, Tc, Yc)
+                    rows.Gn.append(Gn.reshape(-1))
+                    rows.mrows.append(mr)
+                    rows.targets.append(tg)
                     conv.gram(n, At[n])  # restore: the converged update refreshed its Gram
                 ctx.admm_update(n, M, A[n], At[n], Y[n], stats=False)
                 conv.gram(n, At[n])

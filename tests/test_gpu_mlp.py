@@ -79,7 +79,7 @@ def _dense_U(Gn, M, offs):
     return np.array(rows)
 
 
-@pytest.mark.parametrize("R,H", [(4, 32), (8, 64), (20, 256)])
+@pytest.mark.parametrize("R,H", [(4, 32), (8, 64), (20, 256), (32, 256), (50, 256)])
 def test_forward_and_gradients_match_oracle(ntf, R, H):
     from paper_1409_2383_gb300 import warmstart
     flat = warmstart.init_params(R, H, seed=R).numpy()

@@ -158,11 +158,12 @@ def test_system_reports_not_spd(ntf):
         assert ctx.system(0) == 1.0
 
 
-def test_trace_policy_update_reports_not_spd(ntf):
+@pytest.mark.parametrize("R", [6, 32])
+def test_trace_policy_update_reports_not_spd(ntf, R):
     """The same injection under the trace penalty, whose factor update builds its own FP64
-    LDL^T factorization: the update fails with NOT_SPD, leaves the state, and works again once
-    the input is repaired."""
-    R, dims = 6, (8, 9, 10)
+    coefficient system (sweep operator for small R, LDL^T factorization for R >= 28): the
+    update fails with NOT_SPD, leaves the state, and works again once the input is repaired."""
+    dims = (8, 9, 10)
     X, fs = _problem(dims, R)
     p = ntf.default_params(paper_mode=False)
     with ntf.Context(cuda(X), R, p) as ctx:

@@ -454,3 +454,42 @@ def test_stored_trajectory_is_the_oracles():
     # it ends at its lowest value (the converged error the fit target is measured against)
     r = np.asarray(h["rfe"])
     assert len(r) == 200 and r[-1] <= r.min() * (1 + 1e-9)
+
+
+def test_paper_mode_start_has_zero_auxiliaries_and_duals():
+    """Sec. VI-A starts ADMoM from random non-negative B0, C0 with At0 = Y0 = 0 (A0 unused).
+    Pinned against the first update written out from that start: with zero auxiliary and dual
+    the first primal update of eq. (ADMM_NTF_ALS_C) is A1 = M (G + rho0 I)^{-1}, M and G from
+    B0, C0 only; then At1 = (A1)_+ and Y1 = rho0 (A1 - At1).  A start whose auxiliaries were
+    seeded with the random values (or whose A0 entered the update) gives another A1."""
+    rng = np.random.default_rng(21)
+    dims, R = (6, 5, 4), 3
+    X = rng.random(dims)
+    init = [rng.random((d, R)) for d in dims]
+    st = o.init_state(init, o.PAPER)
+    for n in range(3):
+        assert np.array_equal(st.aux[n], np.zeros((dims[n], R)))
+        assert np.array_equal(st.dual[n], np.zeros((dims[n], R)))
+    assert st.rho == [1.0, 1.0, 1.0]
+    # the first factor's update by hand, from B0 and C0 (explicit unfolding X^(1)[i, j + J k])
+    B, C = init[1], init[2]
+    X1 = np.zeros((dims[0], dims[1] * dims[2]))
+    KR = np.zeros((dims[1] * dims[2], R))
+    for i in range(dims[0]):
+        for j in range(dims[1]):
+            for k in range(dims[2]):
+                X1[i, j + dims[1] * k] = X[i, j, k]
+    for j in range(dims[1]):
+        for k in range(dims[2]):
+            KR[j + dims[1] * k] = C[k] * B[j]
+    M = X1 @ KR
+    A1 = np.linalg.solve((KR.T @ KR + np.eye(R)).T, M.T).T
+    o.outer_iteration(X, st, o.PAPER)
+    assert np.allclose(st.primal[0], A1, rtol=1e-12, atol=1e-12)
+    assert np.allclose(st.aux[0], np.maximum(A1, 0.0), rtol=1e-12, atol=1e-12)
+    assert np.allclose(st.dual[0], A1 - np.maximum(A1, 0.0), rtol=1e-12, atol=1e-12)
+    # a start with seeded auxiliaries is not that start
+    seeded = o.State([F.copy() for F in init], [F.copy() for F in init],
+                     [np.zeros_like(F) for F in init], [1.0] * 3)
+    o.outer_iteration(X, seeded, o.PAPER)
+    assert not np.allclose(seeded.primal[0], A1, rtol=1e-6, atol=1e-9)
