@@ -177,6 +177,27 @@ ntf_status ntf_system(ntf_ctx* ctx, int mode, double* d_H, double* d_L, double* 
 ntf_status ntf_admm_update(ntf_ctx* ctx, int mode, const float* d_M, float* d_A, float* d_At,
                            float* d_Y, ntf_update_stats* stats);
 
+/* Structural constraint of a factor's auxiliary (Sec. IV-E; the constraint set of the
+ * projection in eq. ADMoM_NTF):
+ *   NTF_CONSTRAINT_NONNEG  (default) At >= 0: the projection (.)_+ of eq. ADMoM_NTF;
+ *   NTF_CONSTRAINT_BOX     lo <= At <= hi entrywise (hi may be +inf): the projection clamps;
+ *   NTF_CONSTRAINT_SPARSE  At >= 0 with at most max_nonzeros nonzero entries in the whole
+ *                          factor (eq. g_new_def): the projection keeps the max_nonzeros
+ *                          largest positive entries of A + Y / rho (ties: lower flat index
+ *                          first) and zeroes the rest.  Its inner iterations run as separate
+ *                          launches (a selection over all rows per iteration).
+ * Applies to the later ntf_admm_update and ntf_run calls of that factor.  The KKT measures of
+ * ntf_update_stats are those of the non-negative problem whatever the constraint.  Errors:
+ * NTF_ERR_INVALID_ARG for an unknown kind, lo > hi or a NaN bound, max_nonzeros < 0;
+ * NTF_ERR_UNSUPPORTED for the sparsity constraint when I_mode R >= 2^32. */
+typedef enum {
+  NTF_CONSTRAINT_NONNEG = 0,
+  NTF_CONSTRAINT_BOX = 1,
+  NTF_CONSTRAINT_SPARSE = 2
+} ntf_constraint;
+ntf_status ntf_set_constraint(ntf_ctx* ctx, int mode, int kind, double lo, double hi,
+                              int64_t max_nonzeros);
+
 /* Penalty of factor `mode` (used by ADAPTIVE and FIXED policies). */
 ntf_status ntf_set_rho(ntf_ctx* ctx, int mode, double rho);
 ntf_status ntf_get_rho(ntf_ctx* ctx, int mode, double* rho);

@@ -68,6 +68,13 @@ struct ntf_ctx {
   Ctrl* d_ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;        // pinned
   double x_norm2 = 0.0;
+  // structural constraint of each factor's auxiliary (Sec. IV-E; ntf_set_constraint)
+  int cons_kind[ntf::kMaxOrder] = {};
+  float cons_lo[ntf::kMaxOrder] = {}, cons_hi[ntf::kMaxOrder] = {};
+  int64_t cons_c[ntf::kMaxOrder] = {};
+  float* sp_V = nullptr;         // [max_dim, R] scratch of the sparsity projection
+  float* sp_tb = nullptr;        // [max_dim, R] the auxiliary before a sparse-projected update
+  unsigned* sp_sel = nullptr;    // [2] its selection
   ntf_mlp* ws = nullptr;         // attached warm-start network (not owned)
   int ws_sweeps = 0;             // consult it in the first ws_sweeps iterations of a run (0: all)
   bool ws_now = true;            // whether the sweep being enqueued consults it
@@ -382,7 +389,25 @@ ntf::UpdateCall make_call(ntf_ctx* c, int mode, const float* M, float* A, float*
   u.mu = c->prm.mu;
   u.tau_incr = c->prm.tau_incr;
   u.tau_decr = c->prm.tau_decr;
+  u.box_lo = c->cons_lo[mode];
+  u.box_hi = c->cons_hi[mode];
   return u;
+}
+
+// The rows of a factor update (the inner iterations and the update's partial sums); under
+// the sparsity constraint the inner iterations run as separate launches first.
+ntf_status launch_rows(ntf_ctx* c, const ntf::UpdateCall& u, cudaStream_t st) {
+  if (c->cons_kind[u.mode] == NTF_CONSTRAINT_SPARSE) {
+    NTF_CUDA(ntf::launch_sparse_inner(u, c->cons_c[u.mode], c->sp_V, c->sp_tb, c->sp_sel, st));
+    c->launches += ntf::sparse_inner_launches(u.inner);
+    ntf::UpdateCall t = u;
+    t.tail_only = true;
+    t.t_before = c->sp_tb;
+    NTF_CUDA(ntf::launch_update_rows(t, st));
+    return NTF_OK;
+  }
+  NTF_CUDA(ntf::launch_update_rows(u, st));
+  return NTF_OK;
 }
 
 ntf_status warm_start(ntf_ctx* c, int mode, const float* M, float* At, float* Y,
@@ -399,7 +424,7 @@ ntf_status enqueue_update(ntf_ctx* c, int mode, const float* M, float* A, float*
   const ntf::UpdateCall u = make_call(c, mode, M, A, At, Y, want_fit);
   NTF_CUDA(ntf::launch_update_system(u, c->st));
   NTF_TRY(warm_start(c, mode, M, At, Y, c->st));
-  NTF_CUDA(ntf::launch_update_rows(u, c->st));
+  NTF_TRY(launch_rows(c, u, c->st));
   NTF_CUDA(ntf::launch_update_reduce(u, c->st));
   c->launches += ntf::update_fused(u) ? 2 : 3;
   return NTF_OK;
@@ -474,7 +499,7 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
       NTF_TRY(trace_end(c, t, sa));
     }
     t = trace_begin(c, "rows", m, 0, sa);
-    NTF_CUDA(ntf::launch_update_rows(u, sa));
+    NTF_TRY(launch_rows(c, u, sa));
     NTF_TRY(trace_end(c, t, sa));
     NTF_CUDA(cudaEventRecord(c->ev_rows[m], sa));
     c->launches += 1;
@@ -770,6 +795,9 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   const size_t oFp = a0.take(64 * sizeof(double));
   const size_t oDp = a0.take(1024 * sizeof(double));
   const size_t oCtl = a0.take(sizeof(Ctrl));
+  const size_t oSpV = a0.take(c->max_dim * R * sizeof(float));
+  const size_t oSpT = a0.take(c->max_dim * R * sizeof(float));
+  const size_t oSpS = a0.take(2 * sizeof(unsigned));
   e = cudaMalloc(&c->arena[0], a0.off);
   if (e == cudaSuccess) {
     char* b = static_cast<char*>(c->arena[0]);
@@ -793,6 +821,14 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     c->fit_part = reinterpret_cast<double*>(b + oFp);
     c->dpart = reinterpret_cast<double*>(b + oDp);
     c->d_ctrl = reinterpret_cast<Ctrl*>(b + oCtl);
+    c->sp_V = reinterpret_cast<float*>(b + oSpV);
+    c->sp_tb = reinterpret_cast<float*>(b + oSpT);
+    c->sp_sel = reinterpret_cast<unsigned*>(b + oSpS);
+  }
+  for (int m = 0; m < order; ++m) {  // the non-negative orthant (eq. ADMoM_NTF)
+    c->cons_kind[m] = NTF_CONSTRAINT_NONNEG;
+    c->cons_lo[m] = 0.0f;
+    c->cons_hi[m] = HUGE_VALF;
   }
   // tensor-core plans: the split tables must exist before the tensor maps are encoded
   if (e == cudaSuccess && tc) {
@@ -1106,6 +1142,43 @@ ntf_status ntf_warmstart_rows(ntf_ctx* c, int mode, const float* d_M, const floa
   *s_out = s_h;
   NTF_TRY(read_ctrl(c));
   return take_status(c);
+}
+
+ntf_status ntf_set_constraint(ntf_ctx* c, int mode, int kind, double lo, double hi,
+                              int64_t max_nonzeros) {
+  NTF_TRY(check_mode(c, mode));
+  const int64_t n = c->dims[mode] * c->R;
+  switch (kind) {
+    case NTF_CONSTRAINT_NONNEG:
+      lo = 0.0;
+      hi = HUGE_VAL;
+      break;
+    case NTF_CONSTRAINT_BOX:
+      if (!(lo <= hi) || std::isnan(lo) || std::isnan(hi) || lo == HUGE_VAL || hi == -HUGE_VAL)
+        return fail(NTF_ERR_INVALID_ARG, "box constraint needs lo <= hi, not NaN");
+      break;
+    case NTF_CONSTRAINT_SPARSE:
+      if (max_nonzeros < 0) return fail(NTF_ERR_INVALID_ARG, "max_nonzeros must be >= 0");
+      if (n >= (int64_t{1} << 32))
+        return fail(NTF_ERR_UNSUPPORTED, "sparsity constraint needs I_n R < 2^32");
+      lo = 0.0;
+      hi = HUGE_VAL;
+      break;
+    default:
+      return fail(NTF_ERR_INVALID_ARG, "unknown constraint kind %d", kind);
+  }
+  c->cons_kind[mode] = kind;
+  c->cons_lo[mode] = static_cast<float>(lo);
+  c->cons_hi[mode] = static_cast<float>(hi);
+  c->cons_c[mode] = max_nonzeros;
+  // recorded sweeps hold the previous constraints: record them again at the next run
+  for (ntf_ctx::SweepGraph& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+  }
+  return NTF_OK;
 }
 
 ntf_status ntf_sync(ntf_ctx* c) {

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "ntf.h"
@@ -217,6 +218,13 @@ struct UpdateCall {
   int N, mode, R, inner, rho_policy;
   bool kr_aux, want_fit;
   double mu, tau_incr, tau_decr;
+  // projection of the auxiliary (Sec. IV-E): onto the box [box_lo, box_hi] (the default
+  // [0, inf) is the non-negative orthant); the at-most-c-nonzeros projection runs its inner
+  // iterations in sparse_proj.cu and the rows kernel then only forms the partial sums
+  // (tail_only, with the auxiliary before the update in t_before)
+  float box_lo = 0.0f, box_hi = HUGE_VALF;
+  bool tail_only = false;
+  const float* t_before = nullptr;
 };
 int update_blocks(int64_t I);
 int update_scalars();
@@ -273,6 +281,17 @@ cudaError_t ws_fused(const MlpShape& s, const float* p, const __nv_bfloat16* pb,
 // its system slot
 const float* update_sys_h32(const double* sys, int mode, int R);
 const float* update_sys_hinv32(const double* sys, int mode, int R);
+// FP64 (G + rho I)^{-1} of factor `mode` (written by the sweep-operator system: the policies
+// other than trace, and the trace policy for small R)
+const double* update_sys_hinv64(const double* sys, int mode, int R);
+
+// sparse_proj.cu: the inner iterations of a factor update whose auxiliary is projected onto
+// the non-negative matrices with at most c nonzeros (Sec. IV-E): copies At to t_before, then
+// per inner iteration the primal step, the selection of the c largest entries (V [I, R] and
+// sel [2] scratch) and the projection and dual step; the rows kernel then runs with tail_only
+int sparse_inner_launches(int inner);
+cudaError_t launch_sparse_inner(const UpdateCall& u, int64_t c, float* V, float* t_before,
+                                unsigned* sel, cudaStream_t st);
 
 // mlp_api.cu: warm start of a factor update by an attached network
 cudaError_t mlp_warm_start(ntf_mlp* n, const double* sys, int mode, const float* M, float* At,

@@ -77,6 +77,9 @@ struct UpdArgs {
   int N, mode, R, inner, rho_policy, kr_aux, want_fit;
   int fused;            // rows kernel also reduces (last CTA)
   double mu, tau_incr, tau_decr;
+  float box_lo, box_hi;  // projection of the auxiliary: onto [box_lo, box_hi] ((.)_+: [0, inf))
+  int tail_only;         // the inner iterations ran elsewhere: x, At, Y as stored, At before
+  const float* t_before; // the update in t_before (the partial sums and reductions only)
 };
 
 // 1/p for p > 0: the single-precision estimate refined by two Newton-Raphson steps for
@@ -586,15 +589,19 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_update_rows32(UpdArgs a) {
   const Real m = live ? static_cast<Real>(a.M[idx]) : Real(0);
   Real t = live ? static_cast<Real>(a.At[idx]) : Real(0);
   Real y = live ? static_cast<Real>(a.Y[idx]) : Real(0);
+  const bool tail = a.tail_only != 0;
+  const Real x_st = tail && live ? static_cast<Real>(a.A[idx]) : Real(0);
+  const Real t_st = tail && live ? static_cast<Real>(a.t_before[idx]) : t;
   if (bad) return;  // uniform: the system of this factor failed, or the run has stopped; the
                     // state is kept
   const Real rinv = Real(1) / rho;
+  const Real lo = a.box_lo, hi = a.box_hi;
   float part[kScal] = {};
   float f = 0.0f;
   if (row < a.I) {
-    const Real t_in = t;
-    Real x = 0;
-    for (int it = 0; it < a.inner; ++it) {
+    const Real t_in = t_st;
+    Real x = x_st;
+    for (int it = 0; it < (tail ? 0 : a.inner); ++it) {
       const Real v = m + rho * t - y;  // zero in the padding lanes
       Real p0 = 0, p1 = 0, p2 = 0, p3 = 0;
 #pragma unroll
@@ -605,7 +612,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_update_rows32(UpdArgs a) {
         p3 = fma(hc[k + 3], __shfl_sync(0xffffffffu, v, k + 3), p3);
       }
       x = h ? (p0 + p1) + (p2 + p3) : Real(0);
-      const Real n = fmax(Real(0), x + y * rinv);
+      const Real n = fmin(fmax(lo, x + y * rinv), hi);
       y += rho * (x - n);
       t = n;
     }
@@ -687,9 +694,12 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
     const Real m0 = h0 ? a.M[base + j0] : 0, m1 = h1 ? a.M[base + j1] : 0;
     Real t0 = h0 ? a.At[base + j0] : 0, t1 = h1 ? a.At[base + j1] : 0;
     Real y0 = h0 ? a.Y[base + j0] : 0, y1 = h1 ? a.Y[base + j1] : 0;
-    const Real s0 = t0, s1 = t1;
-    Real x0 = 0, x1 = 0;
-    for (int it = 0; it < a.inner; ++it) {
+    const bool tail = a.tail_only != 0;
+    const Real s0 = tail && h0 ? a.t_before[base + j0] : t0;
+    const Real s1 = tail && h1 ? a.t_before[base + j1] : t1;
+    Real x0 = tail && h0 ? a.A[base + j0] : 0, x1 = tail && h1 ? a.A[base + j1] : 0;
+    const Real lo = a.box_lo, hi = a.box_hi;
+    for (int it = 0; it < (tail ? 0 : a.inner); ++it) {
       if (h0) vb[j0] = m0 + rho * t0 - y0;
       if (h1) vb[j1] = m1 + rho * t1 - y1;
       __syncwarp();
@@ -715,7 +725,8 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
       __syncwarp();
       x0 = p0 + q0;
       x1 = p1 + q1;
-      const Real n0 = fmax(Real(0), x0 + y0 * rinv), n1 = fmax(Real(0), x1 + y1 * rinv);
+      const Real n0 = fmin(fmax(lo, x0 + y0 * rinv), hi);
+      const Real n1 = fmin(fmax(lo, x1 + y1 * rinv), hi);
       y0 += rho * (x0 - n0);
       y1 += rho * (x1 - n1);
       t0 = n0;
@@ -1042,6 +1053,9 @@ const float* update_sys_h32(const double* sys, int mode, int R) {
 const float* update_sys_hinv32(const double* sys, int mode, int R) {
   return sys_view(const_cast<double*>(sys), mode, R).hinv32;
 }
+const double* update_sys_hinv64(const double* sys, int mode, int R) {
+  return sys_view(const_cast<double*>(sys), mode, R).hinv64;
+}
 
 int update_blocks(int64_t I) { return static_cast<int>((I + kRowWarps - 1) / kRowWarps); }
 int update_scalars() { return kScal; }
@@ -1074,6 +1088,10 @@ UpdArgs make_args(const UpdateCall& u) {
   a.kr_aux = u.kr_aux ? 1 : 0;
   a.want_fit = u.want_fit ? 1 : 0;
   a.fused = update_fused(u) ? 1 : 0;
+  a.box_lo = u.box_lo;
+  a.box_hi = u.box_hi;
+  a.tail_only = u.tail_only ? 1 : 0;
+  a.t_before = u.t_before;
   a.mu = u.mu;
   a.tau_incr = u.tau_incr;
   a.tau_decr = u.tau_decr;

@@ -20,6 +20,7 @@ NTF_F32, NTF_BF16 = 0, 1
 NTF_KR_PRIMAL, NTF_KR_AUX = 0, 1
 NTF_RHO_ADAPTIVE, NTF_RHO_TRACE, NTF_RHO_FIXED = 0, 1, 2
 NTF_CONTRACT_AUTO, NTF_CONTRACT_TENSOR, NTF_CONTRACT_SIMT = 0, 1, 2
+NTF_CONSTRAINT_NONNEG, NTF_CONSTRAINT_BOX, NTF_CONSTRAINT_SPARSE = 0, 1, 2
 
 STATUS = {
     0: "NTF_OK", 1: "NTF_ERR_INVALID_ARG", 2: "NTF_ERR_CUDA", 3: "NTF_ERR_OOM",
@@ -86,6 +87,8 @@ _SIGS = {
     "ntf_admm_update": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P,
                                        ctypes.POINTER(UpdateStats)]),
     "ntf_set_rho": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "ntf_set_constraint": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, _I64]),
     "ntf_get_rho": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ntf_fit": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
     "ntf_fit_from_mttkrp": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
@@ -310,6 +313,13 @@ class Context:
             return None
         return {k: getattr(st, k) for k, _ in UpdateStats._fields_}
 
+    def set_constraint(self, mode: int, kind: int, lo: float = 0.0, hi: float = float("inf"),
+                       max_nonzeros: int = 0) -> None:
+        """Constraint set of factor `mode`'s auxiliary (NTF_CONSTRAINT_NONNEG / _BOX with
+        [lo, hi] / _SPARSE with at most `max_nonzeros` nonzeros)."""
+        _check(lib().ntf_set_constraint(self._h, mode, int(kind), float(lo), float(hi),
+                                        int(max_nonzeros)))
+
     def set_rho(self, mode: int, rho: float) -> None:
         _check(lib().ntf_set_rho(self._h, mode, float(rho)))
 
@@ -472,4 +482,5 @@ __all__ = ["Context", "Params", "NTFError", "default_params", "to_bf16", "lib", 
            "mttkrp_noalloc", "Mlp",
            "NTF_F32", "NTF_BF16", "NTF_KR_PRIMAL", "NTF_KR_AUX", "NTF_RHO_ADAPTIVE",
            "NTF_RHO_TRACE", "NTF_RHO_FIXED", "NTF_CONTRACT_AUTO", "NTF_CONTRACT_TENSOR",
-           "NTF_CONTRACT_SIMT", "LIB_PATH"]
+           "NTF_CONTRACT_SIMT", "NTF_CONSTRAINT_NONNEG", "NTF_CONSTRAINT_BOX",
+           "NTF_CONSTRAINT_SPARSE", "LIB_PATH"]
