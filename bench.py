@@ -588,6 +588,9 @@ def run_ntf(args):
             torch.cuda.empty_cache()
             main_meas, net = measure_workload(name, args, net=net, training=training)
             variants = {name: main_meas}
+            torch.cuda.empty_cache()
+            variants["sparse_mttkrp_1000x1000x1000_nnz1e8_r32"] = measure_sparse(
+                (1000, 1000, 1000), 100_000_000, 32)
             for other in VARIANT_WORKLOADS:
                 if other == name:
                     continue
@@ -682,6 +685,56 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": args.dims, "rank": args.rank, "storage": args.storage,
                       "engine": args.engine, "calls": 2 * (args.warmup + args.steps), **us,
                       **gbs}))
+
+
+def measure_sparse(dims, nnz: int, R: int, reps: int = 5) -> dict:
+    """Sparse-tensor MTTKRP (coordinate form, Sec. IV-A's sparse case) on nnz uniformly drawn
+    coordinates of a tensor of shape dims (indices and U[0,1] values drawn on the device): the
+    layout build time and, per mode, the MTTKRP time (CUDA events, median of `reps` after one
+    warm-up) with its throughput against the HBM peak; algorithmic bytes per nonzero = the
+    (N + 1) 4-byte words of the mode's layout streamed once (the factor rows it gathers are
+    L2-resident; the output is I_n R floats)."""
+    import torch
+    from paper_1409_2383_gb300 import ntf
+    g = torch.Generator(device="cuda").manual_seed(7)
+    idx = torch.stack([torch.randint(0, int(d), (nnz,), generator=g, device="cuda",
+                                     dtype=torch.int32) for d in dims], dim=1).contiguous()
+    vals = torch.rand(nnz, generator=g, device="cuda")
+    F = [torch.rand(int(d), R, generator=g, device="cuda") for d in dims]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sp = ntf.SparseTensor(idx, vals, dims)
+    build_s = time.perf_counter() - t0
+    del idx, vals
+    peak, peak_kind = _peaks()
+    N = len(dims)
+    modes = []
+    for n in range(N):
+        out = torch.empty(int(dims[n]), R, device="cuda")
+        sp.mttkrp(n, F, out=out)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sp.mttkrp(n, F, out=out)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        t = statistics.median(ts)
+        bytes_ = nnz * (N + 1) * 4 + int(dims[n]) * R * 4
+        modes.append({"mode": n, "ms": t * 1e3, "gbs": bytes_ / t / 1e9,
+                      "frac": bytes_ / t / 1e9 / peak, "gnnz_per_s": nnz / t / 1e9,
+                      "gflops": 3 * nnz * R / t / 1e9})
+    sp.close()
+    return {"dims": list(dims), "nnz": nnz, "rank": R, "layout_build_s": build_s,
+            "bytes_per_nonzero": (N + 1) * 4, "peak": peak, "peak_kind": peak_kind,
+            "modes": modes}
+
+
+def run_sparse_case(args):
+    dims = tuple(int(d) for d in args.dims.split("x"))
+    print(json.dumps({"sparse_case": measure_sparse(dims, args.nnz, args.rank,
+                                                    reps=max(args.steps, 1))}))
 
 
 def run_sweep_case(args):
@@ -829,6 +882,9 @@ def main():
     ap.add_argument("--rank", type=int, default=20)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "tensor", "simt"])
+    ap.add_argument("--sparse-case", action="store_true",
+                    help="sparse-tensor MTTKRP on --nnz random coordinates of --dims")
+    ap.add_argument("--nnz", type=int, default=100_000_000)
     ap.add_argument("--sweep-case", action="store_true",
                     help="run --steps outer iterations of the workload (for ncu launch lists)")
     ap.add_argument("--trace", action="store_true",
@@ -846,6 +902,8 @@ def main():
         run_study(args)
     elif args.kernel_case:
         run_kernel_case(args)
+    elif args.sparse_case:
+        run_sparse_case(args)
     elif args.sweep_case:
         run_sweep_case(args)
     elif args.impl == "reference":

@@ -383,6 +383,34 @@ ntf_status ntf_mttkrp_noalloc(int order, const int64_t* dims, int rank, int dtyp
                               const void* d_tensor, int mode, const float* const* d_factors,
                               float* d_M, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Sparse tensors (the sparse case of Sec. IV-A: with n nonzeros the MTTKRP costs 3nF flops
+ * for a 3-way tensor and never forms the Khatri-Rao matrix).  A tensor given in coordinate
+ * form -- d_idx [nnz, order] int32 (row-major: the order indices of each nonzero, each in
+ * [0, dims[m])), d_vals [nnz] FP32, duplicates allowed (they add up) -- is laid out once by
+ * ntf_sptensor_create: for every mode, the nonzeros sorted by that mode's index (a stable
+ * radix sort on the device) with row offsets.  The layout is owned by the object (about
+ * (order + 1) * order * 4 + 28 bytes per nonzero of device memory, allocated at creation;
+ * the inputs are not referenced afterwards).  Calls run on the stream given at creation;
+ * ntf_sptensor_create synchronizes it. */
+typedef struct ntf_sptensor ntf_sptensor;
+
+/* Errors: NTF_ERR_INVALID_ARG for an order outside [3, 4], a dim outside [1, 2^30], nnz
+ * outside [1, 2^31), a null or misaligned pointer; NTF_ERR_OOM.  Indices outside the dims are
+ * not checked (the caller's contract). */
+ntf_status ntf_sptensor_create(ntf_sptensor** out, int order, const int64_t* dims, int64_t nnz,
+                               const int32_t* d_idx, const float* d_vals, void* stream);
+ntf_status ntf_sptensor_destroy(ntf_sptensor* sp);
+
+/* d_M [I_mode, R] = MTTKRP of mode `mode` (FP32 products and sums, a fixed summation order):
+ * row i is the sum over the nonzeros with i_mode = i of v prod_{m != mode} F_m[i_m, :]
+ * (d_factors: host array of order device pointers [I_m, R], d_factors[mode] ignored).
+ * Asynchronous. */
+ntf_status ntf_sptensor_mttkrp(ntf_sptensor* sp, int mode, int rank,
+                               const float* const* d_factors, float* d_M);
+int64_t ntf_sptensor_nnz(const ntf_sptensor* sp);
+const char* ntf_sptensor_last_error(void);
+
 /* FP32 -> BF16 storage conversion (round to nearest even), n elements, on `stream`.  d_out:
  * device memory.  d_in: device memory, or page-locked host memory that the device addresses
  * directly (cudaHostAlloc / cudaMallocHost under unified addressing): the kernel then reads

@@ -124,6 +124,31 @@ def mttkrp_rows(X: np.ndarray, factors: Sequence[np.ndarray], n: int,
     return unfold(Xs, n) @ kr_others(factors, n)
 
 
+def mttkrp_coo(indices: np.ndarray, values: np.ndarray, factors: Sequence[np.ndarray],
+               n: int) -> np.ndarray:
+    """MTTKRP of a sparse tensor in coordinate form (the sparse case of Sec. IV-A: with n
+    nonzeros it costs 3nF flops for a 3-way tensor).  Entry (i_1, ..., i_N) with value v adds
+    v * prod_{m != n} F_m[i_m, :] to row i_n of M (duplicate coordinates add up, as in the dense
+    tensor they describe).  indices: [nnz, N] integers, values: [nnz]."""
+    indices = np.asarray(indices)
+    values = np.asarray(values, np.float64)
+    R = np.asarray(factors[0]).shape[1]
+    M = np.zeros((np.asarray(factors[n]).shape[0], R))
+    prod = values[:, None] * np.ones((values.size, R))
+    for m, F in enumerate(factors):
+        if m != n:
+            prod = prod * np.asarray(F, np.float64)[indices[:, m]]
+    np.add.at(M, indices[:, n], prod)
+    return M
+
+
+def coo_to_dense(indices: np.ndarray, values: np.ndarray, dims: Sequence[int]) -> np.ndarray:
+    """The dense tensor a coordinate list describes (duplicates add up)."""
+    X = np.zeros(dims)
+    np.add.at(X, tuple(np.asarray(indices).T), np.asarray(values, np.float64))
+    return X
+
+
 def gram(F: np.ndarray) -> np.ndarray:
     """F^T F in FP64."""
     F = np.asarray(F, dtype=np.float64)

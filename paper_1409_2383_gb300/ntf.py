@@ -119,6 +119,13 @@ _SIGS = {
     "ntf_mttkrp_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.c_int,
                                           ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(_P), _P,
                                           _P]),
+    "ntf_sptensor_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int,
+                                           ctypes.POINTER(_I64), _I64, _P, _P, _P]),
+    "ntf_sptensor_destroy": (ctypes.c_int, [_P]),
+    "ntf_sptensor_mttkrp": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P),
+                                           _P]),
+    "ntf_sptensor_nnz": (_I64, [_P]),
+    "ntf_sptensor_last_error": (ctypes.c_char_p, []),
     "ntf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ntf_last_error": (ctypes.c_char_p, []),
 }
@@ -474,12 +481,79 @@ class Mlp:
         return loss.value if want_loss else None
 
 
+def _scheck(status: int) -> None:
+    if status != 0:
+        raise NTFError(status, lib().ntf_sptensor_last_error().decode())
+
+
+class SparseTensor:
+    """A sparse tensor in coordinate form laid out for MTTKRP (wraps ``ntf_sptensor``):
+    indices int32 [nnz, N] and values float32 [nnz] on the GPU."""
+
+    def __init__(self, indices: torch.Tensor, values: torch.Tensor, dims: Sequence[int],
+                 stream: Optional[torch.cuda.Stream] = None):
+        if (not isinstance(indices, torch.Tensor) or not indices.is_cuda
+                or indices.dtype != torch.int32 or indices.dim() != 2
+                or not indices.is_contiguous()):
+            raise ValueError("indices must be a contiguous int32 CUDA tensor [nnz, N]")
+        if (not isinstance(values, torch.Tensor) or not values.is_cuda
+                or values.dtype != torch.float32 or values.shape != (indices.shape[0],)
+                or not values.is_contiguous() or values.device != indices.device):
+            raise ValueError("values must be a contiguous float32 CUDA tensor [nnz]")
+        self.dims = tuple(int(d) for d in dims)
+        self.N = len(self.dims)
+        if indices.shape[1] != self.N:
+            raise ValueError("indices must have one column per mode")
+        self.device = indices.device
+        self.stream = stream
+        self._h = _P()
+        cd = (_I64 * self.N)(*self.dims)
+        with torch.cuda.device(self.device):
+            _scheck(lib().ntf_sptensor_create(ctypes.byref(self._h), self.N, cd,
+                                              int(indices.shape[0]), _ptr(indices),
+                                              _ptr(values), _stream_ptr(stream)))
+
+    @property
+    def nnz(self) -> int:
+        return int(lib().ntf_sptensor_nnz(self._h))
+
+    def mttkrp(self, mode: int, F: Sequence[Optional[torch.Tensor]],
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        R = next(int(t.shape[1]) for m, t in enumerate(F) if m != mode)
+        for m, t in enumerate(F):
+            if m != mode:
+                _mat(t, self.dims[m], R, f"factor {m}", device=self.device)
+        if out is None:
+            out = torch.empty(self.dims[mode], R, device=self.device)
+        _mat(out, self.dims[mode], R, "out", device=self.device)
+        with torch.cuda.device(self.device):
+            _scheck(lib().ntf_sptensor_mttkrp(self._h, mode, R, _ptr_array(F), _ptr(out)))
+        return out
+
+    def close(self) -> None:
+        if self._h:
+            lib().ntf_sptensor_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def zeros_state(dims: Sequence[int], R: int, device="cuda") -> List[torch.Tensor]:
     return [torch.zeros(d, R, device=device) for d in dims]
 
 
 __all__ = ["Context", "Params", "NTFError", "default_params", "to_bf16", "lib", "zeros_state",
-           "mttkrp_noalloc", "Mlp",
+           "mttkrp_noalloc", "Mlp", "SparseTensor",
            "NTF_F32", "NTF_BF16", "NTF_KR_PRIMAL", "NTF_KR_AUX", "NTF_RHO_ADAPTIVE",
            "NTF_RHO_TRACE", "NTF_RHO_FIXED", "NTF_CONTRACT_AUTO", "NTF_CONTRACT_TENSOR",
            "NTF_CONTRACT_SIMT", "NTF_CONSTRAINT_NONNEG", "NTF_CONSTRAINT_BOX",

@@ -152,3 +152,28 @@ WORKLOADS = {
     "200x200x200x50_r16_collinear": dict(dims=(200, 200, 200, 50), R=16, snr_db=10.0,
                                          structure="collinear"),
 }
+
+
+def sparse_tensor(dims: Sequence[int], nnz: int, seed: int, R: Optional[int] = None,
+                  duplicates: bool = False):
+    """A sparse tensor in coordinate form: nnz coordinates drawn uniformly (distinct unless
+    ``duplicates``), values U[0,1] or, with R, the values of a rank-R model of U[0,1] factors
+    (seed's factor streams) at those coordinates.  Returns (indices int32 [nnz, N], values
+    float32 [nnz])."""
+    g = _rng(seed, _NOISE, 1 << 20)
+    numel = int(np.prod(dims))
+    if duplicates:
+        flat = g.integers(0, numel, nnz)
+    else:
+        flat = g.choice(numel, size=nnz, replace=False) if nnz < numel // 4 else \
+            g.permutation(numel)[:nnz]
+    idx = np.stack(np.unravel_index(flat, dims), axis=1).astype(np.int32)
+    if R is None:
+        vals = g.random(nnz)
+    else:
+        fs = factors(dims, R, seed)
+        prod = np.ones((nnz, R))
+        for m, F in enumerate(fs):
+            prod *= F[idx[:, m]]
+        vals = prod.sum(axis=1)
+    return idx, vals.astype(np.float32)

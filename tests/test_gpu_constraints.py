@@ -70,6 +70,10 @@ def _updates(ntf, dims, R, L, policy, cons, seed=11):
             for k in ("primal_res", "dual_res", "norm_A", "norm_At", "norm_Y"):
                 want = getattr(s, k)
                 assert abs(st[k] - want) <= TOL * max(want, s.norm_At), k
+            # the update refreshed the stored Gram of this factor from its new auxiliary
+            # (Khatri-Rao source aux): the next modes see that factor
+            F64[n] = got_t.astype(np.float64)
+            ctx.gram(n, At_d)
             yield got_t, At
 
 

@@ -493,3 +493,30 @@ def test_paper_mode_start_has_zero_auxiliaries_and_duals():
                      [np.zeros_like(F) for F in init], [1.0] * 3)
     o.outer_iteration(X, seeded, o.PAPER)
     assert not np.allclose(seeded.primal[0], A1, rtol=1e-6, atol=1e-9)
+
+
+def test_mttkrp_coo_brute_force_and_dense_equivalent():
+    """The sparse-tensor MTTKRP (Sec. IV-A, n nonzeros): against index loops on a tiny tensor
+    with a duplicated coordinate, and against the dense definition on the tensor the
+    coordinates describe (3- and 4-way, every mode)."""
+    rng = np.random.default_rng(4)
+    idx = np.array([[0, 1, 2], [2, 0, 1], [1, 1, 0], [0, 1, 2], [2, 2, 2]])
+    vals = np.array([1.5, -2.0, 0.5, 0.25, 3.0])
+    fs = [rng.random((3, 2)) for _ in range(3)]
+    for n in range(3):
+        want = np.zeros((3, 2))
+        for e in range(len(vals)):
+            for r in range(2):
+                p = vals[e]
+                for m in range(3):
+                    if m != n:
+                        p *= fs[m][idx[e, m], r]
+                want[idx[e, n], r] += p
+        assert np.allclose(o.mttkrp_coo(idx, vals, fs, n), want, rtol=1e-14, atol=1e-14)
+    for dims, R, nnz in (((7, 6, 5), 3, 40), ((4, 5, 3, 6), 2, 60)):
+        idx, vals = synth.sparse_tensor(dims, nnz, seed=1, duplicates=True)
+        fs = [rng.random((d, R)) for d in dims]
+        X = o.coo_to_dense(idx, vals, dims)
+        for n in range(len(dims)):
+            assert np.allclose(o.mttkrp_coo(idx, vals, fs, n), o.mttkrp(X, fs, n), rtol=1e-12,
+                               atol=1e-12)
