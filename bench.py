@@ -399,7 +399,7 @@ def time_form(X32, R: int, init, storage: str, net, target: float, kkt, max_oute
             c.run(A, T, Y, max_outer)
             prof = c.profile_get()
         with ntf.Context(X32, R, _params(), stream=stream) as c32:
-            err32 = c32.fit(T)
+            err32 = c32.fit_explicit(T)
     del Xf
     return {"fit": fit, "kkt": kk, "final_rfe_vs_fp32_tensor": err32,
             "roofline": _roofline_of(prof, storage, workload)}
@@ -541,7 +541,7 @@ def run_ntf(args):
         ctx.close()
         # error of the form's factors against the FP32 tensor (BF16 storage rounds the data)
         with ntf.Context(Xd, R, _params(), stream=stream) as c32:
-            rfe_vs_fp32 = c32.fit(At)
+            rfe_vs_fp32 = c32.fit_explicit(At)
 
         # end to end through the public API with host buffers: H2D of the FP32 tensor and the
         # start (BF16 form: the conversion kernel reads the pinned host tensor, so the copy and
@@ -806,7 +806,7 @@ def study_case(dims, F, sigma2, realizations, n_max, max_restarts, open_ctx, dev
             rs = restarts.factorize(ctx, A, At, Y, n_max, draw, max_restarts=max_restarts)
             sync()
             secs.append(time.perf_counter() - t0)
-            rfe.append(ctx.fit(At))
+            rfe.append(ctx.fit_explicit(At))
         conv += rs["converged"]
         nrest.append(rs["restarts"])
         iters.append(rs["iters"])

@@ -207,6 +207,13 @@ ntf_status ntf_get_rho(ntf_ctx* ctx, int mode, double* rho);
  * the last factor (one tensor pass).  Does not touch the stored Grams.  Synchronizes. */
 ntf_status ntf_fit(ntf_ctx* ctx, const float* const* d_factors, double* rel_err);
 
+/* The same error by explicit reconstruction: ||X - [F_1..F_N]||_F^2 summed entry by entry
+ * (FP32 model values, FP64 sums) over one tensor pass, with R multiply-adds per entry.  The
+ * identity above subtracts terms of size ||X||^2, so an error e ||X||^2 of <M_N, F_N> (the FP32
+ * contraction's rounding, about 1e-6 relative) moves the squared error by 2e ||X||^2: at low
+ * noise (errors near 1e-3) this call is the accurate one.  Synchronizes. */
+ntf_status ntf_fit_explicit(ntf_ctx* ctx, const float* const* d_factors, double* rel_err);
+
 /* Same, from a last-factor MTTKRP the caller already has (no tensor pass).  Uses the
  * stored Grams, which must be those of d_F_last and of the factors d_M_last was formed
  * with.  Synchronizes. */

@@ -144,7 +144,106 @@ __global__ void k_fit_finalize(const double* __restrict__ part, int nblocks,
   }
 }
 
+// Relative error by explicit reconstruction (Sec. VI-A): sum over the tensor of
+// (x - sum_r prod_m F_m[i_m, r])^2, with no cancellation between large terms (the Gram identity
+// of the fit subtracts quantities of size ||X||^2, so an error e ||X||^2 in <M, F> moves the
+// squared error by 2 e ||X||^2 -- visible at low noise).  One warp per tensor row of the last
+// mode: the product p_r of the other factors' rows is formed once (lanes over r, broadcast
+// through shared memory), then lanes take the row's entries k = lane, lane + 32, ... with the
+// model value sum_r p_r F_last[k, r] in FP32 and the squared residuals summed in FP32 per lane
+// and in FP64 across lanes, warps and blocks (fixed order).
+constexpr int kExWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kExWarps * 32) k_fit_explicit(
+    const T* __restrict__ X, int N, int64_t d0, int64_t d1, int64_t d2, int64_t K,
+    const float* __restrict__ F0, const float* __restrict__ F1, const float* __restrict__ F2,
+    const float* __restrict__ FL, int R, double* __restrict__ part) {
+  __shared__ float p[kExWarps][64];
+  __shared__ double red[kExWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t rows = N == 3 ? d0 * d1 : d0 * d1 * d2;
+  double acc = 0.0;
+  for (int64_t row = static_cast<int64_t>(blockIdx.x) * kExWarps + warp; row < rows;
+       row += static_cast<int64_t>(gridDim.x) * kExWarps) {
+    // row index -> (i0, i1[, i2]) of the leading modes, last of them fastest
+    int64_t i0, i1, i2 = 0;
+    if (N == 3) {
+      i0 = row / d1;
+      i1 = row % d1;
+    } else {
+      i0 = row / (d1 * d2);
+      i1 = (row / d2) % d1;
+      i2 = row % d2;
+    }
+    for (int r = lane; r < R; r += 32) {
+      float v = F0[i0 * R + r] * F1[i1 * R + r];
+      if (N == 4) v *= F2[i2 * R + r];
+      p[warp][r] = v;
+    }
+    __syncwarp();
+    const T* x = X + row * K;
+    float s = 0.0f;
+    for (int64_t k = lane; k < K; k += 32) {
+      const float* fl = FL + k * R;
+      float m0 = 0.0f, m1 = 0.0f;
+      int r = 0;
+      for (; r + 1 < R; r += 2) {
+        m0 = fmaf(p[warp][r], fl[r], m0);
+        m1 = fmaf(p[warp][r + 1], fl[r + 1], m1);
+      }
+      if (r < R) m0 = fmaf(p[warp][r], fl[r], m0);
+      float xv;
+      if constexpr (sizeof(T) == 2) xv = __bfloat162float(x[k]);
+      else xv = x[k];
+      const float d = xv - (m0 + m1);
+      s = fmaf(d, d, s);
+    }
+    __syncwarp();
+    double sd = s;
+    for (int off = 16; off > 0; off >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, off);
+    acc += sd;
+  }
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kExWarps; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_fit_explicit_finalize(const double* __restrict__ part, int nblocks, Ctrl* ctrl) {
+  if (threadIdx.x != 0) return;
+  double e2 = 0.0;
+  for (int b = 0; b < nblocks; ++b) e2 += part[b];
+  ctrl->rel_err = sqrt(e2 / ctrl->x_norm2);
+  if (!isfinite(e2)) atomicOr(&ctrl->status, kStNonFinite);
+}
+
 }  // namespace
+
+cudaError_t launch_fit_explicit(const void* X, int dtype, int N, const int64_t* dims,
+                                const float* const* F, int R, double* partial, int max_blocks,
+                                Ctrl* ctrl, cudaStream_t st) {
+  const int64_t rows = N == 3 ? dims[0] * dims[1] : dims[0] * dims[1] * dims[2];
+  const int nb = static_cast<int>(std::max<int64_t>(
+      1, std::min<int64_t>((rows + kExWarps - 1) / kExWarps, max_blocks)));
+  const int64_t K = dims[N - 1];
+  const float* F2 = N == 4 ? F[2] : nullptr;
+  if (dtype == NTF_BF16)
+    k_fit_explicit<__nv_bfloat16><<<nb, kExWarps * 32, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(X), N, dims[0], dims[1], N == 4 ? dims[2] : 1, K,
+        F[0], F[1], F2, F[N - 1], R, partial);
+  else
+    k_fit_explicit<float><<<nb, kExWarps * 32, 0, st>>>(
+        static_cast<const float*>(X), N, dims[0], dims[1], N == 4 ? dims[2] : 1, K, F[0], F[1],
+        F2, F[N - 1], R, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fit_explicit_finalize<<<1, 32, 0, st>>>(partial, nb, ctrl);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gram(const float* F, int64_t I, int R, double* G, cudaStream_t st) {
   const int npairs = R * (R + 1) / 2;

@@ -1027,6 +1027,19 @@ ntf_status ntf_fit(ntf_ctx* c, const float* const* F, double* rel_err) {
   return take_status(c);
 }
 
+ntf_status ntf_fit_explicit(ntf_ctx* c, const float* const* F, double* rel_err) {
+  (void)cudaGetLastError();  // a stale non-sticky error is not this call's
+  if (!c || !F || !rel_err) return fail(NTF_ERR_INVALID_ARG, "null argument");
+  for (int m = 0; m < c->N; ++m)
+    if (!F[m] || misaligned(F[m], sizeof(float)))
+      return fail(NTF_ERR_INVALID_ARG, "null or misaligned factor %d", m);
+  NTF_CUDA(ntf::launch_fit_explicit(c->X, c->dtype, c->N, c->dims, F, c->R, c->dpart, 1024,
+                                    c->d_ctrl, c->st));
+  NTF_TRY(read_ctrl(c));
+  *rel_err = c->h_ctrl->rel_err;
+  return take_status(c);
+}
+
 ntf_status ntf_fit_from_mttkrp(ntf_ctx* c, const float* d_M_last, const float* d_F_last,
                                double* rel_err) {
   if (!c || !d_M_last || !d_F_last || !rel_err) return fail(NTF_ERR_INVALID_ARG, "null argument");

@@ -191,6 +191,10 @@ cudaError_t launch_gram(const float* F, int64_t I, int R, double* G, cudaStream_
 cudaError_t launch_system(const double* grams, int N, int mode, int R, int rho_policy,
                           Ctrl* ctrl, double* H, double* L, cudaStream_t st);
 int fit_blocks(int64_t I, int R);
+// relative error by explicit reconstruction into ctrl->rel_err (partial: max_blocks doubles)
+cudaError_t launch_fit_explicit(const void* X, int dtype, int N, const int64_t* dims,
+                                const float* const* F, int R, double* partial, int max_blocks,
+                                Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_fit(const float* M, const float* F, int64_t I, int R, const double* grams,
                        int N, double* partial, Ctrl* ctrl, cudaStream_t st);
 

@@ -13,9 +13,10 @@
 // per-warp counts).
 //
 // MTTKRP: warp c takes the sorted nonzeros [128 c, 128 (c + 1)) (balanced whatever the row
-// lengths), lanes over the rank (r = lane, lane + 32); each nonzero is read as a broadcast and
-// the factor rows it names are gathered (L2-resident at these sizes); products and sums in
-// FP32 registers, row by row.  Rows inside a chunk are written to M; the segments of rows cut
+// lengths); its lanes load 32 nonzeros at a time (coalesced), the warp walks them by broadcast
+// with the factor-row gathers of 8 nonzeros in flight (lanes over the rank: r = lane,
+// lane + 32; the factors are L2-resident at these sizes); products and sums in FP32
+// registers, row by row.  Rows inside a chunk are written to M; the segments of rows cut
 // by a chunk boundary go to per-chunk slots that a fix-up kernel adds in chunk order (no
 // atomics: the result does not depend on scheduling).
 #include <algorithm>
@@ -196,30 +197,19 @@ __device__ __forceinline__ void load_nz(const uint32_t* __restrict__ q, uint32_t
   }
 }
 
-// v prod_{m != n} F_m[i_m, col] for this lane's two columns.
-template <int N>
-__device__ __forceinline__ void nz_terms(const uint32_t (&w)[N + 1], const SpF& f, int R,
-                                         int lane, bool h0, bool h1, float& c0, float& c1) {
-  const float v = __uint_as_float(w[N]);
-  c0 = v;
-  c1 = v;
-#pragma unroll
-  for (int m = 0; m < N - 1; ++m) {
-    const float* fr = f.F[m] + static_cast<int64_t>(w[1 + m]) * R;
-    if (h0) c0 *= __ldg(fr + lane);
-    if (h1) c1 *= __ldg(fr + lane + 32);
-  }
-}
-
 // Chunk kernel: warp c sums the products of the sorted nonzeros [c kChunk, (c + 1) kChunk)
-// row by row.  A row wholly inside the chunk is written to M; the segment of a row that
-// began before the chunk goes to partial[c][0], that of a row continuing past it to
-// partial[c][1] (the fix-up kernel adds the segments of such rows in chunk order).
+// row by row.  Lane l loads nonzero base + l of each group of 32 (one coalesced load for the
+// warp); the warp then walks the group by broadcast, kUnroll nonzeros at a time with their
+// factor-row gathers issued together (lanes over the rank: columns lane, lane + 32).  A row
+// wholly inside the chunk is written to M; the segment of a row that began before the chunk
+// goes to partial[c][0], that of a row continuing past it to partial[c][1] (the fix-up
+// kernel adds the segments of such rows in chunk order).
 template <int N>
 __global__ void __launch_bounds__(256) k_sp_chunks(const uint32_t* __restrict__ packed,
                                                    int64_t nnz, int R, SpF f,
                                                    float* __restrict__ M,
                                                    float* __restrict__ partial) {
+  constexpr int kUnroll = 8;
   const int lane = threadIdx.x & 31;
   const bool h0 = lane < R, h1 = lane + 32 < R;
   const int64_t chunks = (nnz + kChunk - 1) / kChunk;
@@ -236,44 +226,47 @@ __global__ void __launch_bounds__(256) k_sp_chunks(const uint32_t* __restrict__ 
       if (h0) o[lane] = a0;
       if (h1) o[lane + 32] = a1;
     };
-    int64_t p = p0;
-    for (; p + 1 < p1; p += 2) {  // two nonzeros in flight
-      uint32_t wa[N + 1], wb[N + 1];
-      load_nz<N>(packed + p * (N + 1), wa);
-      load_nz<N>(packed + (p + 1) * (N + 1), wb);
-      float c0, c1, d0, d1;
-      nz_terms<N>(wa, f, R, lane, h0, h1, c0, c1);
-      nz_terms<N>(wb, f, R, lane, h0, h1, d0, d1);
-      if (wa[0] != row) {  // warp-uniform
-        flush(false);
-        before = false;
-        row = wa[0];
-        a0 = a1 = 0.0f;
+    for (int64_t base = p0; base < p1; base += 32) {
+      const int cnt = p1 - base < 32 ? static_cast<int>(p1 - base) : 32;
+      uint32_t mine[N + 1];
+      if (lane < cnt) {
+        load_nz<N>(packed + (base + lane) * (N + 1), mine);
+      } else {
+#pragma unroll
+        for (int k = 0; k <= N; ++k) mine[k] = 0;
       }
-      a0 += c0;
-      a1 += c1;
-      if (wb[0] != row) {
-        flush(false);
-        before = false;
-        row = wb[0];
-        a0 = a1 = 0.0f;
+      for (int j0 = 0; j0 < cnt; j0 += kUnroll) {
+        uint32_t key[kUnroll];
+        float t0[kUnroll], t1[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {  // broadcast nonzero j0 + u, gather its rows
+          const int j = j0 + u < cnt ? j0 + u : cnt - 1;
+          key[u] = __shfl_sync(0xffffffffu, mine[0], j);
+          const float v = __uint_as_float(__shfl_sync(0xffffffffu, mine[N], j));
+          float c0 = v, c1 = v;
+#pragma unroll
+          for (int m = 0; m < N - 1; ++m) {
+            const uint32_t im = __shfl_sync(0xffffffffu, mine[1 + m], j);
+            const float* fr = f.F[m] + static_cast<int64_t>(im) * R;
+            if (h0) c0 *= __ldg(fr + lane);
+            if (h1) c1 *= __ldg(fr + lane + 32);
+          }
+          t0[u] = c0;
+          t1[u] = c1;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {  // accumulate in order, row by row
+          if (j0 + u >= cnt) break;           // warp-uniform
+          if (key[u] != row) {
+            flush(false);
+            before = false;
+            row = key[u];
+            a0 = a1 = 0.0f;
+          }
+          a0 += t0[u];
+          a1 += t1[u];
+        }
       }
-      a0 += d0;
-      a1 += d1;
-    }
-    if (p < p1) {
-      uint32_t wa[N + 1];
-      load_nz<N>(packed + p * (N + 1), wa);
-      float c0, c1;
-      nz_terms<N>(wa, f, R, lane, h0, h1, c0, c1);
-      if (wa[0] != row) {
-        flush(false);
-        before = false;
-        row = wa[0];
-        a0 = a1 = 0.0f;
-      }
-      a0 += c0;
-      a1 += c1;
     }
     flush(p1 < nnz && __ldg(packed + p1 * (N + 1)) == row);
   }

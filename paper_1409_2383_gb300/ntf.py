@@ -92,6 +92,7 @@ _SIGS = {
     "ntf_get_rho": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ntf_fit": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
     "ntf_fit_from_mttkrp": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ntf_fit_explicit": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
     "ntf_run": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(RunStats)]),
@@ -338,6 +339,12 @@ class Context:
     def fit(self, F: Sequence[torch.Tensor]) -> float:
         v = ctypes.c_double()
         _check(lib().ntf_fit(self._h, self._factors(F), ctypes.byref(v)))
+        return v.value
+
+    def fit_explicit(self, F: Sequence[torch.Tensor]) -> float:
+        """Relative error by explicit reconstruction (accurate at low noise)."""
+        v = ctypes.c_double()
+        _check(lib().ntf_fit_explicit(self._h, self._factors(F), ctypes.byref(v)))
         return v.value
 
     def fit_from_mttkrp(self, M_last: torch.Tensor, F_last: torch.Tensor) -> float:

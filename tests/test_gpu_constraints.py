@@ -66,14 +66,20 @@ def _updates(ntf, dims, R, L, policy, cons, seed=11):
             got_t = At_d.cpu().numpy()
             assert rel(A_d.cpu().numpy(), A) <= TOL, n
             assert rel(got_t, At) <= TOL, n
-            assert rel(Y_d.cpu().numpy(), Y) <= TOL, n
+            # the dual in units of rho At: inside a box it is zero up to FP32 rounding of x - At
+            dy = np.linalg.norm(Y_d.cpu().numpy().astype(np.float64) - Y)
+            assert dy <= TOL * max(np.linalg.norm(Y), rho * np.linalg.norm(At)), n
             for k in ("primal_res", "dual_res", "norm_A", "norm_At", "norm_Y"):
                 want = getattr(s, k)
                 assert abs(st[k] - want) <= TOL * max(want, s.norm_At), k
             # the update refreshed the stored Gram of this factor from its new auxiliary
-            # (Khatri-Rao source aux): the next modes see that factor
-            F64[n] = got_t.astype(np.float64)
-            ctx.gram(n, At_d)
+            # (Khatri-Rao source aux): the next modes see that factor -- unless it is zero
+            # (c = 0), which would leave them no coefficient matrix: keep the old one then
+            if np.any(got_t):
+                F64[n] = got_t.astype(np.float64)
+                ctx.gram(n, At_d)
+            else:
+                ctx.gram(n, torch.as_tensor(fs[n]).cuda())
             yield got_t, At
 
 

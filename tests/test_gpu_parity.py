@@ -253,6 +253,29 @@ def test_fit(ntf, dims, R):
                             rel_tol=1e-12)
 
 
+@pytest.mark.parametrize("dims,R,snr,bf16", [((30, 40, 50), 4, 15.0, False),
+                                             ((10, 12, 14, 16), 6, 15.0, False),
+                                             ((40, 30, 20), 8, 15.0, True),
+                                             ((60, 50, 40), 10, 70.0, False)])  # low noise
+def test_fit_explicit(ntf, dims, R, snr, bf16):
+    """The fit by explicit reconstruction against the oracle's: equal to 1e-5 relative plus
+    1e-7 absolute at any noise level (at 70 dB the Gram identity of ntf_fit loses accuracy to
+    cancellation; the explicit sum does not)."""
+    fs = synth.factors(dims, R, 2)
+    X = synth.tensor(fs, 2, snr_db=snr)
+    G = [np.clip(F + 1e-4 * np.random.default_rng(3).standard_normal(F.shape), 0, None)
+         .astype(np.float32) for F in fs]
+    Xd = cuda(X)
+    Xref = X.astype(np.float64)
+    if bf16:
+        Xd = ntf.to_bf16(Xd)
+        Xref = Xd.float().cpu().numpy().astype(np.float64)
+    with ntf.Context(Xd, R) as ctx:
+        got = ctx.fit_explicit([cuda(F) for F in G])
+    want = o.rfe(Xref, [F.astype(np.float64) for F in G])
+    assert abs(got - want) <= 1e-5 * want + 1e-7, (got, want)
+
+
 def _run_gpu(ntf, X, init, p, iters, stream=None, paper=False):
     R = init[0].shape[1]
     dims = X.shape

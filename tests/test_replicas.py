@@ -273,7 +273,7 @@ def test_table1_study_loop_on_a_stand_in_context():
             return {"iters": 17 if ok else n_max, "converged": int(ok),
                     "reached_target": 0, "rel_err": 0.0}
 
-        def fit(self, F):
+        def fit_explicit(self, F):
             return float(self.X.abs().mean())
 
     dims, F = (6, 5, 4), 2
@@ -316,7 +316,7 @@ def test_table1_study_lines(capsys):
         def run(self, A, At, Y, n_max, target_rfe=0.0, check_every=1):
             return {"iters": 40, "converged": 1, "reached_target": 0, "rel_err": 0.0}
 
-        def fit(self, F):
+        def fit_explicit(self, F):
             return 0.14
 
     bench.run_study(Args(), open_ctx=Ctx, device="cpu")
