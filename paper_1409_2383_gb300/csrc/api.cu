@@ -526,7 +526,7 @@ ntf_status enqueue_sweep(ntf_ctx* c, float* const* A, float* const* At, float* c
     if (fused) NTF_CUDA(ntf::launch_update_system(un, sa));
     else NTF_CUDA(ntf::launch_update_reduce_system(u, un, sa));
     NTF_TRY(trace_end(c, t, sa));
-    c->launches += fused ? 1 : ntf::update_reduce_system_launches(un);
+    c->launches += 1;
     if (m + 1 < c->N) {
       // C: the next factor's MTTKRP, next to A's reduction (needs factor m updated; the right
       // group needs T_L, enqueued above in this or an earlier iteration of this sweep)

@@ -242,8 +242,6 @@ bool update_fused(const UpdateCall& u);
 // only for !update_fused(u)
 cudaError_t launch_update_reduce_system(const UpdateCall& u, const UpdateCall& next,
                                         cudaStream_t st);
-// kernels launch_update_reduce_system enqueues (2 when next's system is a cluster launch)
-int update_reduce_system_launches(const UpdateCall& next);
 cudaError_t launch_update(const UpdateCall& u, cudaStream_t st);
 
 // mlp.cu: warm-start network (parameter layout, forward, backward, Adam) and its use

@@ -23,8 +23,6 @@
 // table from the new rows.
 #include <cmath>
 
-#include <cooperative_groups.h>
-
 #include "ntf_internal.cuh"
 
 namespace ntf {
@@ -78,8 +76,6 @@ struct UpdArgs {
   int64_t I;
   int N, mode, R, inner, rho_policy, kr_aux, want_fit;
   int fused;            // rows kernel also reduces (last CTA)
-  int no_system;        // reduce-and-system kernel: reduction only (the system is a
-                        // cluster launch of its own)
   double mu, tau_incr, tau_decr;
   float box_lo, box_hi;  // projection of the auxiliary: onto [box_lo, box_hi] ((.)_+: [0, inf))
   int tail_only;         // the inner iterations ran elsewhere: x, At, Y as stored, At before
@@ -477,244 +473,6 @@ template <int S, int NT>
 __device__ __forceinline__ void system_any(const UpdArgs& a) {
   if (a.rho_policy == NTF_RHO_TRACE && a.R >= kLdlMinRank) system_ldl<S, NT>(a);
   else system_body<S, NT>(a);
-}
-
-// The trace-policy factorization of system_ldl spread over a cluster of kClu CTAs: on one SM it
-// is bound by the SM's FP64 instruction rate (reading of the ncu profile: FP64 pipe half busy,
-// the rest latency), so each CTA of the cluster updates a quarter of every step's trailing
-// entries -- warp-sized pieces of the column-packed triangle dealt round-robin to the CTAs,
-// so that every step's suffix stays balanced -- and the owners of the next column write it
-// into every CTA's shared memory (distributed shared memory) before the step's cluster
-// barrier.  After the last step every CTA writes its FP32 L entries into CTA 0, which forms
-// H^{-1} = L^{-T} D^{-1} L^{-1} as system_ldl does.  A pivot that is not a positive normal
-// number is seen by every CTA at the same step (the values are the same everywhere): they
-// all leave the loop there and CTA 0 reports NOT_SPD.
-constexpr int kClu = 4;
-
-template <int S>
-__global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(256)
-    k_system_cluster(UpdArgs a) {
-  namespace cg = cooperative_groups;
-  constexpr int NT = 256;
-  __shared__ double s_col[2][kMaxRank];
-  __shared__ double s_piv[2], s_c[2];
-  __shared__ double s_rho;
-  __shared__ unsigned long long s_gmax[NT / 32], s_gclu[kClu];
-  __shared__ double s_pk[kMaxRank], s_ck[kMaxRank], s_rp[kMaxRank];
-  __shared__ float s_l[kMaxRank * (kMaxRank + 1) / 2];  // CTA 0: L, then W = L^{-1}
-  __shared__ float s_dinv[kMaxRank];
-  if (a.ctrl->stop) return;  // the run has stopped (the same value in every CTA)
-  cg::cluster_group cl = cg::this_cluster();
-  const unsigned rank = cl.block_rank();
-  cl.sync();  // every CTA of the cluster runs before any writes into another's shared memory
-  const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const SysView sv = sys_view(a.sys, a.mode, R);
-  double v[S];
-  int ii[S], jj[S], pp[S];
-  unsigned long long gmax = 0;
-#pragma unroll
-  for (int q = 0; q < S; ++q) {
-    // packed position of slot q: warp-sized pieces dealt round-robin to the CTAs
-    const int p = (((q * (NT / 32) + warp) * kClu + static_cast<int>(rank)) << 5) + lane;
-    pp[q] = p;
-    int j = -1, i = -1;
-    if (p < T) {
-      const float b2 = 2.0f * R + 1.0f;
-      j = static_cast<int>((b2 - sqrtf(b2 * b2 - 8.0f * p)) * 0.5f);
-      j = j < 0 ? 0 : j > R - 1 ? R - 1 : j;
-      while (j > 0 && col_start(j, R) > p) --j;
-      while (j + 1 < R && col_start(j + 1, R) <= p) ++j;
-      i = j + (p - col_start(j, R));
-    }
-    ii[q] = i;
-    jj[q] = j;
-    double h = 0.0;
-    if (p < T) {
-      const int e = i * R + j;
-      const double g0 = a.grams[(0 < a.mode ? 0 : 1) * RR + e];
-      const double g1 = a.grams[(1 < a.mode ? 1 : 2) * RR + e];
-      const double g2 = a.N > 3 ? a.grams[(2 < a.mode ? 2 : 3) * RR + e] : 1.0;
-      h = g0 * g1;
-      if (a.N > 3) h *= g2;
-      const float hf = static_cast<float>(h);
-      sv.h32[i * R + j] = hf;
-      sv.h32[j * R + i] = hf;
-      const unsigned long long bits =
-          static_cast<unsigned long long>(__double_as_longlong(h)) & 0x7FFFFFFFFFFFFFFFull;
-      gmax = bits > gmax ? bits : gmax;
-    }
-    v[q] = h;
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, gmax, off);
-    gmax = o > gmax ? o : gmax;
-  }
-  if (lane == 0) s_gmax[warp] = gmax;
-  if (warp == 0) {  // trace(G), the same sums in every CTA
-    double t = 0.0;
-    for (int j = lane; j < R; j += 32) {
-      double d = 1.0;
-      for (int m = 0; m < a.N; ++m)
-        if (m != a.mode) d *= a.grams[m * RR + j * R + j];
-      t += d;
-    }
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if (lane == 0) s_rho = t / R;
-  }
-  __syncthreads();
-  const double rho = s_rho;
-  if (tid == 0) {  // this CTA's max |G| to CTA 0
-    unsigned long long g = 0;
-    for (int w = 0; w < NT / 32; ++w) g = s_gmax[w] > g ? s_gmax[w] : g;
-    cl.map_shared_rank(s_gclu, 0)[rank] = g;
-  }
-  bool fail = !(rho > 0.0) || !isfinite(rho);
-#pragma unroll
-  for (int q = 0; q < S; ++q) {
-    if (ii[q] >= 0 && ii[q] == jj[q]) v[q] += rho;
-    if (jj[q] == 0) {  // publish column 0 (c = 1) to every CTA
-      for (unsigned r = 0; r < kClu; ++r) {
-        cl.map_shared_rank(&s_col[0][0], r)[ii[q]] = v[q];
-        if (ii[q] == 0) {
-          *cl.map_shared_rank(&s_piv[0], r) = v[q];
-          *cl.map_shared_rank(&s_c[0], r) = 1.0;
-        }
-      }
-    }
-  }
-  cl.sync();
-  for (int k = 0; k < R && !fail; ++k) {
-    const int b = k & 1;
-    const double piv = s_piv[b], c = s_c[b];
-    const int pex = __double2hiint(piv) >> 20;
-    if (static_cast<unsigned>(pex - 1) >= 0x7FEu) {  // the same value in every CTA: uniform
-      fail = true;
-      break;
-    }
-    if (tid == 0) {
-      s_pk[k] = piv;
-      s_ck[k] = c;
-    }
-    const int e = 1023 - pex;
-    const int first = col_start(k + 1, R);
-#pragma unroll
-    for (int q = 0; q < S; ++q) {
-      if (pp[q] < first || ii[q] < 0) continue;
-      const int i = ii[q], j = jj[q];
-      const double nv = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e);
-      v[q] = nv;
-      if (j == k + 1) {  // publish column k + 1 to every CTA for the next step
-        const double cn = i == j ? scale_pow2(c * piv, e) : 0.0;
-        for (unsigned r = 0; r < kClu; ++r) {
-          cl.map_shared_rank(&s_col[b ^ 1][0], r)[i] = nv;
-          if (i == j) {
-            *cl.map_shared_rank(&s_piv[b ^ 1], r) = nv;
-            *cl.map_shared_rank(&s_c[b ^ 1], r) = cn;
-          }
-        }
-      }
-    }
-    cl.sync();  // one cluster barrier per step: the next step reads the other buffers
-  }
-  if (fail) {  // uniform over the cluster
-    if (rank == 0 && tid == 0) {
-      a.ctrl->bad[a.mode] = 1;
-      atomicOr(&a.ctrl->status, kStNotSpd);
-    }
-    return;
-  }
-  // L (unit lower, FP32) into CTA 0, D^{-1} there
-  if (tid < R) {
-    const double rp = recip_newton(s_pk[tid]);
-    s_rp[tid] = rp;
-    if (rank == 0) s_dinv[tid] = static_cast<float>(s_ck[tid] * rp);
-  }
-  __syncthreads();
-  float* l0 = cl.map_shared_rank(s_l, 0);
-#pragma unroll
-  for (int q = 0; q < S; ++q) {
-    const int i = ii[q], j = jj[q];
-    if (i < 0) continue;
-    l0[pp[q]] = i == j ? 1.0f : static_cast<float>(v[q] * s_rp[j]);
-  }
-  cl.sync();  // CTA 0 holds L; the other CTAs are done
-  if (rank != 0) return;
-  if (tid == 0) {
-    unsigned long long g = 0;
-    for (int r = 0; r < kClu; ++r) g = s_gclu[r] > g ? s_gclu[r] : g;
-    a.ctrl->kkt[a.mode][3] = __longlong_as_double(static_cast<long long>(g));  // max |G|
-  }
-  // W = L^{-1}: warp w forms the columns j = w, w + 8, ...; lane l holds rows l, l + 32
-  constexpr int kCols = kMaxRank / (NT / 32);
-  float w0[kCols], w1[kCols];
-#pragma unroll
-  for (int cc = 0; cc < kCols; ++cc) {
-    const int j = warp + (NT / 32) * cc;
-    w0[cc] = lane == j ? 1.0f : 0.0f;
-    w1[cc] = lane + 32 == j ? 1.0f : 0.0f;
-  }
-  for (int k = 0; k + 1 < R; ++k) {
-    const int ck = col_start(k, R) - k;  // s_l[ck + i] = L_ik
-    const float la = lane > k && lane < R ? s_l[ck + lane] : 0.0f;
-    const float lb = lane + 32 > k && lane + 32 < R ? s_l[ck + lane + 32] : 0.0f;
-#pragma unroll
-    for (int cc = 0; cc < kCols; ++cc) {
-      const int j = warp + (NT / 32) * cc;
-      if (j > k || j >= R) continue;  // warp-uniform
-      const float y = __shfl_sync(0xffffffffu, k < 32 ? w0[cc] : w1[cc], k & 31);
-      w0[cc] = fmaf(-la, y, w0[cc]);
-      w1[cc] = fmaf(-lb, y, w1[cc]);
-    }
-  }
-  __syncthreads();  // every warp has read L
-#pragma unroll
-  for (int cc = 0; cc < kCols; ++cc) {
-    const int j = warp + (NT / 32) * cc;
-    if (j >= R) continue;
-    const int cj = col_start(j, R) - j;
-    if (lane >= j && lane < R) s_l[cj + lane] = w0[cc];
-    if (lane + 32 >= j && lane + 32 < R) s_l[cj + lane + 32] = w1[cc];
-  }
-  __syncthreads();
-  // H^{-1}_ij = sum_{k >= i} W_ki W_kj / d_k over the packed entries (i >= j)
-  for (int p = tid; p < T; p += NT) {
-    int j = static_cast<int>((2.0f * R + 1.0f - sqrtf((2.0f * R + 1.0f) * (2.0f * R + 1.0f) - 8.0f * p)) * 0.5f);
-    j = j < 0 ? 0 : j > R - 1 ? R - 1 : j;
-    while (j > 0 && col_start(j, R) > p) --j;
-    while (j + 1 < R && col_start(j + 1, R) <= p) ++j;
-    const int i = j + (p - col_start(j, R));
-    const float* wi = s_l + col_start(i, R) - i;
-    const float* wj = s_l + col_start(j, R) - j;
-    float acc0 = 0.0f, acc1 = 0.0f;
-    int k = i;
-    for (; k + 1 < R; k += 2) {
-      acc0 = fmaf(wi[k] * wj[k], s_dinv[k], acc0);
-      acc1 = fmaf(wi[k + 1] * wj[k + 1], s_dinv[k + 1], acc1);
-    }
-    if (k < R) acc0 = fmaf(wi[k] * wj[k], s_dinv[k], acc0);
-    const float h = acc0 + acc1;
-    sv.hinv32[i * R + j] = h;
-    sv.hinv32[j * R + i] = h;
-  }
-  if (tid == 0) {
-    a.ctrl->bad[a.mode] = 0;
-    a.ctrl->stats[a.mode][5] = rho;
-  }
-}
-
-bool system_on_cluster(const UpdArgs& a) {
-  return a.rho_policy == NTF_RHO_TRACE && a.R >= kLdlMinRank;
-}
-
-cudaError_t launch_system_cluster(const UpdArgs& a, cudaStream_t st) {
-  const int T = a.R * (a.R + 1) / 2;
-  const int per = kClu * 256;
-  if (T <= per) k_system_cluster<1><<<kClu, 256, 0, st>>>(a);
-  else if (T <= 2 * per) k_system_cluster<2><<<kClu, 256, 0, st>>>(a);
-  else if (T <= 3 * per) k_system_cluster<3><<<kClu, 256, 0, st>>>(a);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
 }
 
 __device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
@@ -1279,7 +1037,7 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (!as.no_system) system_any<S, 256>(as);
+  system_any<S, 256>(as);
   if (tid == 0) {
     a.ctrl->sys_count = 0;
     // every CTA of this kernel has read stop by now
@@ -1343,7 +1101,6 @@ UpdArgs make_args(const UpdateCall& u) {
 
 cudaError_t launch_update_system(const UpdateCall& u, cudaStream_t st) {
   const UpdArgs a = make_args(u);
-  if (system_on_cluster(a)) return launch_system_cluster(a, st);
   const int T = u.R * (u.R + 1) / 2;  // packed lower triangle, S entries per thread
   if (T <= 1 * kSysThreads) k_update_system<1><<<1, kSysThreads, 0, st>>>(a);
   else if (T <= 2 * kSysThreads) k_update_system<2><<<1, kSysThreads, 0, st>>>(a);
@@ -1389,23 +1146,9 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int update_reduce_system_launches(const UpdateCall& next) {
-  return system_on_cluster(make_args(next)) ? 2 : 1;
-}
-
 cudaError_t launch_update_reduce_system(const UpdateCall& u, const UpdateCall& next,
                                         cudaStream_t st) {
-  const UpdArgs a = make_args(u);
-  UpdArgs as = make_args(next);
-  if (system_on_cluster(as)) {  // the reduction, then the system as a cluster launch
-    as.no_system = 1;
-    const int gram_ctas = (u.R * (u.R + 1) / 2 + kRedEntries - 1) / kRedEntries;
-    k_update_reduce_system<1><<<gram_ctas + 1, 256, 0, st>>>(a, as, update_blocks(u.I));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    as.no_system = 0;
-    return launch_system_cluster(as, st);
-  }
+  const UpdArgs a = make_args(u), as = make_args(next);
   const int gram_ctas = (u.R * (u.R + 1) / 2 + kRedEntries - 1) / kRedEntries;
   const int T = u.R * (u.R + 1) / 2, nb = update_blocks(u.I);
   const dim3 grid(gram_ctas + 1);
