@@ -5,7 +5,9 @@
 // T_R = X[P_R, Q_R] * KR(factors s_R+1..N) (P_R = I_1..I_{s_R}), the remaining factors from
 // one contraction T_L = X[P_L, Q_L]^T * KR(factors 1..s_L) (s_L <= s_R); s_R = 2, s_L = 1 for
 // N = 3 and s_R = s_L = 2 for N = 4, so that each Khatri-Rao operand of a 3-way tensor is a
-// single factor and no contraction range needs splitting.  Gauss-Seidel order (eq.
+// single factor and no contraction range needs splitting -- except for skewed 3-way shapes
+// whose last extent does not give 16-byte rows (then s_R = 1 and both passes view X as
+// [I_1, I_2 I_3], for the tensor cores).  Gauss-Seidel order (eq.
 // ADMM_NTF_ALS_C) is respected: T_R only involves factors that are not updated before the
 // factors it serves, and T_L only involves factors already updated.  So a sweep reads the
 // tensor twice, whatever N is, and every M_n equals the MTTKRP of its definition up to
@@ -720,7 +722,8 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   c->s_R = 2;
   c->s_L = order == 3 ? 1 : 2;
   // each half is a product of at most two dims (<= 2^60), so nothing here overflows; the
-  // tensor's size is formed only once both halves are known to be below 2^31
+  // tensor's size is formed only once both halves are known to be below 2^31 (checked on both
+  // matrix views, whichever split the passes use)
   c->P_R = c->P_L = c->Q_R = c->Q_L = 1;
   for (int m = 0; m < order; ++m) {
     c->dims[m] = dims[m];
@@ -732,6 +735,19 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
       c->P_L >= (int64_t{1} << 31) || c->Q_L >= (int64_t{1} << 31)) {
     delete c;
     return fail(NTF_ERR_UNSUPPORTED, "tensor halves must each have < 2^31 entries");
+  }
+  // Skewed 3-way shapes (the paper's I x 50 x 50): when the rows of X[I_1 I_2, I_3] are not
+  // 16-byte multiples (TMA needs that pitch) but those of X[I_1, I_2 I_3] are, both passes use
+  // the second view (s_R = 1: factor 1 from X[I_1, I_2 I_3] KR(factors 2, 3), the others from
+  // its transpose as before), so that both contractions run on the tensor cores.
+  if (order == 3 && p->contraction != NTF_CONTRACT_SIMT) {
+    const int64_t es = dtype == NTF_BF16 ? 2 : 4;
+    const bool last_ok = (dims[2] * es) % 16 == 0, pair_ok = (dims[1] * dims[2] * es) % 16 == 0;
+    if (!last_ok && pair_ok) {
+      c->s_R = 1;
+      c->P_R = dims[0];
+      c->Q_R = dims[1] * dims[2];
+    }
   }
   c->numel = c->P_R * c->Q_R;
   int dev = 0;

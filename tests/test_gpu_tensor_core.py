@@ -55,6 +55,8 @@ SHAPES = [
     ((512, 40, 48), 20),     # few output tiles: split contraction range
     ((20, 24, 16, 50), 16),  # 4-way
     ((64, 8, 8, 40), 24),    # 4-way, split contraction range
+    ((300, 50, 50), 10),     # skewed (FP32): 200-byte rows of X[I1 I2, I3]; both passes on X[I1, I2 I3]
+    ((1000, 50, 50), 3),     # the paper's Table 1 shape family, F = 3
 ]
 
 
@@ -86,6 +88,28 @@ def test_tensor_core_agrees_with_fma_path(ntf, storage):
             out[eng] = [ctx.mttkrp(n, Fd).cpu().numpy() for n in range(3)]
     for n in range(3):
         assert rel(out[ntf.NTF_CONTRACT_TENSOR][n], out[ntf.NTF_CONTRACT_SIMT][n]) <= 2 * TOL
+
+
+def test_skewed_run_matches_oracle(ntf):
+    """Ten outer iterations on a 400 x 50 x 50 rank-6 tensor (FP32: both passes on the
+    [400, 2500] view, tensor cores) against the oracle's, L = 5, trace penalty."""
+    import synth
+    dims, R = (400, 50, 50), 6
+    X, _, init = synth.workload(dims, R, seed=2, snr_db=20.0)
+    init = [F.astype(np.float32).astype(np.float64) for F in init]
+    params = o.Params(inner_iters=5, kr_source="aux", rho_policy="trace")
+    st, _, _ = o.factorize(X.astype(np.float64), init, params, 10, stop_on_residuals=False,
+                           record_rfe=False)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0,
+                           contraction=ntf.NTF_CONTRACT_TENSOR)
+    A = [torch.as_tensor(F, dtype=torch.float32).cuda() for F in init]
+    At = [a.clone() for a in A]
+    Y = [torch.zeros_like(a) for a in A]
+    with ntf.Context(torch.as_tensor(X).cuda(), R, p) as ctx:
+        rs = ctx.run(A, At, Y, 10)
+    for n in range(3):
+        assert rel(At[n].cpu().numpy(), st.aux[n]) <= 1e-4, n
+    assert abs(rs["rel_err"] - o.rfe(X.astype(np.float64), st.aux)) <= 1e-4
 
 
 def test_tensor_engine_rejects_unaligned_rows(ntf):
