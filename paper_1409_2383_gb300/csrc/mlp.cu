@@ -6,7 +6,8 @@
 // s = trace(G)/R, z = (G + s I)^{-1} m (the first primal iterate of the row's ADMM from zero),
 // to [x* ; y*/s] (the problem is invariant under (G, m) -> (cG, cm) with x* and z fixed and y*
 // scaled by c).  Layers: R^2+2R -> H -> H -> 2R, exact GELU, BF16 weights in the products
-// with FP32 master copies and FP32 accumulation everywhere.  The first layer is split
+// with FP32 master copies and FP32 accumulation everywhere; the training GEMMs run on the
+// tensor cores (FP32 activations and gradients as two BF16 parts).  The first layer is split
 // W1 = [W1_G | W1_u]: W1_G vec(G/s) is formed once per coefficient matrix and shared by all
 // of its rows; W1_u acts on the per-row input u = [m/s ; z] (2R values).  Training: mean
 // squared error, Adam (Kingma & Ba).  All reductions run in a fixed order.
@@ -19,9 +20,14 @@ namespace ntf {
 namespace {
 
 // ------------------------------------------------------------------------ GEMM
-// C[M, N] = op(A)[M, K] * op(B)[K, N] (+ bias[N]) (+ C if accumulate), FP32 accumulation.
-// TA: A is stored [K, M] (else [M, K]); TB: B is stored [N, K] (else [K, N]).  64 x 64 tiles,
-// 16-deep K slices through shared memory, 4 x 4 outputs per thread.
+// C[M, N] = op(A)[M, K] * op(B)[K, N] (+ bias[N]) (+ C if accumulate), FP32 accumulation on the
+// tensor cores (mma.sync m16n8k16, BF16 operands).  TA: A is stored [K, M] (else [M, K]); TB:
+// B is stored [N, K] (else [K, N]).  FP32 operands are split into BF16 parts v = hi + lo
+// (hi = bf16(v), lo = bf16(v - hi): 16 significant bits; the remainder is below 2^-16 |v|) and
+// the products formed as hi hi + hi lo + lo hi (lo lo, below 2^-16 relative, is dropped); BF16
+// weights are exact and need one part.  64 x 64 output tile per CTA of 8 warps (2 x 4, each
+// 32 x 16 = 2 x 2 MMA tiles), K staged 32 at a time through shared memory (K-contiguous rows,
+// padded so that the fragment loads are free of bank conflicts).
 template <typename T>
 __device__ __forceinline__ float to_f(T v);
 template <>
@@ -29,64 +35,128 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+constexpr int kGT = 64;       // output tile
+constexpr int kGK = 32;       // K per stage
+constexpr int kGLd = kGK + 8; // padded row (bf16 elements)
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
 template <bool TA, bool TB, typename TBt>
 __global__ void __launch_bounds__(256)
     k_gemm(int M, int N, int K, const float* __restrict__ A, int lda, const TBt* __restrict__ B,
            int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias, int accumulate) {
-  __shared__ float As[16][65];
-  __shared__ float Bs[16][65];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
-      const int kk = idx / 64, mm = idx % 64;
-      const int gm = m0 + mm, gk = k0 + kk;
+  constexpr bool kBSplit = sizeof(TBt) == 4;  // FP32 B: two parts
+  __shared__ __align__(16) __nv_bfloat16 Ah[kGT][kGLd], Al[kGT][kGLd];
+  __shared__ __align__(16) __nv_bfloat16 Bh[kGT][kGLd], Bl[kBSplit ? kGT : 1][kGLd];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3;    // warp tile: rows 32 wm .., columns 16 wn ..
+  const int g = lane >> 2, t = lane & 3;
+  const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
+  float acc[2][2][4] = {};
+  for (int k0 = 0; k0 < K; k0 += kGK) {
+    // stage op(A)[m0.., k0..] and op(B)^T[n0.., k0..] as K-contiguous BF16 parts
+    for (int idx = tid; idx < kGT * kGK; idx += 256) {
+      int r, kk;
+      if (TA) {  // A stored [K, M]: consecutive threads along M
+        kk = idx / kGT;
+        r = idx % kGT;
+      } else {   // A stored [M, K]: consecutive threads along K
+        r = idx / kGK;
+        kk = idx % kGK;
+      }
+      const int gm = m0 + r, gk = k0 + kk;
       float a = 0.0f;
-      if (gm < M && gk < K) a = TA ? A[static_cast<int64_t>(gk) * lda + gm] : A[static_cast<int64_t>(gm) * lda + gk];
-      As[kk][mm] = a;
-      const int gn = n0 + mm;
+      if (gm < M && gk < K)
+        a = TA ? A[static_cast<int64_t>(gk) * lda + gm] : A[static_cast<int64_t>(gm) * lda + gk];
+      const __nv_bfloat16 h = __float2bfloat16_rn(a);
+      Ah[r][kk] = h;
+      Al[r][kk] = __float2bfloat16_rn(a - __bfloat162float(h));
+    }
+    for (int idx = tid; idx < kGT * kGK; idx += 256) {
+      int c, kk;
+      if (TB) {  // B stored [N, K]: along K
+        c = idx / kGK;
+        kk = idx % kGK;
+      } else {   // B stored [K, N]: along N
+        kk = idx / kGT;
+        c = idx % kGT;
+      }
+      const int gn = n0 + c, gk = k0 + kk;
       float b = 0.0f;
       if (gn < N && gk < K)
-        b = TB ? to_f<TBt>(B[static_cast<int64_t>(gn) * ldb + gk]) : to_f<TBt>(B[static_cast<int64_t>(gk) * ldb + gn]);
-      Bs[kk][mm] = b;
+        b = TB ? to_f<TBt>(B[static_cast<int64_t>(gn) * ldb + gk])
+               : to_f<TBt>(B[static_cast<int64_t>(gk) * ldb + gn]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(b);
+      Bh[c][kk] = h;
+      if constexpr (kBSplit) Bl[c][kk] = __float2bfloat16_rn(b - __bfloat162float(h));
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
+    for (int ks = 0; ks < kGK; ks += 16) {
+      uint32_t ah[2][4], al[2][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 2; ++i) {
+        const int r = 32 * wm + 16 * i + g;
+        ah[i][0] = ld32(&Ah[r][ks + 2 * t]);
+        ah[i][1] = ld32(&Ah[r + 8][ks + 2 * t]);
+        ah[i][2] = ld32(&Ah[r][ks + 2 * t + 8]);
+        ah[i][3] = ld32(&Ah[r + 8][ks + 2 * t + 8]);
+        al[i][0] = ld32(&Al[r][ks + 2 * t]);
+        al[i][1] = ld32(&Al[r + 8][ks + 2 * t]);
+        al[i][2] = ld32(&Al[r][ks + 2 * t + 8]);
+        al[i][3] = ld32(&Al[r + 8][ks + 2 * t + 8]);
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 2; ++j) {
+        const int c = 16 * wn + 8 * j + g;
+        const uint32_t bh0 = ld32(&Bh[c][ks + 2 * t]), bh1 = ld32(&Bh[c][ks + 2 * t + 8]);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][j], ah[i], bh0, bh1);
+          mma_bf16(acc[i][j], al[i], bh0, bh1);
+        }
+        if constexpr (kBSplit) {
+          const uint32_t bl0 = ld32(&Bl[c][ks + 2 * t]), bl1 = ld32(&Bl[c][ks + 2 * t + 8]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], ah[i], bl0, bl1);
+        }
+      }
     }
     __syncthreads();
   }
+  // accumulator layout: acc[i][j] = rows (g, g + 8) x columns (2t, 2t + 1) of the 16 x 8 tile
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx + 16 * j;
-      if (gn >= N) continue;
-      float v = acc[i][j];
-      if (bias) v += bias[gn];
-      float* c = C + static_cast<int64_t>(gm) * ldc + gn;
-      *c = accumulate ? *c + v : v;
-    }
-  }
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gm = m0 + 32 * wm + 16 * i + g + (q >= 2 ? 8 : 0);
+        const int gn = n0 + 16 * wn + 8 * j + 2 * t + (q & 1);
+        if (gm >= M || gn >= N) continue;
+        float v = acc[i][j][q];
+        if (bias) v += bias[gn];
+        float* cp = C + static_cast<int64_t>(gm) * ldc + gn;
+        *cp = accumulate ? *cp + v : v;
+      }
 }
 
 template <bool TA, bool TB, typename TBt>
 cudaError_t gemm(int M, int N, int K, const float* A, int lda, const TBt* B, int ldb, float* C,
                  int ldc, const float* bias, bool accumulate, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
   k_gemm<TA, TB, TBt><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias,
                                             accumulate ? 1 : 0);
   return cudaGetLastError();

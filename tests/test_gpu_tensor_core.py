@@ -55,9 +55,10 @@ SHAPES = [
     ((512, 40, 48), 20),     # few output tiles: split contraction range
     ((20, 24, 16, 50), 16),  # 4-way
     ((64, 8, 8, 40), 24),    # 4-way, split contraction range
-    ((300, 50, 50), 10),     # skewed (FP32): 200-byte rows of X[I1 I2, I3]; both passes on X[I1, I2 I3]
-    ((1000, 50, 50), 3),     # the paper's Table 1 shape family, F = 3
 ]
+
+# Skewed shapes (FP32 storage): 200-byte rows of X[I1 I2, I3]; both passes on X[I1, I2 I3]
+SKEWED = [((300, 50, 50), 10), ((1000, 50, 50), 3)]
 
 
 @pytest.mark.parametrize("dims,R", SHAPES)
@@ -74,6 +75,20 @@ def test_tensor_core_mttkrp_all_modes(ntf, dims, R, storage):
             assert rel(M, want) <= TOL, (n, rel(M, want))
             again = ctx.mttkrp(n, Fd).cpu().numpy()
             assert np.array_equal(M, again)          # deterministic
+
+
+@pytest.mark.parametrize("dims,R", SKEWED)
+def test_tensor_core_mttkrp_skewed_fp32(ntf, dims, R):
+    test_tensor_core_mttkrp_all_modes(ntf, dims, R, "f32")
+
+
+def test_skewed_bf16_has_no_aligned_view(ntf):
+    """BF16 I x 50 x 50: rows of 100 and 5000 bytes, neither a 16-byte multiple: the tensor
+    engine is refused (the default engine falls back to the FMA kernels)."""
+    X = torch.rand(64, 50, 50, device="cuda").to(torch.bfloat16)
+    with pytest.raises(ntf.NTFError) as ei:
+        ntf.Context(X, 4, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR))
+    assert "UNSUPPORTED" in str(ei.value)
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
