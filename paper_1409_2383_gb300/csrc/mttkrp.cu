@@ -451,6 +451,7 @@ cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R,
 cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float* out,
                               cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  prefer_shared_carveout<k_sum_splits>();
   k_sum_splits<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, st>>>(partial, splits, n, out);
   return cudaGetLastError();
 }
@@ -458,6 +459,7 @@ cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float
 cudaError_t launch_post_fast(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                              float* out, cudaStream_t st) {
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(Ia, 65535));
+  prefer_shared_carveout<k_post_fast>();
   k_post_fast<<<blocks, 256, 0, st>>>(T, Ia, Ib, R, F, out);
   return cudaGetLastError();
 }
@@ -475,6 +477,7 @@ cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, cons
   const int bpb = 256 / R;
   dim3 grid(splits, static_cast<unsigned>((Ib + bpb - 1) / bpb));
   float* dst = splits > 1 ? partial : out;
+  prefer_shared_carveout<k_post_slow>();
   k_post_slow<<<grid, 256, 0, st>>>(T, Ia, Ib, R, F, splits, dst);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
@@ -490,6 +493,7 @@ cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, con
                               float* out, cudaStream_t st) {
   const int Q = R / 4;
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(Ia, 65535));
+  prefer_shared_carveout<k_post_fast4>();
   k_post_fast4<<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float4*>(T), Ia, Ib, Q,
                                           reinterpret_cast<const float4*>(F),
                                           reinterpret_cast<float4*>(out));
@@ -510,6 +514,7 @@ cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, con
                               cudaStream_t st) {
   const int Q = R / 4;
   dim3 grid(static_cast<unsigned>(post_slow4_blocks(Ib)), static_cast<unsigned>(splits));
+  prefer_shared_carveout<k_post_slow4>();
   k_post_slow4<<<grid, kPostBB * Q, 0, st>>>(
       reinterpret_cast<const float4*>(T), Ia, Ib, Q, reinterpret_cast<const float4*>(F), splits,
       reinterpret_cast<float4*>(partial), count, reinterpret_cast<float4*>(out));

@@ -8,11 +8,37 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "ntf.h"
 
 namespace ntf {
 
 constexpr int kMaxOrder = 4;
+
+// The persistent tensor-core contractions hold most of every SM's shared memory and run in
+// the SM configuration with the largest shared-memory carve-out.  A kernel that runs beside
+// them (the factor updates, reductions, coefficient systems and second tree levels of a sweep)
+// asks for that configuration too, so that its CTAs can be placed on an SM next to a
+// contraction CTA instead of waiting for one to exit.  Set once per kernel and device; a
+// refusal only loses the hint, and its error is cleared.
+template <auto kKernel>
+inline void prefer_shared_carveout() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(kKernel),
+                           cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) == cudaSuccess)
+    done.fetch_or(bit, std::memory_order_relaxed);
+  else
+    (void)cudaGetLastError();
+}
 
 // Records the calling thread's last-error message (returned by ntf_last_error) and returns s.
 ntf_status record_error(ntf_status s, const char* fmt, ...);

@@ -221,8 +221,17 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 }
 
 // ---------------------------------------------------------------------------- kernel
+// Register cap: the sweep's other kernels (factor updates, reductions, coefficient systems,
+// second tree levels) run beside the persistent contraction, and one of their 8-warp CTAs
+// shares an SM with a contraction CTA only if two of its warps fit next to the contraction's
+// two warps in a scheduler's 16384 registers.  At N = 64 the uncapped kernel takes 202
+// registers (13312 of a scheduler's registers for two warps) and nothing fits; capped at 168
+// (10752) the reductions and second tree levels (80-84 registers) do, for a few spilled bytes.
+template <int kN>
+constexpr int kUmmaMaxRegs = kN > 32 ? 168 : 144;
+
 template <bool kT, bool kF32, int kN, bool kWRes>
-__global__ void __launch_bounds__(Cfg<kT, kF32, kN, kWRes>::kThreads, 1)
+__global__ void __maxnreg__(kUmmaMaxRegs<kN>)
     k_umma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw,
            Args a) {
   using C = Cfg<kT, kF32, kN, kWRes>;

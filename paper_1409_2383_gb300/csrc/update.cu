@@ -77,6 +77,7 @@ struct UpdArgs {
   int N, mode, R, inner, rho_policy, kr_aux, want_fit;
   int fused;            // rows kernel also reduces (last CTA)
   double mu, tau_incr, tau_decr;
+  double inv_r;          // 1 / R, formed on the host (an FP64 division is slow on this GPU)
   float box_lo, box_hi;  // projection of the auxiliary: onto [box_lo, box_hi] ((.)_+: [0, inf))
   int tail_only;         // the inner iterations ran elsewhere: x, At, Y as stored, At before
   const float* t_before; // the update in t_before (the partial sums and reductions only)
@@ -115,17 +116,31 @@ __device__ __forceinline__ double recip_newton(double p) {
 // u, b_kk and c are published through shared memory (double-buffered, one barrier per step).
 constexpr int kSysThreads = 256;
 
-// x 2^e for the scale factor of a pivot, e in [-1023, 1022]: exact, on the exponent field,
-// when x and the result are normal numbers; otherwise (zero, subnormal, NaN, infinity,
-// leaving the normal range) by scalbn, which keeps zero, NaN and infinity what they are.
+// x 2^e for the scale factor of a pivot, e in [-1023, 1022], on the exponent field alone
+// (integer instructions and selects: on this GPU every FP64 instruction, even one whose
+// predicate is off, holds the small FP64 unit, and a library scaling call on the rare path
+// was issued with every entry).  Exact when x and the result are normal numbers; zero,
+// subnormals, infinities and NaN stay what they are; a result below the normal range becomes
+// a signed zero and one above it a signed infinity (for an SPD matrix scaled by its pivots
+// neither happens short of entries 10^300 apart).
 __device__ __forceinline__ double scale_pow2(double x, int e) {
   const int hi = __double2hiint(x);
+  const int lo = __double2loint(x);
   const int ex = (hi >> 20) & 0x7FF;
-  if (static_cast<unsigned>(ex - 1) < 0x7FEu && static_cast<unsigned>(ex + e - 1) < 0x7FEu)
-    return __hiloint2double(static_cast<int>(static_cast<unsigned>(hi) +
-                                             (static_cast<unsigned>(e) << 20)),
-                            __double2loint(x));
-  return scalbn(x, e);
+  const int ne = ex + e;
+  const int sign = hi & static_cast<int>(0x80000000u);
+  int rhi = static_cast<int>(static_cast<unsigned>(hi) + (static_cast<unsigned>(e) << 20));
+  int rlo = lo;
+  if (ex == 0 || ex == 0x7FF) {  // zero, subnormal, infinity, NaN: unchanged
+    rhi = hi;
+  } else if (ne <= 0) {          // below the normal range: signed zero
+    rhi = sign;
+    rlo = 0;
+  } else if (ne >= 0x7FF) {      // above it: signed infinity
+    rhi = sign | 0x7FF00000;
+    rlo = 0;
+  }
+  return __hiloint2double(rhi, rlo);
 }
 
 template <int S, int NT>
@@ -183,7 +198,7 @@ __device__ void system_body(const UpdArgs& a) {
     double t = 0.0;
 #pragma unroll
     for (int w = 0; w < NT / 32; ++w) t += s_red[w];
-    rho = t / R;
+    rho = t * a.inv_r;
   } else {
     rho = a.ctrl->rho[a.mode];
   }
@@ -285,14 +300,19 @@ __device__ void system_ldl(const UpdArgs& a) {
   // FP64 instructions are scarce on this GPU (a small fraction of the FP32 rate), so the
   // prologue spends them only on the Hadamard products: |h| maxima on the bit patterns (the
   // order of non-negative doubles), the trace by one warp from the diagonals.
+  // Slot q of thread t holds packed entry p = T - 1 - (t + NT q), the packing read backwards:
+  // the trailing part of step k (p >= col_start(k + 1)) is then a prefix of the slots, and a
+  // step runs only the slots that hold some of it (a count that is the same in every thread)
+  // instead of issuing every slot's FP64 instructions under a predicate.
+  const int nslot = (T + NT - 1) / NT;  // slots that hold entries
   double v[S];
   int ii[S], jj[S];
   unsigned long long gmax = 0;
 #pragma unroll
   for (int q = 0; q < S; ++q) {
-    const int p = tid + NT * q;
+    const int p = T - 1 - (tid + NT * q);  // negative: no entry
     int j = -1, i = -1;
-    if (p < T) {  // column j of the packing holds rows j .. R-1: col_start(j) <= p
+    if (p >= 0) {  // column j of the packing holds rows j .. R-1: col_start(j) <= p
       const float b2 = 2.0f * R + 1.0f;
       j = static_cast<int>((b2 - sqrtf(b2 * b2 - 8.0f * p)) * 0.5f);
       j = j < 0 ? 0 : j > R - 1 ? R - 1 : j;
@@ -303,7 +323,7 @@ __device__ void system_ldl(const UpdArgs& a) {
     ii[q] = i;
     jj[q] = j;
     double h = 0.0;
-    if (p < T) {
+    if (p >= 0) {
       // the other factors' Grams: factors o = k (k < mode) or k + 1, k = 0 .. N-2; loads
       // first, then the N - 2 products
       const int e = i * R + j;
@@ -335,7 +355,7 @@ __device__ void system_ldl(const UpdArgs& a) {
       t += d;
     }
     for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if (lane == 0) s_rho = t / R;
+    if (lane == 0) s_rho = t * a.inv_r;
   }
   __syncthreads();
   const double rho = s_rho;
@@ -370,12 +390,17 @@ __device__ void system_ldl(const UpdArgs& a) {
       s_ck[k] = c;
     }
     const int e = 1023 - pex;   // b_kk 2^e in [1, 2)
-    const int first = col_start(k + 1, R);  // the trailing part is p >= first
+    const int first = col_start(k + 1, R);  // the trailing part is p >= first: slots
+    const int nact = (T - first + NT - 1) / NT;  // t + NT q < T - first, the first nact
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-      if (tid + NT * q < first || ii[q] < 0) continue;
+      if (q >= nact) break;                       // the same in every thread
+      if (tid + NT * q >= T - first) continue;  // only in the last of them
       const int i = ii[q], j = jj[q];
-      const double nv = scale_pow2(fma(-s_col[b][i], s_col[b][j], v[q] * piv), e);
+      // b_ij b_kk - b_ik b_kj with the product of the loaded column entries formed here: a
+      // product of register values alone (b_ij b_kk) would be computed ahead of the slot
+      // test for every slot, each one a full FP64 instruction
+      const double nv = scale_pow2(fma(v[q], piv, -(s_col[b][i] * s_col[b][j])), e);
       v[q] = nv;
       if (j == k + 1) {  // publish column k + 1 for the next step
         s_col[b ^ 1][i] = nv;
@@ -403,9 +428,10 @@ __device__ void system_ldl(const UpdArgs& a) {
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < S; ++q) {
+    if (q >= nslot) break;
     const int i = ii[q], j = jj[q];
     if (i < 0) continue;
-    s_l[tid + NT * q] = i == j ? 1.0f : static_cast<float>(v[q] * s_pk[j]);
+    s_l[T - 1 - (tid + NT * q)] = i == j ? 1.0f : static_cast<float>(v[q] * s_pk[j]);
   }
   __syncthreads();
   // W = L^{-1}: warp w forms the columns j = w, w + NT/32, ...; lane l holds rows l, l + 32
@@ -421,10 +447,11 @@ __device__ void system_ldl(const UpdArgs& a) {
     const int ck = col_start(k, R) - k;  // s_l[ck + i] = L_ik
     const float l0 = lane > k && lane < R ? s_l[ck + lane] : 0.0f;
     const float l1 = lane + 32 > k && lane + 32 < R ? s_l[ck + lane + 32] : 0.0f;
+    // every column, without a test: for j > k the entry w_kj is still zero and the update
+    // changes nothing, and columns j >= R are never stored; branch-free, the columns'
+    // shuffles and multiply-adds interleave
 #pragma unroll
     for (int cc = 0; cc < kCols; ++cc) {
-      const int j = warp + (NT / 32) * cc;
-      if (j > k || j >= R) continue;  // w_kj = 0: nothing to eliminate (warp-uniform)
       const float y = __shfl_sync(0xffffffffu, k < 32 ? w0[cc] : w1[cc], k & 31);
       w0[cc] = fmaf(-l0, y, w0[cc]);
       w1[cc] = fmaf(-l1, y, w1[cc]);
@@ -443,6 +470,7 @@ __device__ void system_ldl(const UpdArgs& a) {
   // H^{-1}_ij = sum_{k >= i} W_ki W_kj / d_k (i >= j)
 #pragma unroll
   for (int q = 0; q < S; ++q) {
+    if (q >= nslot) break;
     const int i = ii[q], j = jj[q];
     if (i < 0) continue;
     const float* wi = s_l + col_start(i, R) - i;
@@ -466,8 +494,9 @@ __device__ void system_ldl(const UpdArgs& a) {
 
 // The coefficient system of a factor update: the FP64 factorization above under the trace
 // policy for R >= kLdlMinRank, the FP64 sweep operator otherwise (under the other policies the
-// rows then run in FP64 from its FP64 inverse).  Measured per launch on GB300: R = 20: sweep
-// 11.9 us, LDL^T 18.2 us; R = 32: 70 / 46 us; R = 50: 158 / 99 us; R = 64: 159 us (LDL^T).
+// rows then run in FP64 from its FP64 inverse).  Measured per launch on GB300 (alone): sweep
+// operator R = 20: 13.5 us, R = 32: 34 us, R = 40: 48 us; LDL^T R = 32: 26 us, R = 50: 51 us,
+// R = 64: 83 us.
 constexpr int kLdlMinRank = 28;
 template <int S, int NT>
 __device__ __forceinline__ void system_any(const UpdArgs& a) {
@@ -557,8 +586,17 @@ __global__ void __launch_bounds__(kSysThreads) k_update_system(UpdArgs a) {
 // element j and holds column j of H^{-1} (= row j: symmetric) in registers for the whole
 // update; x = H^{-1} v takes v_k from lane k by shuffles.  kR = R rounded up to a multiple of
 // 4 fixes the loop lengths at compile time (the padding lanes and columns hold zeros).
+// Register cap of the FP32 rows kernel: the factor updates run while a persistent
+// contraction CTA (6 warps, 144 registers each at rank <= 32) holds each SM, and a rows CTA
+// (8 warps, two on each of the SM's four schedulers) shares an SM with it only if two of its
+// warps fit in what the contraction's two warps leave of a scheduler's 16384 registers:
+// 2 x 32 x 112 + 2 x 32 x 144 = 16384.  (The FP64 rows of the other penalty policies spill at
+// that cap and keep their registers.)
+template <typename Real>
+constexpr int kRows32MaxRegs = sizeof(Real) == 4 ? 112 : 168;
+
 template <typename Real, int kR>
-__global__ void __launch_bounds__(kRowThreads, 1) k_update_rows32(UpdArgs a) {
+__global__ void __maxnreg__(kRows32MaxRegs<Real>) k_update_rows32(UpdArgs a) {
   __shared__ double frow[kRowWarps][32];  // FP64 copies: one conversion per element
   __shared__ double red[kRowWarps][kScal];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -802,42 +840,69 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(UpdArgs a) {
 
 // Residual norms, penalty rule (Sec. IV-D) and, for the last factor of a sweep, the fit,
 // from the fixed-order sums of the scalar partials (one thread).
-__device__ void update_finalize(const UpdArgs& a, const double* sum) {
+// Called by one whole warp (lane-parallel arithmetic; lane 0 writes).  FP64 division and
+// square root are long instruction sequences on this GPU, so the quotients of the update's
+// measures are formed in one division (lane q: quotient q) and the roots in one square root
+// (lane q: root q) instead of one after the other.
+__device__ void update_finalize(const UpdArgs& a, const double* sum, int lane) {
   Ctrl* c = a.ctrl;
   const double rho = c->stats[a.mode][5];
-  const double P = sqrt(sum[0]), D = rho * sqrt(sum[1]);
+  // KKT measures of the factor's row problems at At (eq. KKT_NTF), scaled as
+  // s_x = max |At|, s_g = max |G| s_x + max |M|
+  const double sx = fmax(sum[9], 1e-30);
+  const double sg = c->kkt[a.mode][3] * sx + sum[10];
+  const double e2 = a.want_fit ? c->x_norm2 - 2.0 * sum[5] + sum[6] : 0.0;
+  // quotients: lane 0 the relative squared error, 1 the negativity, 2 the dual infeasibility,
+  // 3 the complementarity
+  double num = 0.0, den = 1.0;
+  if (lane == 0 && a.want_fit) {
+    num = fmax(e2, 0.0);
+    den = c->x_norm2;
+  } else if (lane == 1) {
+    num = fmax(0.0, sum[11]);
+    den = sx;
+  } else if (lane == 2 && sg > 0.0) {
+    num = fmax(0.0, sum[8]);
+    den = sg;
+  } else if (lane == 3 && sg > 0.0) {
+    num = sum[7];
+    den = sg * sx * static_cast<double>(a.I) * a.R;
+  }
+  const double quo = num / den;
+  // roots: lanes 0-4 the norms of sum[0..4], lane 5 the relative error
+  const double q0 = __shfl_sync(0xffffffffu, quo, 0);
+  const double rad = lane < 5 ? sum[lane < 5 ? lane : 0] : lane == 5 ? q0 : 0.0;
+  const double root = sqrt(rad);
+  double q[4], r[6];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q[k] = __shfl_sync(0xffffffffu, quo, k);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r[k] = __shfl_sync(0xffffffffu, root, k);
+  if (lane != 0) return;
+  const double P = r[0], D = rho * r[1];
   c->stats[a.mode][0] = P;
   c->stats[a.mode][1] = D;
-  c->stats[a.mode][2] = sqrt(sum[2]);
-  c->stats[a.mode][3] = sqrt(sum[3]);
-  c->stats[a.mode][4] = sqrt(sum[4]);
+  c->stats[a.mode][2] = r[2];
+  c->stats[a.mode][3] = r[3];
+  c->stats[a.mode][4] = r[4];
   bool finite = true;
-  for (int q = 0; q < 5; ++q) finite = finite && isfinite(sum[q]);
+  for (int k = 0; k < 5; ++k) finite = finite && isfinite(sum[k]);
   if (a.rho_policy == NTF_RHO_ADAPTIVE) {
     // eq. (varying_penalty_rule); the cases exclude each other because mu > 1
-    double r = rho;
-    if (P > a.mu * D) r = a.tau_incr * rho;
-    else if (D > a.mu * P) r = rho / a.tau_decr;
-    c->rho[a.mode] = r;
+    double rr = rho;
+    if (P > a.mu * D) rr = a.tau_incr * rho;
+    else if (D > a.mu * P) rr = rho / a.tau_decr;
+    c->rho[a.mode] = rr;
   } else if (a.rho_policy == NTF_RHO_TRACE) {
     c->rho[a.mode] = rho;
   }
-  {
-    // KKT measures of the factor's row problems at At (eq. KKT_NTF), scaled as
-    // s_x = max |At|, s_g = max |G| s_x + max |M|
-    const double sx = fmax(sum[9], 1e-30);
-    const double sg = c->kkt[a.mode][3] * sx + sum[10];
-    const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
-    c->kkt[a.mode][0] = fmax(0.0, sum[11]) / sx;
-    c->kkt[a.mode][1] = fmax(0.0, sum[8]) * inv;
-    c->kkt[a.mode][2] = sum[7] * inv / (sx * static_cast<double>(a.I) * a.R);
-  }
+  c->kkt[a.mode][0] = q[1];
+  c->kkt[a.mode][1] = q[2];
+  c->kkt[a.mode][2] = q[3];
   if (a.want_fit) {
-    const double inner = sum[5], quad = sum[6];
-    const double e2 = c->x_norm2 - 2.0 * inner + quad;
-    c->fit_inner = inner;
-    c->fit_gram = quad;
-    c->rel_err = sqrt(fmax(e2, 0.0) / c->x_norm2);
+    c->fit_inner = sum[5];
+    c->fit_gram = sum[6];
+    c->rel_err = r[5];
     finite = finite && isfinite(e2);
   }
   if (!finite) atomicOr(&c->status, kStNonFinite);
@@ -979,7 +1044,7 @@ __device__ void update_reduce_cta(const UpdArgs& a, int nblocks) {
     if (lane == 0) s_sum[q] = v;
   }
   __syncthreads();
-  if (tid == 0) update_finalize(a, s_sum);
+  if (warp == 0) update_finalize(a, s_sum, lane);
 }
 
 // Separate reduction: CTAs 0..gridDim.x-2 sum kRedEntries packed Gram entries each (8 lanes
@@ -1000,7 +1065,7 @@ __global__ void __launch_bounds__(256) k_update_reduce(UpdArgs a, int nblocks) {
     if (lane == 0) s_sum[q] = v;
   }
   __syncthreads();
-  if (tid == 0) update_finalize(a, s_sum);
+  if (warp == 0) update_finalize(a, s_sum, lane);
 }
 
 // The reduction of factor m's update (as k_update_reduce) followed, in the last of its CTAs
@@ -1028,7 +1093,7 @@ __global__ void __launch_bounds__(256) k_update_reduce_system(UpdArgs a, UpdArgs
         if (lane == 0) s_sum[q] = v;
       }
       __syncthreads();
-      if (tid == 0) update_finalize(a, s_sum);
+      if (warp == 0) update_finalize(a, s_sum, lane);
     }
   }
   __threadfence();
@@ -1095,6 +1160,7 @@ UpdArgs make_args(const UpdateCall& u) {
   a.mu = u.mu;
   a.tau_incr = u.tau_incr;
   a.tau_decr = u.tau_decr;
+  a.inv_r = 1.0 / u.R;
   return a;
 }
 }  // namespace
@@ -1102,11 +1168,17 @@ UpdArgs make_args(const UpdateCall& u) {
 cudaError_t launch_update_system(const UpdateCall& u, cudaStream_t st) {
   const UpdArgs a = make_args(u);
   const int T = u.R * (u.R + 1) / 2;  // packed lower triangle, S entries per thread
-  if (T <= 1 * kSysThreads) k_update_system<1><<<1, kSysThreads, 0, st>>>(a);
-  else if (T <= 2 * kSysThreads) k_update_system<2><<<1, kSysThreads, 0, st>>>(a);
-  else if (T <= 4 * kSysThreads) k_update_system<4><<<1, kSysThreads, 0, st>>>(a);
-  else if (T <= 9 * kSysThreads) k_update_system<9><<<1, kSysThreads, 0, st>>>(a);
+#define NTF_SYS(s)                                    \
+  {                                                   \
+    prefer_shared_carveout<k_update_system<s>>();     \
+    k_update_system<s><<<1, kSysThreads, 0, st>>>(a); \
+  }
+  if (T <= 1 * kSysThreads) NTF_SYS(1)
+  else if (T <= 2 * kSysThreads) NTF_SYS(2)
+  else if (T <= 4 * kSysThreads) NTF_SYS(4)
+  else if (T <= 9 * kSysThreads) NTF_SYS(9)
   else return cudaErrorInvalidValue;
+#undef NTF_SYS
   return cudaGetLastError();
 }
 
@@ -1119,8 +1191,13 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
     switch ((u.R + 3) / 4) {
 #define NTF_ROWS32(q)                                                       \
   case q:                                                                   \
-    if (fp32) k_update_rows32<float, 4 * q><<<nb, kRowThreads, 0, st>>>(a); \
-    else k_update_rows32<double, 4 * q><<<nb, kRowThreads, 0, st>>>(a);     \
+    if (fp32) {                                                             \
+      prefer_shared_carveout<k_update_rows32<float, 4 * q>>();              \
+      k_update_rows32<float, 4 * q><<<nb, kRowThreads, 0, st>>>(a);         \
+    } else {                                                                \
+      prefer_shared_carveout<k_update_rows32<double, 4 * q>>();             \
+      k_update_rows32<double, 4 * q><<<nb, kRowThreads, 0, st>>>(a);        \
+    }                                                                       \
     break;
       NTF_ROWS32(1) NTF_ROWS32(2) NTF_ROWS32(3) NTF_ROWS32(4)
       NTF_ROWS32(5) NTF_ROWS32(6) NTF_ROWS32(7) NTF_ROWS32(8)
@@ -1134,10 +1211,12 @@ cudaError_t launch_update_rows(const UpdateCall& u, cudaStream_t st) {
                           kRowWarps * 64 * 4;
   cudaError_t e;
   if (fp32) {
+    prefer_shared_carveout<k_update_rows<float>>();
     e = cudaFuncSetAttribute(k_update_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(row_smem));
     if (e == cudaSuccess) k_update_rows<float><<<nb, kRowThreads, row_smem, st>>>(a);
   } else {
+    prefer_shared_carveout<k_update_rows<double>>();
     e = cudaFuncSetAttribute(k_update_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(row_smem));
     if (e == cudaSuccess) k_update_rows<double><<<nb, kRowThreads, row_smem, st>>>(a);
@@ -1152,11 +1231,17 @@ cudaError_t launch_update_reduce_system(const UpdateCall& u, const UpdateCall& n
   const int gram_ctas = (u.R * (u.R + 1) / 2 + kRedEntries - 1) / kRedEntries;
   const int T = u.R * (u.R + 1) / 2, nb = update_blocks(u.I);
   const dim3 grid(gram_ctas + 1);
-  if (T <= 256) k_update_reduce_system<1><<<grid, 256, 0, st>>>(a, as, nb);
-  else if (T <= 512) k_update_reduce_system<2><<<grid, 256, 0, st>>>(a, as, nb);
-  else if (T <= 1024) k_update_reduce_system<4><<<grid, 256, 0, st>>>(a, as, nb);
-  else if (T <= 2304) k_update_reduce_system<9><<<grid, 256, 0, st>>>(a, as, nb);
+#define NTF_RSYS(s)                                              \
+  {                                                              \
+    prefer_shared_carveout<k_update_reduce_system<s>>();         \
+    k_update_reduce_system<s><<<grid, 256, 0, st>>>(a, as, nb);  \
+  }
+  if (T <= 256) NTF_RSYS(1)
+  else if (T <= 512) NTF_RSYS(2)
+  else if (T <= 1024) NTF_RSYS(4)
+  else if (T <= 2304) NTF_RSYS(9)
   else return cudaErrorInvalidValue;
+#undef NTF_RSYS
   return cudaGetLastError();
 }
 
@@ -1168,6 +1253,7 @@ cudaError_t launch_update_reduce(const UpdateCall& u, cudaStream_t st) {
   if (update_fused(u)) return cudaSuccess;  // done by the rows kernel
   const UpdArgs a = make_args(u);
   const int gram_ctas = (u.R * (u.R + 1) / 2 + kRedEntries - 1) / kRedEntries;
+  prefer_shared_carveout<k_update_reduce>();
   k_update_reduce<<<gram_ctas + 1, 256, 0, st>>>(a, update_blocks(u.I));
   return cudaGetLastError();
 }

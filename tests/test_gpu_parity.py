@@ -537,3 +537,38 @@ def test_run_stops_at_the_kkt_tolerance(ntf, check_every):
             A3, At3, Y3 = fresh()
             rp = ctx.run(A3, At3, Y3, rs["iters"] - check_every, check_every=1)
             assert not (rp["kkt_dual"] <= tol_d and rp["kkt_comp"] <= tol_c)
+
+
+@pytest.mark.parametrize("R,scale", [(8, 1e-6), (24, 1e-7), (40, 1e-6)])
+def test_ill_conditioned_update_matches_the_cholesky_solve(ntf, R, scale):
+    """Small penalty, nearly collinear factors: cond(G + rho I) from 7e5 to 1.6e7 under the fixed
+    policy, where the rows run in FP64 against the FP64 sweep-operator inverse.  One update
+    (L = 3) against the oracle's Cholesky solve; the tolerance grows with the condition
+    number, cond * 2^-52 on top of the FP32 storage of the result (1e-5)."""
+    import synth
+    dims = (60, 50, 40)
+    fs = synth.factors(dims, R, seed=R, structure="collinear", congruence=0.99999)
+    fs = [F.astype(np.float32) for F in fs]
+    F64 = [F.astype(np.float64) for F in fs]
+    rng = np.random.default_rng(R)
+    X = rng.random(dims).astype(np.float32)
+    p = ntf.default_params(inner_iters=3, rho_policy=ntf.NTF_RHO_FIXED, kr_source=ntf.NTF_KR_AUX)
+    with ntf.Context(cuda(X), R, p) as ctx:
+        for m in range(3):
+            ctx.gram(m, cuda(fs[m]))
+        n = 0
+        G = o.coeff_matrix(F64, n)
+        rho = scale * o.rho_trace(G)
+        cond = np.linalg.cond(G + rho * np.eye(R))
+        assert cond > 1e5
+        ctx.set_rho(n, rho)
+        M = o.mttkrp(X.astype(np.float64), F64, n).astype(np.float32)
+        At0 = np.maximum(rng.standard_normal((dims[n], R)), 0).astype(np.float32)
+        Y0 = np.zeros((dims[n], R), np.float32)
+        A_d, At_d, Y_d = torch.empty(dims[n], R, device="cuda"), cuda(At0), cuda(Y0)
+        ctx.admm_update(n, cuda(M), A_d, At_d, Y_d)
+        A, At, Y, _ = o.admm_factor_update(M.astype(np.float64), G, At0.astype(np.float64),
+                                           Y0.astype(np.float64), rho, 3)
+        tol = TOL + cond * 2.0 ** -52
+        assert rel(host(A_d), A) <= tol, (rel(host(A_d), A), cond)
+        assert rel(host(At_d), At) <= tol, (rel(host(At_d), At), cond)
