@@ -285,14 +285,24 @@ __device__ void system_body(const UpdArgs& a) {
 // written (the rows kernel of this policy reads nothing else).
 __device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
 
+// Largest rank whose packed lower triangle fits in n entries (at most kMaxRank).
+__host__ __device__ constexpr int ldl_max_rank(int n) {
+  int r = 0;
+  while (r < kMaxRank && (r + 1) * (r + 2) / 2 <= n) ++r;
+  return r;
+}
+
 template <int S, int NT>
 __device__ void system_ldl(const UpdArgs& a) {
+  constexpr int kRmax = ldl_max_rank(S * NT);
+  constexpr int kVBuf = kRmax * (kRmax | 1);  // V with an odd row stride (R | 1 <= kRmax | 1)
+  constexpr int kBuf = S * NT > kVBuf ? S * NT : kVBuf;
   __shared__ double s_col[2][kMaxRank];  // column k + 1 of B, published during step k
   __shared__ double s_piv[2], s_c[2];
   __shared__ double s_rho;
   __shared__ unsigned long long s_gmax[NT / 32];
   __shared__ double s_pk[kMaxRank], s_ck[kMaxRank];  // b_kk and c of every step
-  __shared__ float s_l[S * NT];                       // L, then W = L^{-1} (packed by column)
+  __shared__ float s_l[kBuf];  // L (packed by column), then V = D^{-1/2} L^{-1} (by rows)
   __shared__ float s_dinv[kMaxRank];
   const int R = a.R, RR = R * R, T = R * (R + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -458,30 +468,33 @@ __device__ void system_ldl(const UpdArgs& a) {
     }
   }
   __syncthreads();  // every warp has read L
+  // V = D^{-1/2} W by rows (row k at k vs; vs = R | 1 is odd, so a warp's column store and
+  // its reads of a row's consecutive entries are free of bank conflicts); H^{-1} = V^T V
+  const int vs = R | 1;
+  const float d0 = lane < R ? sqrtf(s_dinv[lane]) : 0.0f;
+  const float d1 = lane + 32 < R ? sqrtf(s_dinv[lane + 32]) : 0.0f;
 #pragma unroll
   for (int cc = 0; cc < kCols; ++cc) {
     const int j = warp + (NT / 32) * cc;
     if (j >= R) continue;
-    const int cj = col_start(j, R) - j;  // s_l[cj + i] = W_ij, i >= j
-    if (lane >= j && lane < R) s_l[cj + lane] = w0[cc];
-    if (lane + 32 >= j && lane + 32 < R) s_l[cj + lane + 32] = w1[cc];
+    if (lane < R) s_l[lane * vs + j] = w0[cc] * d0;
+    if (lane + 32 < R) s_l[(lane + 32) * vs + j] = w1[cc] * d1;
   }
   __syncthreads();
-  // H^{-1}_ij = sum_{k >= i} W_ki W_kj / d_k (i >= j)
+  // H^{-1}_ij = sum_{k >= i} V_ki V_kj (i >= j; V_ki = 0 for k < i): the lanes of a warp hold
+  // consecutive i of one column j, so V_ki is a contiguous read and V_kj a broadcast
 #pragma unroll
   for (int q = 0; q < S; ++q) {
     if (q >= nslot) break;
     const int i = ii[q], j = jj[q];
     if (i < 0) continue;
-    const float* wi = s_l + col_start(i, R) - i;
-    const float* wj = s_l + col_start(j, R) - j;
     float acc0 = 0.0f, acc1 = 0.0f;
     int k = i;
     for (; k + 1 < R; k += 2) {
-      acc0 = fmaf(wi[k] * wj[k], s_dinv[k], acc0);
-      acc1 = fmaf(wi[k + 1] * wj[k + 1], s_dinv[k + 1], acc1);
+      acc0 = fmaf(s_l[k * vs + i], s_l[k * vs + j], acc0);
+      acc1 = fmaf(s_l[(k + 1) * vs + i], s_l[(k + 1) * vs + j], acc1);
     }
-    if (k < R) acc0 = fmaf(wi[k] * wj[k], s_dinv[k], acc0);
+    if (k < R) acc0 = fmaf(s_l[k * vs + i], s_l[k * vs + j], acc0);
     const float h = acc0 + acc1;
     sv.hinv32[i * R + j] = h;
     sv.hinv32[j * R + i] = h;
@@ -500,8 +513,13 @@ __device__ void system_ldl(const UpdArgs& a) {
 constexpr int kLdlMinRank = 28;
 template <int S, int NT>
 __device__ __forceinline__ void system_any(const UpdArgs& a) {
-  if (a.rho_policy == NTF_RHO_TRACE && a.R >= kLdlMinRank) system_ldl<S, NT>(a);
-  else system_body<S, NT>(a);
+  if constexpr (S >= 2) {  // R >= kLdlMinRank takes at least two slots per thread
+    if (a.rho_policy == NTF_RHO_TRACE && a.R >= kLdlMinRank) {
+      system_ldl<S, NT>(a);
+      return;
+    }
+  }
+  system_body<S, NT>(a);
 }
 
 __device__ void update_reduce_cta(const UpdArgs& a, int nblocks);
