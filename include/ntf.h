@@ -97,6 +97,13 @@ typedef struct {
    * ntf_update_stats for the measures). */
   double kkt_dual_tol;
   double kkt_comp_tol;
+  /* Factor 0's second tree level (Sec. IV-A: the MTTKRP finished from the shared
+   * contraction) formed in that contraction's epilogue instead of a separate pass over its
+   * [I_1 I_2, R] intermediate; applies to the tensor-core engine with one contraction chunk,
+   * R <= 32 and I_2 >= 32.  0 (default): where it applies and the intermediate is at least
+   * half the L2 size; 1: wherever it applies; -1: never.  Results equal to rounding. */
+  int fuse_level;
+  int reserved;      /* 0 */
 } ntf_params;
 
 /* Per-factor residuals of one update (Sec. IV-C), all Frobenius norms, and the KKT measures

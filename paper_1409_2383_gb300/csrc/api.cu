@@ -47,6 +47,11 @@ struct ntf_ctx {
   void* arena[2] = {nullptr, nullptr};
   float* partial = nullptr;      // partial sums of the first contraction and of the posts
   float* partial_b = nullptr;    // partial sums of the second contraction (its own stream)
+  // factor 0's second tree level formed in the first contraction's epilogue (tensor cores,
+  // one K-chunk, N <= 32, s_R >= 2, I_1 >= 32): per-32-row-group sums [ceil(P_R / 32), 2, R],
+  // and whether the last enqueued first contraction wrote them for the next factor-0 level
+  float* fpart = nullptr;
+  bool fpart_ready = false;
   float* TR = nullptr;           // [P_R, R]
   float* TL = nullptr;           // [Q_L, R]
   float* W = nullptr;            // Khatri-Rao table of the first contraction [K_pad, RP]
@@ -170,6 +175,8 @@ ntf_status check_params(const ntf_params* p) {
     return fail(NTF_ERR_INVALID_ARG, "negative stopping tolerance");
   if (p->contraction < NTF_CONTRACT_AUTO || p->contraction > NTF_CONTRACT_SIMT)
     return fail(NTF_ERR_INVALID_ARG, "unknown contraction engine %d", p->contraction);
+  if (p->fuse_level < -1 || p->fuse_level > 1)
+    return fail(NTF_ERR_INVALID_ARG, "fuse_level must be -1, 0 or 1, not %d", p->fuse_level);
   if (!(p->kkt_dual_tol >= 0.0) || !(p->kkt_comp_tol >= 0.0))
     return fail(NTF_ERR_INVALID_ARG, "negative KKT tolerance");
   return NTF_OK;
@@ -245,8 +252,9 @@ ntf_status trace_end(ntf_ctx* c, int i, cudaStream_t st) {
 // T_R[P_R, R] = X[P_R, Q_R] * KR(factors s_R..N-1), on stream st (table_ready: the split
 // table was written by the last factor's rows kernel)
 ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStream_t st,
-                          bool table_ready = false) {
+                          bool table_ready = false, bool fuse0 = false) {
   const Group g = make_group(c, c->s_R, c->N - c->s_R, F);
+  c->fpart_ready = false;
   if (c->un.on) {
     if (!table_ready) {
       NTF_CUDA(ntf::launch_kr_split(g, c->un, c->R, c->Wu, st));
@@ -255,8 +263,12 @@ ntf_status contract_right(ntf_ctx* c, const float* const* F, float* dst, cudaStr
     const int chunks = c->un.args.chunks;
     float* out = chunks > 1 ? c->partial : dst;
     NTF_TRY(prof_mark(c, 0, 0, st));
+    // factor 0's second tree level in the epilogue when factor 0's MTTKRP follows
+    const bool fz = fuse0 && c->fpart != nullptr;
     NTF_CUDA(ntf::launch_umma(c->un, out, &c->d_ctrl->status, c->umma_sched, &c->d_ctrl->stop,
-                              st));
+                              st, fz ? F[1] : nullptr, fz ? c->dims[1] : 0,
+                              fz ? c->fpart : nullptr));
+    c->fpart_ready = fz;
     NTF_TRY(prof_mark(c, 0, 1, st));
     c->launches += 1;
     if (chunks > 1) {
@@ -347,7 +359,12 @@ ntf_status finish_mode(ntf_ctx* c, int mode, const float* T, const float* const*
     return NTF_OK;
   }
   const int64_t Ia = c->dims[first], Ib = c->dims[first + 1];
-  if (mode == first) {
+  if (mode == first && left && c->fpart_ready) {
+    // the contraction's epilogue formed the group sums: only their sum per row remains
+    NTF_CUDA(ntf::launch_post_part(c->fpart, Ia, Ib, c->R, M, st));
+    c->fpart_ready = false;
+    c->launches += 1;
+  } else if (mode == first) {
     if (ntf::post4_ok(c->R, T, F[first + 1], M))
       NTF_CUDA(ntf::launch_post_fast4(T, Ia, Ib, c->R, F[first + 1], M, st));
     else
@@ -437,7 +454,7 @@ ntf_status enqueue_lead(ntf_ctx* c, const float* const* src, cudaStream_t st, in
                         bool table_ready = false) {
   const float* T = c->s_R == 1 ? c->Mbuf : c->TR;
   int t = trace_begin(c, "contract_right", 0, sid, st);
-  NTF_TRY(contract_right(c, src, const_cast<float*>(T), st, table_ready));
+  NTF_TRY(contract_right(c, src, const_cast<float*>(T), st, table_ready, true));
   NTF_TRY(trace_end(c, t, st));
   t = trace_begin(c, "mttkrp_level2", 0, sid, st);
   NTF_TRY(finish_mode(c, 0, T, src, c->Mbuf, st));
@@ -675,6 +692,8 @@ void ntf_default_params(ntf_params* p, int paper_mode) {
   p->contraction = NTF_CONTRACT_AUTO;
   p->kkt_dual_tol = 0.0;
   p->kkt_comp_tol = 0.0;
+  p->fuse_level = 0;
+  p->reserved = 0;
 }
 
 const char* ntf_status_string(ntf_status s) {
@@ -753,6 +772,8 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  int l2_bytes = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, dev);
   if (e != cudaSuccess) {
     delete c;
     return fail(NTF_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
@@ -870,10 +891,21 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   // arena 1: the partial sums, sized by the plans
   Carver a1;
   const size_t oP = a1.take(part * sizeof(float)), oPb = a1.take(part_b * sizeof(float));
+  // Factor 0's second tree level in the first contraction's epilogue: worth it when T_R is
+  // not served from L2 by the separate level (at least half the L2: reading it back then costs
+  // a DRAM pass, and its write-back competes) and N <= 32 (at N = 64 the epilogue's extra
+  // registers slow the contraction more than the level costs).
+  const bool fuse_fits = c->un.on && c->un.args.chunks == 1 && c->un.N <= 32 && c->s_R >= 2 &&
+                         dims[1] >= 32;
+  const bool fuse = fuse_fits && (p->fuse_level == 1 ||
+                                  (p->fuse_level == 0 && static_cast<double>(c->P_R) * R *
+                                                                 sizeof(float) >= 0.5 * l2_bytes));
+  const size_t oFz = a1.take(fuse ? ((c->P_R + 31) / 32) * 2 * R * sizeof(float) : 0);
   if (e == cudaSuccess) e = cudaMalloc(&c->arena[1], a1.off);
   if (e == cudaSuccess) {
     c->partial = reinterpret_cast<float*>(static_cast<char*>(c->arena[1]) + oP);
     c->partial_b = reinterpret_cast<float*>(static_cast<char*>(c->arena[1]) + oPb);
+    if (fuse) c->fpart = reinterpret_cast<float*>(static_cast<char*>(c->arena[1]) + oFz);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->umma_sched, 0, 4 * sizeof(unsigned), c->st);
   if (e == cudaSuccess)
@@ -945,7 +977,7 @@ ntf_status ntf_mttkrp(ntf_ctx* c, int mode, const float* const* F, float* d_M) {
   if (misaligned(d_M, sizeof(float))) return fail(NTF_ERR_INVALID_ARG, "misaligned output");
   if (mode < c->s_R) {
     float* T = c->s_R == 1 ? d_M : c->TR;
-    NTF_TRY(contract_right(c, F, T, c->st));
+    NTF_TRY(contract_right(c, F, T, c->st, false, mode == 0));
     NTF_TRY(finish_mode(c, mode, T, F, d_M, c->st));
   } else {
     NTF_TRY(contract_left(c, F, c->TL, c->st));

@@ -195,6 +195,32 @@ __global__ void __launch_bounds__(512) k_post_fast4(const float4* __restrict__ T
   }
 }
 
+// The last step of the second tree level formed in the GEMM-N epilogue: one thread per
+// (a, r), the 32-row groups holding rows of a summed in increasing order.
+__global__ void k_post_part(const float* __restrict__ part, int64_t Ia, int64_t Ib, int R,
+                            float* __restrict__ out) {
+  const int64_t n = Ia * R;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t a = i / R;
+    const int r = static_cast<int>(i - a * R);
+    const int64_t g0 = (a * Ib) / 32, g1 = ((a + 1) * Ib - 1) / 32;
+    // the first group may hold a's rows in its second slot; every later one in its first
+    float s = part[(g0 * 2 + (a - (g0 * 32) / Ib)) * R + r];
+    int64_t g = g0 + 1;
+    for (; g + 4 <= g1 + 1; g += 4) {  // four independent loads in flight, added in order
+      const float p0 = part[(g * 2) * R + r], p1 = part[((g + 1) * 2) * R + r];
+      const float p2 = part[((g + 2) * 2) * R + r], p3 = part[((g + 3) * 2) * R + r];
+      s += p0;
+      s += p1;
+      s += p2;
+      s += p3;
+    }
+    for (; g <= g1; ++g) s += part[(g * 2) * R + r];
+    out[i] = s;
+  }
+}
+
 // slow: out[b, :] = sum_a T[a, b, :] * F[a, :].  CTA (b-block of kPostBB rows, a-split):
 // thread (bb, chunk) accumulates over its split's a-range; every CTA writes its partial,
 // and the last CTA of a b-block to finish (counter) adds the splits in order 0, 1, ... and
@@ -497,6 +523,15 @@ cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, con
   k_post_fast4<<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float4*>(T), Ia, Ib, Q,
                                           reinterpret_cast<const float4*>(F),
                                           reinterpret_cast<float4*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_post_part(const float* part, int64_t Ia, int64_t Ib, int R, float* out,
+                             cudaStream_t st) {
+  if (Ib < 32) return cudaErrorInvalidValue;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((Ia * R + 255) / 256, 4096));
+  prefer_shared_carveout<k_post_part>();
+  k_post_part<<<std::max(blocks, 1u), 256, 0, st>>>(part, Ia, Ib, R, out);
   return cudaGetLastError();
 }
 

@@ -159,6 +159,11 @@ cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, cons
 bool post4_ok(int R, const void* T, const void* F, const void* out);
 cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               float* out, cudaStream_t st);
+// The last step of the second tree level formed in a GEMM-N epilogue (umma::Args::post_*):
+// out[a, r] = sum over the 32-row groups g holding rows of a, in increasing g, of
+// part[g][a - 32 g / Ib][r]  (Ib >= 32).
+cudaError_t launch_post_part(const float* part, int64_t Ia, int64_t Ib, int R, float* out,
+                             cudaStream_t st);
 int post_slow4_splits(int64_t Ia, int64_t Ib, int num_sms);
 int64_t post_slow4_blocks(int64_t Ib);
 cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
@@ -181,6 +186,13 @@ struct Args {
   int* err;           // device status word: kStTimeout is or-ed in on a timeout
   unsigned* sched;    // [2] work-item counter and finished-CTA counter (zero between launches)
   const int* skip;    // nonzero flag (read once per CTA): no work; may be null
+  // GEMM-N with one K-chunk: the leading mode's second tree level formed in the epilogue.
+  // Output row p = a Ib + b contributes out[p] * post_F[b] to mode a's MTTKRP row; per group
+  // of 32 rows g, post_part[g][0..1][0..R) hold the sums over its rows of the first and the
+  // second value of a it meets (post_Ib >= 32).  post_F null: off.
+  const float* post_F;
+  int64_t post_Ib;
+  float* post_part;
 };
 }  // namespace umma
 
@@ -207,7 +219,8 @@ cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* W
 // sched: 2 device counters owned by the caller, zero before the first launch (each launch
 // leaves them zero); launches sharing a counter pair must not overlap
 cudaError_t launch_umma(const UmmaPlan& plan, float* out, int* err, unsigned* sched,
-                        const int* skip, cudaStream_t st);
+                        const int* skip, cudaStream_t st, const float* post_F = nullptr,
+                        int64_t post_Ib = 0, float* post_part = nullptr);
 // The contractions' bounded mbarrier wait, on a barrier that nothing completes: ors
 // kStTimeout into *err after limit_ns.
 cudaError_t launch_wait_check(int* err, uint64_t limit_ns, cudaStream_t st);

@@ -119,9 +119,15 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
 }
 
 cudaError_t launch_umma(const UmmaPlan& p, float* out, int* err, unsigned* sched,
-                        const int* skip, cudaStream_t st) {
+                        const int* skip, cudaStream_t st, const float* post_F, int64_t post_Ib,
+                        float* post_part) {
   if (!p.on || !sched) return cudaErrorInvalidValue;
+  if (post_F && (p.transposed || p.args.chunks != 1 || p.N > 32 || post_Ib < 32 || !post_part))
+    return cudaErrorInvalidValue;
   umma::Args a = p.args;
+  a.post_F = post_F;
+  a.post_Ib = post_Ib;
+  a.post_part = post_part;
   a.out = out;
   a.err = err;
   a.sched = sched;

@@ -220,6 +220,67 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = x - hi;
 }
 
+// Sums over the 32 lanes of a warp of x[0..31], one column per lane: lane l returns the sum
+// of the lanes' x[l].  Halves are exchanged at distances 16, 8, 4, 2, 1 (a lane keeps the
+// half its lane bit selects and adds its partner's copy of it): 31 shuffles, a fixed order.
+__device__ __forceinline__ float warp_colsum(float (&x)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = up ? x[j] : x[j + h];
+      const float keep = up ? x[j + h] : x[j];
+      x[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return x[0];
+}
+
+// The leading mode's second tree level for this warp's 32 output rows (group g): row
+// p = a Ib + b weighs its row v by F[b]; the group's rows belong to at most two values of a
+// (Ib >= 32), a0 = 32 g / Ib and a0 + 1, whose column sums go to part[g][0] and part[g][1]
+// (the second only when the group reaches a0 + 1: no other slot is read).  v is consumed.
+template <int kN>
+__device__ __forceinline__ void post_group(const Args& a, float (&v)[kN], int tile, int warp,
+                                           int lane) {
+  const int64_t g = static_cast<int64_t>(tile) * (kTileM / 32) + warp;
+  if (g * 32 >= a.M) return;  // warp-uniform: no rows
+  const int64_t p = g * 32 + lane;
+  const bool live = p < a.M;
+  const int64_t a0 = (g * 32) / a.post_Ib;
+  const int64_t ar = live ? p / a.post_Ib : a0;
+  const int seg = static_cast<int>(ar - a0);
+  const float* f = a.post_F + (live ? p - ar * a.post_Ib : 0) * a.R;
+  if ((a.R & 3) == 0) {  // rows of F 16-byte aligned: four columns per load
+#pragma unroll
+    for (int c = 0; c < kN; c += 4) {
+      const float4 q = live && c < a.R ? __ldg(reinterpret_cast<const float4*>(f + c))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[c] *= q.x;
+      v[c + 1] *= q.y;
+      v[c + 2] *= q.z;
+      v[c + 3] *= q.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < kN; ++c) v[c] = live && c < a.R ? v[c] * __ldg(f + c) : 0.0f;
+  }
+  const int segs = __any_sync(0xffffffffu, seg == 1) ? 2 : 1;
+  for (int sg = 0; sg < segs; ++sg) {
+    float* dst = a.post_part + (g * 2 + sg) * a.R;
+#pragma unroll
+    for (int blk = 0; blk < kN; blk += 32) {
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        x[j] = blk + j < kN && seg == sg ? v[blk + j < kN ? blk + j : 0] : 0.0f;
+      const float sum = warp_colsum(x, lane);
+      if (blk + lane < a.R) dst[blk + lane] = sum;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------- kernel
 // Register cap: the sweep's other kernels (factor updates, reductions, coefficient systems,
 // second tree levels) run beside the persistent contraction, and one of their 8-warp CTAs
@@ -519,6 +580,9 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
           for (int c = 0; c < kN; ++c)
             if (c < a.R) o[c] = v[c];
         }
+      }
+      if constexpr (!kT && kN <= 32) {  // (wider rows: the level runs as its own kernel)
+        if (a.post_F) post_group<kN>(a, v, tile, warp, lane);
       }
     }
   } else if constexpr (kF32) {

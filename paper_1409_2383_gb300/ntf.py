@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("mu", ctypes.c_double), ("tau_incr", ctypes.c_double),
                 ("tau_decr", ctypes.c_double), ("eps_abs", ctypes.c_double),
                 ("eps_rel", ctypes.c_double), ("contraction", ctypes.c_int),
-                ("kkt_dual_tol", ctypes.c_double), ("kkt_comp_tol", ctypes.c_double)]
+                ("kkt_dual_tol", ctypes.c_double), ("kkt_comp_tol", ctypes.c_double),
+                ("fuse_level", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class TraceEntry(ctypes.Structure):

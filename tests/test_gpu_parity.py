@@ -65,6 +65,10 @@ SHAPES = [
     ((8, 40, 36), 8),           # vectorised second level with one split (short reduced range)
     ((12, 16, 20, 24), 4),      # 4-way, vectorised second levels
     ((200, 160, 40), 12),       # vectorised slow level with many splits and b-blocks
+    # one K-chunk with >= 32 rows per leading index (the shapes of the fused second level)
+    ((157, 131, 24), 20),
+    ((160, 130, 30), 50),
+    ((160, 128, 8, 6), 7),
 ]
 
 
@@ -83,6 +87,36 @@ def test_mttkrp_all_modes(ntf, dims, R, storage):
             M = host(ctx.mttkrp(n, Fd))
             want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], n)
             assert rel(M, want) <= TOL, (n, rel(M, want))
+
+
+@pytest.mark.parametrize("dims,R", [((157, 131, 24), 20), ((160, 130, 30), 32),
+                                    ((160, 128, 8, 6), 7)])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_mttkrp_with_the_fused_second_level(ntf, dims, R, storage):
+    """Factor 0's second tree level formed in the first contraction's epilogue (forced with
+    fuse_level = 1; by default only for intermediates of at least half the L2): mode 0 against
+    the oracle at the MTTKRP tolerance and against the separate level, and a short run that
+    uses it in every sweep against one that does not (ragged 32-row groups, I_2 = 131)."""
+    X, fs = _problem(dims, R, seed=7 * R + len(dims), signed=False)
+    Xt = torch.as_tensor(X).to(torch.bfloat16).cuda() if storage == "bf16" else cuda(X)
+    Xref = torch.as_tensor(X).to(torch.bfloat16).double().numpy() if storage == "bf16" \
+        else X.astype(np.float64)
+    Fd = [cuda(F) for F in fs]
+    want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], 0)
+    got = {}
+    for fl in (1, -1):
+        with ntf.Context(Xt, R, ntf.default_params(fuse_level=fl)) as ctx:
+            got[fl] = host(ctx.mttkrp(0, Fd))
+            assert rel(got[fl], want) <= TOL, (fl, rel(got[fl], want))
+    assert rel(got[1], got[-1]) <= 4 * TOL
+    init = [np.random.default_rng(40 + n).random((d, R)).astype(np.float32)
+            for n, d in enumerate(dims)]
+    errs = {}
+    for fl in (1, -1):
+        with ntf.Context(Xt, R, ntf.default_params(fuse_level=fl)) as ctx:
+            A, At, Y = [cuda(F) for F in init], [cuda(F) for F in init], ntf.zeros_state(dims, R)
+            errs[fl] = ctx.run(A, At, Y, 6)["rel_err"]
+    assert abs(errs[1] - errs[-1]) <= 1e-5 * errs[-1], errs
 
 
 @pytest.mark.parametrize("n", [1 << 20, 1000003])
