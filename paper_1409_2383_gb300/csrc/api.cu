@@ -795,13 +795,14 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
   int64_t post_counts = 0;
   if (R % 4 == 0) {
     if (c->s_R == 2) {
-      c->post4_split_left = ntf::post_slow4_splits(dims[0], dims[1], c->num_sms);
+      c->post4_split_left = ntf::post_slow4_splits(dims[0], dims[1], R, c->num_sms);
       part = std::max<int64_t>(part, c->post4_split_left * dims[1] * R);
       post_counts += ntf::post_slow4_blocks(dims[1]);
     }
     c->post_count_right = post_counts;
     if (order - c->s_L == 2) {
-      c->post4_split_right = ntf::post_slow4_splits(dims[c->s_L], dims[c->s_L + 1], c->num_sms);
+      c->post4_split_right =
+          ntf::post_slow4_splits(dims[c->s_L], dims[c->s_L + 1], R, c->num_sms);
       part = std::max<int64_t>(part, c->post4_split_right * dims[c->s_L + 1] * R);
       post_counts += ntf::post_slow4_blocks(dims[c->s_L + 1]);
     }

@@ -208,13 +208,12 @@ __global__ void k_post_part(const float* __restrict__ part, int64_t Ia, int64_t 
     // the first group may hold a's rows in its second slot; every later one in its first
     float s = part[(g0 * 2 + (a - (g0 * 32) / Ib)) * R + r];
     int64_t g = g0 + 1;
-    for (; g + 4 <= g1 + 1; g += 4) {  // four independent loads in flight, added in order
-      const float p0 = part[(g * 2) * R + r], p1 = part[((g + 1) * 2) * R + r];
-      const float p2 = part[((g + 2) * 2) * R + r], p3 = part[((g + 3) * 2) * R + r];
-      s += p0;
-      s += p1;
-      s += p2;
-      s += p3;
+    for (; g + 8 <= g1 + 1; g += 8) {  // eight independent loads in flight, added in order
+      float q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = part[((g + u) * 2) * R + r];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += q[u];
     }
     for (; g <= g1; ++g) s += part[(g * 2) * R + r];
     out[i] = s;
@@ -535,9 +534,19 @@ cudaError_t launch_post_part(const float* part, int64_t Ia, int64_t Ib, int R, f
   return cudaGetLastError();
 }
 
-int post_slow4_splits(int64_t Ia, int64_t Ib, int num_sms) {
+int post_slow4_splits(int64_t Ia, int64_t Ib, int R, int num_sms) {
+  // As many splits of the reduced range as keep every CTA resident at once: a second,
+  // partial wave of CTAs would take as long as the first (at 1000 x 1000, R = 32: 320 CTAs
+  // at 2 per SM were 1.05 waves and took twice the time of 288).
   const int64_t bblocks = (Ib + kPostBB - 1) / kPostBB;
-  int64_t splits = (static_cast<int64_t>(num_sms) * 2 + bblocks - 1) / bblocks;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_slow4, kPostBB * (R / 4),
+                                                    0) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  int64_t splits = static_cast<int64_t>(per_sm) * num_sms / bblocks;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, Ia / 16)));
   return static_cast<int>(std::min<int64_t>(splits, 64));
 }
