@@ -54,17 +54,17 @@ struct Cfg {
   static constexpr int kSplits = kF32 ? 2 : 3;     // W parts
   static constexpr int kABytes = kTileM * 128;     // operand tile (hi part for FP32)
   static constexpr int kLoBytes = kF32 ? kTileM * 128 : 0;
-  static constexpr int kRawBytes = (kF32 && kT) ? kTileM * 128 : 0;  // untransposed X rows
   static constexpr int kWBlockBytes = kSplits * kN * 128;            // W rows of one K block
   static constexpr int kWBytes = kWRes ? 0 : kWBlockBytes;           // W per stage
   static constexpr int kWBlocks = kWRes ? (kN <= 16 ? 8 : 7) : 0;    // resident K blocks
   static constexpr int kWResBytes = kWBlocks * kWBlockBytes;
-  static constexpr int kStageBytes = kABytes + kLoBytes + kRawBytes + kWBytes;
+  // (FP32 GEMM-T: the untransposed X rows land in the operand tile and are transposed there)
+  static constexpr int kStageBytes = kABytes + kLoBytes + kWBytes;
   static constexpr int kStagesRaw =
       ((kWRes ? 224 * 1024 : kSmemBudget) - kWResBytes) / kStageBytes;
   static constexpr int kStagesMax = kWRes ? 8 : 6;
   static constexpr int kStages = kStagesRaw > kStagesMax ? kStagesMax : kStagesRaw;
-  static constexpr int kTxBytes = ((kF32 && kT) ? kRawBytes : kABytes) + kWBytes;
+  static constexpr int kTxBytes = kABytes + kWBytes;
   static constexpr int kWarps = kF32 ? 10 : 6;
   static constexpr int kThreads = kWarps * 32;
   // Accumulator of one segment: one N-column block per W part (x w1 | x w2 | x w3 for BF16,
@@ -299,6 +299,7 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[S], ready[S], empty[S], tfull[2], tempty[2], drain, wfull;
+  __shared__ uint64_t cread[S];  // FP32 GEMM-T: every converter warp has read the raw tile
   __shared__ uint64_t ifull[kItemQ], iempty[kItemQ];
   __shared__ int s_item[kItemQ];
   __shared__ uint32_t tmem_base;
@@ -328,6 +329,7 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
     for (int s = 0; s < S; ++s) {
       bar_init(&full[s], 1);
       bar_init(&ready[s], 4);
+      bar_init(&cread[s], 4);
       bar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -377,8 +379,7 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
   const uint32_t stages_s = base_s + C::kWResBytes;
   auto stage_ptr = [&](int slot) { return base + C::kWResBytes + slot * C::kStageBytes; };
   // piece offsets within a stage
-  constexpr int kOffA = 0, kOffLo = C::kABytes, kOffRaw = kOffLo + C::kLoBytes,
-                kOffW = kOffRaw + C::kRawBytes;
+  constexpr int kOffA = 0, kOffLo = C::kABytes, kOffW = kOffLo + C::kLoBytes;
 
   if (warp == 4) {
     // ------------------------------------------------------------------ TMA producer
@@ -425,7 +426,7 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
             tma_2d(st + kOffA, &tx, m0, kx, &full[slot]);
             tma_2d(st + kOffA + kTileM * 64, &tx, m0 + 64, kx, &full[slot]);
           } else {
-            tma_2d(st + kOffRaw, &tx, m0, kx, &full[slot]);
+            tma_2d(st + kOffA, &tx, m0, kx, &full[slot]);  // raw rows, transposed in place
           }
           if constexpr (!kWRes) tma_2d(st + kOffW, &tw, kx, 0, &full[slot]);
         }
@@ -628,18 +629,31 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
             *reinterpret_cast<float4*>(st + kOffLo + off) = l;
           }
         } else {
-          // transpose: raw rows [32 K][128 M] (plain layout) -> K-major rows of the
-          // operand tiles, 128 bytes (32 K values) per M row, 16-byte chunk c stored at
-          // chunk position c ^ (m & 7) (the 128-byte swizzle)
-          const float* raw = reinterpret_cast<const float*>(st + kOffRaw);
+          // transpose in place: thread m reads column m of the raw rows [32 K][128 M] (plain
+          // layout) into registers; once all four converter warps have read the tile (cread:
+          // one arrival per warp, a bounded wait) the K-major operand rows overwrite it, 128
+          // bytes (32 K values) per M row, 16-byte chunk c at chunk position c ^ (m & 7) (the
+          // 128-byte swizzle), and the lo parts go to the lo tile.  (A separate raw buffer
+          // would cost two of the five stages.)
+          const float* raw = reinterpret_cast<const float*>(st + kOffA);
           const int m = t;
+          float xv[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) xv[k] = raw[k * kTileM + m];
+          __syncwarp();
+          if (lane == 0) bar_arrive(&cread[slot]);
+          ok = __all_sync(0xffffffffu, bar_wait(&cread[slot], (g / S) & 1, abrt));
+          if (!ok) {
+            if (lane == 0) give_up();
+            break;
+          }
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             float4 h, l;
-            split_tf32(raw[(4 * c + 0) * kTileM + m], h.x, l.x);
-            split_tf32(raw[(4 * c + 1) * kTileM + m], h.y, l.y);
-            split_tf32(raw[(4 * c + 2) * kTileM + m], h.z, l.z);
-            split_tf32(raw[(4 * c + 3) * kTileM + m], h.w, l.w);
+            split_tf32(xv[4 * c + 0], h.x, l.x);
+            split_tf32(xv[4 * c + 1], h.y, l.y);
+            split_tf32(xv[4 * c + 2], h.z, l.z);
+            split_tf32(xv[4 * c + 3], h.w, l.w);
             const int off = m * 128 + ((c ^ (m & 7)) << 4);
             *reinterpret_cast<float4*>(st + kOffA + off) = h;
             *reinterpret_cast<float4*>(st + kOffLo + off) = l;
