@@ -3,10 +3,12 @@
 // Khatri-Rao matrix).  Entry (i_1, ..., i_N) with value v adds v prod_{m != n} F_m[i_m, :] to
 // row i_n of M.
 //
-// Layout, built once by ntf_sptensor_create: for every mode n, the nonzeros sorted by i_n
-// (stable: equal i_n keep their input order) as packed words (i_n, the other modes' indices,
-// the value's bits) -- N + 1 words, one 16-byte load for a 3-way tensor -- plus row offsets
-// [I_n + 1], so that an MTTKRP streams each nonzero once, in order.  The sort is a
+// Layout, built once by ntf_sptensor_create: for every mode n, the nonzeros sorted by i_n and,
+// within a row, by the index of the first other mode (equal pairs keep their input order), as
+// packed words (i_n, the other modes' indices, the value's bits) -- N + 1 words, one 16-byte
+// load for a 3-way tensor -- plus row offsets [I_n + 1], so that an MTTKRP streams each
+// nonzero once, in order, and the nonzeros of a row that share that index come together (their
+// factor row is gathered once from L2, then from L1).  The sort is a
 // least-significant-digit radix sort, 8 bits per pass, each pass a stable counting sort over
 // tiles of 4096 nonzeros: per-tile digit histograms, their prefix over (digit, tile), and a
 // scatter in which each tile ranks its nonzeros in order (warp match on the digit, then
@@ -134,6 +136,14 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     run[tid] += c;
     __syncthreads();
   }
+}
+
+// key[p] = the mode-`mode` index of nonzero pay[p] (the second key of a two-key sort).
+__global__ void k_gather_keys(const int32_t* __restrict__ idx, int N, int mode, int64_t n,
+                              const uint32_t* __restrict__ pay, uint32_t* __restrict__ key) {
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    key[p] = static_cast<uint32_t>(idx[static_cast<int64_t>(pay[p]) * N + mode]);
 }
 
 __global__ void k_iota_keys(const int32_t* __restrict__ idx, int N, int mode, int64_t n,
@@ -364,17 +374,27 @@ ntf_status ntf_sptensor_create(ntf_sptensor** out, int order, const int64_t* dim
   s->partial = reinterpret_cast<float*>(b + oPart);
   cudaStream_t st = s->st;
   for (int m = 0; m < order && e == cudaSuccess; ++m) {
-    k_iota_keys<<<grid_for(nnz, 256), 256, 0, st>>>(d_idx, order, m, nnz, key[0], pay[0]);
+    // two stable passes of the radix sort: by the first other mode's index, then by this
+    // mode's (the order of the first survives among equal i_n)
+    const int m2 = m == 0 ? 1 : 0;
+    k_iota_keys<<<grid_for(nnz, 256), 256, 0, st>>>(d_idx, order, m2, nnz, key[0], pay[0]);
     int cur = 0;
-    for (int shift = 0; shift < 32 && e == cudaSuccess; shift += 8) {
-      if (shift > 0 && (dims[m] - 1) >> shift == 0) break;  // the remaining digits are zero
-      k_digit_hist<<<static_cast<unsigned>(tiles), kSortThreads, 0, st>>>(key[cur], nnz, shift,
-                                                                         hist);
-      k_digit_offsets<<<1, 256, 0, st>>>(hist, static_cast<int>(tiles));
-      k_digit_scatter<<<static_cast<unsigned>(tiles), kSortThreads, 0, st>>>(
-          key[cur], pay[cur], nnz, shift, hist, key[cur ^ 1], pay[cur ^ 1]);
-      cur ^= 1;
-      e = cudaGetLastError();
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+      const int64_t I = pass == 0 ? dims[m2] : dims[m];
+      if (pass == 1) {
+        k_gather_keys<<<grid_for(nnz, 256), 256, 0, st>>>(d_idx, order, m, nnz, pay[cur],
+                                                          key[cur]);
+      }
+      for (int shift = 0; shift < 32 && e == cudaSuccess; shift += 8) {
+        if (shift > 0 && (I - 1) >> shift == 0) break;  // the remaining digits are zero
+        k_digit_hist<<<static_cast<unsigned>(tiles), kSortThreads, 0, st>>>(key[cur], nnz,
+                                                                           shift, hist);
+        k_digit_offsets<<<1, 256, 0, st>>>(hist, static_cast<int>(tiles));
+        k_digit_scatter<<<static_cast<unsigned>(tiles), kSortThreads, 0, st>>>(
+            key[cur], pay[cur], nnz, shift, hist, key[cur ^ 1], pay[cur ^ 1]);
+        cur ^= 1;
+        e = cudaGetLastError();
+      }
     }
     if (e != cudaSuccess) break;
     k_pack<<<grid_for(nnz, 256), 256, 0, st>>>(d_idx, d_vals, order, m, nnz, pay[cur],
