@@ -282,6 +282,101 @@ __global__ void __launch_bounds__(256) k_sp_chunks(const uint32_t* __restrict__ 
   }
 }
 
+// The same chunks for R <= 32 (one column per lane), with fewer instructions per nonzero: each
+// group of 32 nonzeros is loaded coalesced (the next group's load issued before the current
+// group is walked) and staged in shared memory, from which every lane reads the nonzero it
+// walks as one broadcast load (instead of a shuffle per field); the row of the first other
+// mode, whose equal indices the layout keeps together within a row, stays in a register while
+// the index repeats; the rows of the other modes are gathered kUnroll nonzeros at a time.
+template <int N>
+__global__ void __launch_bounds__(256) k_sp_chunks32(const uint32_t* __restrict__ packed,
+                                                     int64_t nnz, int R, SpF f,
+                                                     float* __restrict__ M,
+                                                     float* __restrict__ partial) {
+  constexpr int kUnroll = 8, kW = N + 1;
+  __shared__ __align__(16) uint32_t s_nz[8][32 * kW + 4];  // per warp: 32 nonzeros (N + 1 words)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* const sw = s_nz[warp];
+  const bool h = lane < R;
+  const int64_t chunks = (nnz + kChunk - 1) / kChunk;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp; c < chunks;
+       c += warps) {
+    const int64_t p0 = c * kChunk, p1 = p0 + kChunk < nnz ? p0 + kChunk : nnz;
+    uint32_t row = __ldg(packed + p0 * kW);
+    bool before = p0 > 0 && __ldg(packed + (p0 - 1) * kW) == row;
+    float acc = 0.0f;
+    uint32_t cur = 0xFFFFFFFFu;  // index of the first other mode's row held in g
+    float g = 0.0f;
+    float* const part = partial + c * 2 * 64;
+    auto flush = [&](bool cont) {
+      float* o = before ? part : cont ? part + 64 : M + static_cast<int64_t>(row) * R;
+      if (h) o[lane] = acc;
+    };
+    uint32_t nxt[kW];
+    if (lane < p1 - p0) {
+      load_nz<N>(packed + (p0 + lane) * kW, nxt);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kW; ++k) nxt[k] = 0;
+    }
+    for (int64_t base = p0; base < p1; base += 32) {
+      const int cnt = p1 - base < 32 ? static_cast<int>(p1 - base) : 32;
+      __syncwarp();
+      if constexpr (N == 3) {
+        *reinterpret_cast<uint4*>(sw + lane * 4) = make_uint4(nxt[0], nxt[1], nxt[2], nxt[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kW; ++k) sw[lane * kW + k] = nxt[k];
+      }
+      __syncwarp();
+      if (base + 32 + lane < p1) load_nz<N>(packed + (base + 32 + lane) * kW, nxt);
+      for (int j0 = 0; j0 < cnt; j0 += kUnroll) {
+        float t[kUnroll];
+        uint32_t key[kUnroll], i1[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {  // value times the rows of modes 2 .. N-1
+          const int j = j0 + u < cnt ? j0 + u : cnt - 1;
+          uint32_t q[kW];
+          if constexpr (N == 3) {
+            const uint4 w = *reinterpret_cast<const uint4*>(sw + j * 4);  // broadcast
+            q[0] = w.x;
+            q[1] = w.y;
+            q[2] = w.z;
+            q[3] = w.w;
+          } else {
+#pragma unroll
+            for (int k = 0; k < kW; ++k) q[k] = sw[j * kW + k];
+          }
+          key[u] = q[0];
+          i1[u] = q[1];
+          float v = __uint_as_float(q[N]);
+#pragma unroll
+          for (int m = 1; m < N - 1; ++m)
+            v *= h ? __ldg(f.F[m] + static_cast<int64_t>(q[1 + m]) * R + lane) : 0.0f;
+          t[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {  // in order: row changes, the first mode's row
+          if (j0 + u >= cnt) break;           // warp-uniform
+          if (key[u] != row) {
+            flush(false);
+            before = false;
+            row = key[u];
+            acc = 0.0f;
+          }
+          if (i1[u] != cur) {  // warp-uniform
+            cur = i1[u];
+            g = h ? __ldg(f.F[0] + static_cast<int64_t>(cur) * R + lane) : 0.0f;
+          }
+          acc = fmaf(t[u], g, acc);
+        }
+      }
+    }
+    flush(p1 < nnz && __ldg(packed + p1 * kW) == row);
+  }
+}
+
 // Rows cut by chunk boundaries: the sum of their segments in chunk order; rows without
 // nonzeros: zero.  One warp per row.
 __global__ void __launch_bounds__(256) k_sp_fixup(const int64_t* __restrict__ rowptr, int64_t I,
@@ -441,7 +536,11 @@ ntf_status ntf_sptensor_mttkrp(ntf_sptensor* s, int mode, int rank,
   const int64_t I = s->dims[mode];
   const int64_t chunks = (s->nnz + kChunk - 1) / kChunk;
   const unsigned gc = grid_for(chunks * 32, 256), gf = grid_for(I * 32, 256);
-  if (s->N == 3)
+  if (rank <= 32 && s->N == 3)
+    k_sp_chunks32<3><<<gc, 256, 0, s->st>>>(s->packed[mode], s->nnz, rank, f, d_M, s->partial);
+  else if (rank <= 32)
+    k_sp_chunks32<4><<<gc, 256, 0, s->st>>>(s->packed[mode], s->nnz, rank, f, d_M, s->partial);
+  else if (s->N == 3)
     k_sp_chunks<3><<<gc, 256, 0, s->st>>>(s->packed[mode], s->nnz, rank, f, d_M, s->partial);
   else
     k_sp_chunks<4><<<gc, 256, 0, s->st>>>(s->packed[mode], s->nnz, rank, f, d_M, s->partial);
