@@ -140,6 +140,21 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
   }
 }
 
+// The same for waits that last a whole accumulation segment (the epilogue's): a short sleep
+// between tests leaves the SM's issue slots to the kernels that share it.
+__device__ __forceinline__ bool bar_wait_patient(uint64_t* b, uint32_t parity,
+                                                 volatile int* abort_flag) {
+  uint64_t t0 = 0;
+  for (uint32_t n = 0;; ++n) {
+    if (bar_try(b, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    const uint64_t t = now_ns();
+    if (n == 0) t0 = t;
+    else if (t - t0 > kWaitNs) return false;
+    __nanosleep(256);
+  }
+}
+
 __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y,
                                        uint64_t* bar) {
   asm volatile(
@@ -542,7 +557,7 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
       for (int c = 0; c < kN; ++c) v[c] = 0.0f;
       for (int s0 = 0; s0 < nks; s0 += C::kSegStages, ++u) {
         const uint32_t b = u & 1;
-        ok = __all_sync(0xffffffffu, bar_wait(&tfull[b], (u >> 1) & 1, abrt));
+        ok = __all_sync(0xffffffffu, bar_wait_patient(&tfull[b], (u >> 1) & 1, abrt));
         if (!ok) {
           if (lane == 0) give_up();
           break;
