@@ -793,7 +793,7 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     part = std::max<int64_t>(part, c->post_split_right * dims[c->s_L + 1] * R);
   }
   int64_t post_counts = 0;
-  if (R % 4 == 0) {
+  if (R % 4 == 0 || (R % 2 == 0 && R <= 64)) {  // the vectorised levels (float4 or float2)
     if (c->s_R == 2) {
       c->post4_split_left = ntf::post_slow4_splits(dims[0], dims[1], R, c->num_sms);
       part = std::max<int64_t>(part, c->post4_split_left * dims[1] * R);

@@ -195,6 +195,63 @@ __global__ void __launch_bounds__(512) k_post_fast4(const float4* __restrict__ T
   }
 }
 
+// The same for even R that is not a multiple of 4, in float2 vectors (R <= 64: up to 32 Q =
+// 1024 threads).  The kernels below are written over the vector type V and instantiated for
+// float2 only (float4 instances of them ran 18 % slower than the kernels above).
+template <typename V>
+constexpr int kPostMaxThreads = 1024;
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ void vfma(float2& s, const float2& a, const float2& b) {
+  s.x = fmaf(a.x, b.x, s.x);
+  s.y = fmaf(a.y, b.y, s.y);
+}
+__device__ __forceinline__ void vadd(float2& s, const float2& p) {
+  s.x += p.x;
+  s.y += p.y;
+}
+
+// The fast level in V vectors (Q = R / V's width per row; T, F, out aligned to V):
+// out[a, :] = sum_b T[a, b, :] * F[b, :].  One CTA (32 Q threads) per a; the slab
+// T[a] (Ib Q vectors, contiguous) is read in order: thread t takes vector q = t % Q of rows
+// b = t / Q, t / Q + 32, ... (eight rows in flight), so consecutive threads read
+// consecutive vectors; then the 32 partial sums of each vector are added in a fixed order
+// through shared memory.
+template <typename V>
+__global__ void __launch_bounds__(kPostMaxThreads<V>) k_post_fastv(const V* __restrict__ T, int64_t Ia,
+                                                    int64_t Ib, int Q, const V* __restrict__ F,
+                                                    V* __restrict__ out) {
+  __shared__ V part[1024];
+  const int t = threadIdx.x, q = t % Q, b0 = t / Q;
+  for (int64_t a = blockIdx.x; a < Ia; a += gridDim.x) {
+    const V* Ta = T + a * Ib * Q;
+    V s[2] = {vzero<V>(), vzero<V>()};
+    for (int64_t bb = b0; bb < Ib; bb += 32 * 8) {
+      V tv[8], fv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t b = bb + 32 * u;
+        tv[u] = fv[u] = vzero<V>();
+        if (b < Ib) {
+          tv[u] = Ta[b * Q + q];
+          fv[u] = __ldg(F + b * Q + q);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) vfma(s[u & 1], tv[u], fv[u]);
+    }
+    vadd(s[0], s[1]);
+    part[t] = s[0];
+    __syncthreads();
+    if (t < Q) {  // vector t: partials t, t + Q, ..., t + 31 Q
+      V v = part[t];
+      for (int j = 1; j < 32; ++j) vadd(v, part[t + j * Q]);
+      out[a * Q + t] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // The last step of the second tree level formed in the GEMM-N epilogue: one thread per
 // (a, r), the 32-row groups holding rows of a summed in increasing order.
 __global__ void k_post_part(const float* __restrict__ part, int64_t Ia, int64_t Ib, int R,
@@ -315,6 +372,74 @@ __global__ void k_post_slow4(const float4* __restrict__ T, int64_t Ia, int64_t I
       acc.z += p.z;
       acc.w += p.w;
     }
+    out[b * Q + q] = acc;
+  }
+  if (t == 0) count[blockIdx.x] = 0;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kPostMaxThreads<V>) k_post_slowv(const V* __restrict__ T, int64_t Ia,
+                                                    int64_t Ib, int Q, const V* __restrict__ F,
+                                                    int splits, V* __restrict__ partial,
+                                                    unsigned* __restrict__ count,
+                                                    V* __restrict__ out) {
+  const int split = blockIdx.y;
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x) * kPostBB;
+  const int t = threadIdx.x;
+  const int bb = t / Q, q = t - bb * Q;
+  const int64_t b = b0 + bb;
+  const int64_t a_beg = Ia * split / splits, a_end = Ia * (split + 1) / splits;
+  V s[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) s[u] = vzero<V>();
+  if (b < Ib) {
+    int64_t a = a_beg;
+    for (; a + 7 < a_end; a += 8) {  // eight rows' loads in flight
+      V tv[8], fv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        tv[u] = T[((a + u) * Ib + b) * Q + q];
+        fv[u] = __ldg(F + (a + u) * Q + q);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) vfma(s[u & 3], tv[u], fv[u]);
+    }
+    for (; a + 3 < a_end; a += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vfma(s[u], T[((a + u) * Ib + b) * Q + q], __ldg(F + (a + u) * Q + q));
+    }
+    for (; a < a_end; ++a) vfma(s[0], T[(a * Ib + b) * Q + q], __ldg(F + a * Q + q));
+  }
+  vadd(s[0], s[1]);
+  vadd(s[2], s[3]);
+  vadd(s[0], s[2]);
+  const V v = s[0];
+  if (splits == 1) {
+    if (b < Ib) out[b * Q + q] = v;
+    return;
+  }
+  if (b < Ib) partial[(static_cast<int64_t>(split) * Ib + b) * Q + q] = v;
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(count + blockIdx.x, 1u) == static_cast<unsigned>(splits - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (b < Ib) {
+    // splits added in order 0, 1, ...; loads issued eight at a time (independent) so that
+    // the L2 round trips overlap
+    V acc = vzero<V>();
+    int k = 0;
+    for (; k + 8 <= splits; k += 8) {
+      V pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        pv[u] = __ldcg(partial + (static_cast<int64_t>(k + u) * Ib + b) * Q + q);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) vadd(acc, pv[u]);
+    }
+    for (; k < splits; ++k) vadd(acc, __ldcg(partial + (static_cast<int64_t>(k) * Ib + b) * Q + q));
     out[b * Q + q] = acc;
   }
   if (t == 0) count[blockIdx.x] = 0;
@@ -509,19 +634,36 @@ cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, cons
   return launch_sum_splits(partial, splits, Ib * R, out, st);
 }
 
-bool post4_ok(int R, const void* T, const void* F, const void* out) {
+namespace {
+// float4 when R % 4 == 0 and the arrays are 16-byte aligned, else float2 (even R, 8 bytes)
+bool post_vec4(int R, const void* T, const void* F, const void* out) {
   const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   return R % 4 == 0 && R <= 128 && al(T) && al(F) && al(out);
+}
+}  // namespace
+
+bool post4_ok(int R, const void* T, const void* F, const void* out) {
+  if (post_vec4(R, T, F, out)) return true;
+  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; };
+  return R % 2 == 0 && R <= 64 && al(T) && al(F) && al(out);
 }
 
 cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               float* out, cudaStream_t st) {
-  const int Q = R / 4;
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(Ia, 65535));
-  prefer_shared_carveout<k_post_fast4>();
-  k_post_fast4<<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float4*>(T), Ia, Ib, Q,
-                                          reinterpret_cast<const float4*>(F),
-                                          reinterpret_cast<float4*>(out));
+  if (post_vec4(R, T, F, out)) {
+    const int Q = R / 4;
+    prefer_shared_carveout<k_post_fast4>();
+    k_post_fast4<<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float4*>(T), Ia, Ib, Q,
+                                            reinterpret_cast<const float4*>(F),
+                                            reinterpret_cast<float4*>(out));
+  } else {
+    const int Q = R / 2;
+    prefer_shared_carveout<k_post_fastv<float2>>();
+    k_post_fastv<float2><<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float2*>(T), Ia,
+                                                    Ib, Q, reinterpret_cast<const float2*>(F),
+                                                    reinterpret_cast<float2*>(out));
+  }
   return cudaGetLastError();
 }
 
@@ -540,9 +682,12 @@ int post_slow4_splits(int64_t Ia, int64_t Ib, int R, int num_sms) {
   // at 2 per SM were 1.05 waves and took twice the time of 288).
   const int64_t bblocks = (Ib + kPostBB - 1) / kPostBB;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_slow4, kPostBB * (R / 4),
-                                                    0) != cudaSuccess ||
-      per_sm < 1) {
+  const cudaError_t oe =
+      R % 4 == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_slow4,
+                                                                 kPostBB * (R / 4), 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_slowv<float2>,
+                                                                 kPostBB * (R / 2), 0);
+  if (oe != cudaSuccess || per_sm < 1) {
     (void)cudaGetLastError();
     per_sm = 1;
   }
@@ -556,12 +701,20 @@ int64_t post_slow4_blocks(int64_t Ib) { return (Ib + kPostBB - 1) / kPostBB; }
 cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               int splits, float* partial, unsigned* count, float* out,
                               cudaStream_t st) {
-  const int Q = R / 4;
   dim3 grid(static_cast<unsigned>(post_slow4_blocks(Ib)), static_cast<unsigned>(splits));
-  prefer_shared_carveout<k_post_slow4>();
-  k_post_slow4<<<grid, kPostBB * Q, 0, st>>>(
-      reinterpret_cast<const float4*>(T), Ia, Ib, Q, reinterpret_cast<const float4*>(F), splits,
-      reinterpret_cast<float4*>(partial), count, reinterpret_cast<float4*>(out));
+  if (post_vec4(R, T, F, out) && (reinterpret_cast<uintptr_t>(partial) & 15) == 0) {
+    const int Q = R / 4;
+    prefer_shared_carveout<k_post_slow4>();
+    k_post_slow4<<<grid, kPostBB * Q, 0, st>>>(
+        reinterpret_cast<const float4*>(T), Ia, Ib, Q, reinterpret_cast<const float4*>(F),
+        splits, reinterpret_cast<float4*>(partial), count, reinterpret_cast<float4*>(out));
+  } else {
+    const int Q = R / 2;
+    prefer_shared_carveout<k_post_slowv<float2>>();
+    k_post_slowv<float2><<<grid, kPostBB * Q, 0, st>>>(
+        reinterpret_cast<const float2*>(T), Ia, Ib, Q, reinterpret_cast<const float2*>(F),
+        splits, reinterpret_cast<float2*>(partial), count, reinterpret_cast<float2*>(out));
+  }
   return cudaGetLastError();
 }
 

@@ -154,8 +154,9 @@ cudaError_t launch_post_fast(const float* T, int64_t Ia, int64_t Ib, int R, cons
 int post_slow_splits(int64_t Ia, int64_t Ib, int R, int num_sms);
 cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                              int splits, float* partial, float* out, cudaStream_t st);
-// Vectorised variants (R % 4 == 0, 16-byte aligned T, F, out: post4_ok); slow: splits of the
-// reduced range with partials [splits, Ib, R] and per-b-block counters (zeroed, left zeroed)
+// Vectorised variants (post4_ok: float4 for R % 4 == 0 and 16-byte aligned T, F, out; else
+// float2 for even R <= 64 and 8-byte alignment); slow: splits of the reduced range with
+// partials [splits, Ib, R] and per-b-block counters (zeroed, left zeroed)
 bool post4_ok(int R, const void* T, const void* F, const void* out);
 cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               float* out, cudaStream_t st);

@@ -69,6 +69,10 @@ SHAPES = [
     ((157, 131, 24), 20),
     ((160, 130, 30), 50),
     ((160, 128, 8, 6), 7),
+    # even ranks that are not multiples of 4: the second tree levels in float2 vectors
+    ((90, 50, 60), 18),
+    ((64, 80, 48), 2),
+    ((40, 36, 30, 20), 10),
 ]
 
 
