@@ -797,14 +797,14 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     if (c->s_R == 2) {
       c->post4_split_left = ntf::post_slow4_splits(dims[0], dims[1], R, c->num_sms);
       part = std::max<int64_t>(part, c->post4_split_left * dims[1] * R);
-      post_counts += ntf::post_slow4_blocks(dims[1]);
+      post_counts += ntf::post_slow4_blocks(dims[1], R);
     }
     c->post_count_right = post_counts;
     if (order - c->s_L == 2) {
       c->post4_split_right =
           ntf::post_slow4_splits(dims[c->s_L], dims[c->s_L + 1], R, c->num_sms);
       part = std::max<int64_t>(part, c->post4_split_right * dims[c->s_L + 1] * R);
-      post_counts += ntf::post_slow4_blocks(dims[c->s_L + 1]);
+      post_counts += ntf::post_slow4_blocks(dims[c->s_L + 1], R);
     }
   }
   const int64_t w_rows = ntf::kr_rows_padded(c->Q_R), w_rows_b = ntf::kr_rows_padded(c->P_L);

@@ -200,6 +200,10 @@ __global__ void __launch_bounds__(512) k_post_fast4(const float4* __restrict__ T
 // float2 only (float4 instances of them ran 18 % slower than the kernels above).
 template <typename V>
 constexpr int kPostMaxThreads = 1024;
+// b-block of the slow level in float2 vectors: 8 rows (8 Q <= 256 threads: a CTA fits on an
+// SM beside a persistent contraction CTA, which the 32-row block of up to 1024 threads
+// does not, and the level runs beside the contraction in a sweep)
+constexpr int kPostBB2 = 8;
 template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 __device__ __forceinline__ void vfma(float2& s, const float2& a, const float2& b) {
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kPostMaxThreads<V>) k_post_slowv(const V* __re
                                                     unsigned* __restrict__ count,
                                                     V* __restrict__ out) {
   const int split = blockIdx.y;
-  const int64_t b0 = static_cast<int64_t>(blockIdx.x) * kPostBB;
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x) * kPostBB2;
   const int t = threadIdx.x;
   const int bb = t / Q, q = t - bb * Q;
   const int64_t b = b0 + bb;
@@ -635,23 +639,21 @@ cudaError_t launch_post_slow(const float* T, int64_t Ia, int64_t Ib, int R, cons
 }
 
 namespace {
-// float4 when R % 4 == 0 and the arrays are 16-byte aligned, else float2 (even R, 8 bytes)
-bool post_vec4(int R, const void* T, const void* F, const void* out) {
-  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  return R % 4 == 0 && R <= 128 && al(T) && al(F) && al(out);
-}
+// the vector type by the rank alone: float4 when R % 4 == 0, else float2 (even R)
+bool post_vec4(int R) { return R % 4 == 0; }
+int post_bb(int R) { return post_vec4(R) ? kPostBB : kPostBB2; }
 }  // namespace
 
 bool post4_ok(int R, const void* T, const void* F, const void* out) {
-  if (post_vec4(R, T, F, out)) return true;
-  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; };
-  return R % 2 == 0 && R <= 64 && al(T) && al(F) && al(out);
+  const uintptr_t m = post_vec4(R) ? 15 : 7;
+  const auto al = [m](const void* p) { return (reinterpret_cast<uintptr_t>(p) & m) == 0; };
+  return (post_vec4(R) ? R <= 128 : R % 2 == 0 && R <= 64) && al(T) && al(F) && al(out);
 }
 
 cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               float* out, cudaStream_t st) {
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(Ia, 65535));
-  if (post_vec4(R, T, F, out)) {
+  if (post_vec4(R)) {
     const int Q = R / 4;
     prefer_shared_carveout<k_post_fast4>();
     k_post_fast4<<<blocks, 32 * Q, 0, st>>>(reinterpret_cast<const float4*>(T), Ia, Ib, Q,
@@ -680,13 +682,13 @@ int post_slow4_splits(int64_t Ia, int64_t Ib, int R, int num_sms) {
   // As many splits of the reduced range as keep every CTA resident at once: a second,
   // partial wave of CTAs would take as long as the first (at 1000 x 1000, R = 32: 320 CTAs
   // at 2 per SM were 1.05 waves and took twice the time of 288).
-  const int64_t bblocks = (Ib + kPostBB - 1) / kPostBB;
+  const int64_t bblocks = post_slow4_blocks(Ib, R);
   int per_sm = 0;
   const cudaError_t oe =
       R % 4 == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_slow4,
                                                                  kPostBB * (R / 4), 0)
                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_slowv<float2>,
-                                                                 kPostBB * (R / 2), 0);
+                                                                 kPostBB2 * (R / 2), 0);
   if (oe != cudaSuccess || per_sm < 1) {
     (void)cudaGetLastError();
     per_sm = 1;
@@ -696,13 +698,13 @@ int post_slow4_splits(int64_t Ia, int64_t Ib, int R, int num_sms) {
   return static_cast<int>(std::min<int64_t>(splits, 64));
 }
 
-int64_t post_slow4_blocks(int64_t Ib) { return (Ib + kPostBB - 1) / kPostBB; }
+int64_t post_slow4_blocks(int64_t Ib, int R) { return (Ib + post_bb(R) - 1) / post_bb(R); }
 
 cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               int splits, float* partial, unsigned* count, float* out,
                               cudaStream_t st) {
-  dim3 grid(static_cast<unsigned>(post_slow4_blocks(Ib)), static_cast<unsigned>(splits));
-  if (post_vec4(R, T, F, out) && (reinterpret_cast<uintptr_t>(partial) & 15) == 0) {
+  dim3 grid(static_cast<unsigned>(post_slow4_blocks(Ib, R)), static_cast<unsigned>(splits));
+  if (post_vec4(R)) {
     const int Q = R / 4;
     prefer_shared_carveout<k_post_slow4>();
     k_post_slow4<<<grid, kPostBB * Q, 0, st>>>(
@@ -711,7 +713,7 @@ cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, con
   } else {
     const int Q = R / 2;
     prefer_shared_carveout<k_post_slowv<float2>>();
-    k_post_slowv<float2><<<grid, kPostBB * Q, 0, st>>>(
+    k_post_slowv<float2><<<grid, kPostBB2 * Q, 0, st>>>(
         reinterpret_cast<const float2*>(T), Ia, Ib, Q, reinterpret_cast<const float2*>(F),
         splits, reinterpret_cast<float2*>(partial), count, reinterpret_cast<float2*>(out));
   }

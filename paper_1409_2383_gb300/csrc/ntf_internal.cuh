@@ -166,7 +166,7 @@ cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, con
 cudaError_t launch_post_part(const float* part, int64_t Ia, int64_t Ib, int R, float* out,
                              cudaStream_t st);
 int post_slow4_splits(int64_t Ia, int64_t Ib, int R, int num_sms);
-int64_t post_slow4_blocks(int64_t Ib);
+int64_t post_slow4_blocks(int64_t Ib, int R);
 cudaError_t launch_post_slow4(const float* T, int64_t Ia, int64_t Ib, int R, const float* F,
                               int splits, float* partial, unsigned* count, float* out,
                               cudaStream_t st);
