@@ -77,26 +77,36 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
   p->K_pad = pad64(K);
   const int stage_k = f32 ? 32 : 64;
   const int64_t tiles = (M + 127) / 128;
-  // Split the contraction range only when there are fewer tiles than SMs; a chunk keeps at
-  // least 4 stages and is a multiple of 64 long.
-  int64_t chunks = 1;
+  // Persistent CTAs, one per SM, but two SMs fewer than the GPU has: the sweep runs small
+  // kernels (coefficient systems, reductions) on other streams at the same time, and a CTA
+  // that cannot become resident until such a kernel leaves its SM would hold back its whole
+  // share of tiles.
+  const int64_t ctas = num_sms > 8 ? num_sms - 2 : num_sms;
+  // Fewer tiles than SMs: split the contraction range into chunks (multiples of 64, at least
+  // 4 stages long) so that the work items, tiles x chunks, fill the grid's rounds evenly.  The
+  // split minimises the contraction length that the busiest CTA covers, rounds x (chunk
+  // length + 512 for an item's start-up), over at most 16 rounds.
+  int64_t chunks = 1, len = pad64(K);
   if (tiles < num_sms) {
-    chunks = (num_sms + tiles - 1) / tiles;
-    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, K / 256));
+    int64_t best = -1;
+    const int64_t cmax = std::max<int64_t>(1, std::min<int64_t>(K / 256, 16 * ctas / tiles));
+    for (int64_t c = 1; c <= cmax; ++c) {
+      const int64_t l = pad64((K + c - 1) / c);
+      const int64_t ce = (K + l - 1) / l;
+      const int64_t cost = (tiles * ce + ctas - 1) / ctas * (l + 512);
+      if (best < 0 || cost < best) {
+        best = cost;
+        chunks = ce;
+        len = l;
+      }
+    }
   }
-  int64_t len = pad64((K + chunks - 1) / chunks);
-  chunks = (K + len - 1) / len;
   p->args.M = M;
   p->args.K = K;
   p->args.chunk_len = len;
   p->args.R = R;
   p->args.tiles = static_cast<int>(tiles);
   p->args.chunks = static_cast<int>(chunks);
-  // Persistent CTAs, one per SM, but two SMs fewer than the GPU has: the sweep runs small
-  // kernels (coefficient systems, reductions) on other streams at the same time, and a CTA
-  // that cannot become resident until such a kernel leaves its SM would hold back its whole
-  // share of tiles.
-  const int64_t ctas = num_sms > 8 ? num_sms - 2 : num_sms;
   p->grid = static_cast<int>(std::min<int64_t>(tiles * chunks, ctas));
   const CUtensorMapDataType t =
       f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;

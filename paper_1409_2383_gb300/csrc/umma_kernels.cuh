@@ -17,8 +17,11 @@
 //   FP32 storage: X = xh + xl and W = wh + wl with xh, wh = the value truncated to TF32
 //                 (10 stored mantissa bits) and xl, wl = the exact remainders; X W is formed
 //                 as xh wh + xh wl + xl wh (two kind::tf32 MMAs), dropping xl wl
-//                 (relative size 2^-22).  The split of X happens in shared memory between
-//                 the TMA load and the MMA (converter warps).
+//                 (relative size 2^-22).  A kind::tf32 MMA reads an FP32 operand by its
+//                 sign, exponent and 10 leading mantissa bits, so a tensor value serves as
+//                 its own xh: converter warps write xl beside the K-major tensor tile (and,
+//                 for GEMM-T, first transpose the tile in place), between the TMA load and
+//                 the MMA.
 //
 // CTA roles (persistent: one CTA per SM walks the (tile, K-chunk) work items):
 //   warps 0-3  epilogue: TMEM -> registers -> global, warp w owns TMEM lanes 32w..32w+31
@@ -26,7 +29,7 @@
 //   warp 5     MMA issuer (one thread): tcgen05.mma into a double-buffered accumulator; a
 //              tile's contraction range is accumulated in segments of 8 stages, each in a
 //              fresh accumulator that the epilogue adds into FP32 registers
-//   warps 6-9  (FP32 only) converters: split X into hi/lo operand tiles
+//   warps 6-9  (FP32 only) converters: the lo operand tile xl (GEMM-T: and the transpose)
 // Stages form a ring guarded by mbarriers (full: TMA bytes landed; ready: converted; empty:
 // the MMAs reading the stage completed).  Every wait is bounded: on timeout the kernel sets
 // the timeout bit in *err, every role leaves its loop, outstanding copies and MMAs are
@@ -52,7 +55,7 @@ struct Cfg {
   static_assert(!(kWRes && kF32), "resident tables are for BF16 storage");
   static constexpr int kStageK = kF32 ? 32 : 64;   // K per stage: 128 bytes of one row
   static constexpr int kSplits = kF32 ? 2 : 3;     // W parts
-  static constexpr int kABytes = kTileM * 128;     // operand tile (hi part for FP32)
+  static constexpr int kABytes = kTileM * 128;     // tensor tile (the hi part for FP32)
   static constexpr int kLoBytes = kF32 ? kTileM * 128 : 0;
   static constexpr int kWBlockBytes = kSplits * kN * 128;            // W rows of one K block
   static constexpr int kWBytes = kWRes ? 0 : kWBlockBytes;           // W per stage
@@ -229,10 +232,10 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// TF32 split: hi keeps sign, exponent and the 10 leading mantissa bits; lo = x - hi exactly.
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  lo = x - hi;
+// TF32 split remainder: hi = x with its 13 trailing mantissa bits cleared (sign, exponent and
+// the 10 leading mantissa bits, what a kind::tf32 MMA reads of x); lo = x - hi, exact.
+__device__ __forceinline__ float tf32_rem(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
 // Sums over the 32 lanes of a warp of x[0..31], one column per lane: lane l returns the sum
@@ -629,26 +632,22 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
         }
         uint8_t* st = stage_ptr(slot);
         if constexpr (!kT) {
-          // in place: the hi part overwrites X, the lo part goes to the same offset of the
-          // lo tile, so both keep the swizzled layout the TMA wrote
+          // the tile stays as the hi part; the lo part goes to the same offset of the lo
+          // tile, so it keeps the swizzled layout the TMA wrote
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int off = (t + 128 * i) * 16;
             const float4 x = *reinterpret_cast<const float4*>(st + kOffA + off);
-            float4 h, l;
-            split_tf32(x.x, h.x, l.x);
-            split_tf32(x.y, h.y, l.y);
-            split_tf32(x.z, h.z, l.z);
-            split_tf32(x.w, h.w, l.w);
-            *reinterpret_cast<float4*>(st + kOffA + off) = h;
-            *reinterpret_cast<float4*>(st + kOffLo + off) = l;
+            *reinterpret_cast<float4*>(st + kOffLo + off) =
+                make_float4(tf32_rem(x.x), tf32_rem(x.y), tf32_rem(x.z), tf32_rem(x.w));
           }
         } else {
           // transpose in place: thread m reads column m of the raw rows [32 K][128 M] (plain
           // layout) into registers; once all four converter warps have read the tile (cread:
           // one arrival per warp, a bounded wait) the K-major operand rows overwrite it, 128
           // bytes (32 K values) per M row, 16-byte chunk c at chunk position c ^ (m & 7) (the
-          // 128-byte swizzle), and the lo parts go to the lo tile.  (A separate raw buffer
+          // 128-byte swizzle): the values themselves (the hi parts) to the operand tile, the
+          // lo parts to the lo tile.  (A separate raw buffer
           // would cost two of the five stages.)
           const float* raw = reinterpret_cast<const float*>(st + kOffA);
           const int m = t;
@@ -664,14 +663,11 @@ __global__ void __maxnreg__(kUmmaMaxRegs<kN>)
           }
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            float4 h, l;
-            split_tf32(xv[4 * c + 0], h.x, l.x);
-            split_tf32(xv[4 * c + 1], h.y, l.y);
-            split_tf32(xv[4 * c + 2], h.z, l.z);
-            split_tf32(xv[4 * c + 3], h.w, l.w);
+            const float4 h = make_float4(xv[4 * c], xv[4 * c + 1], xv[4 * c + 2], xv[4 * c + 3]);
             const int off = m * 128 + ((c ^ (m & 7)) << 4);
             *reinterpret_cast<float4*>(st + kOffA + off) = h;
-            *reinterpret_cast<float4*>(st + kOffLo + off) = l;
+            *reinterpret_cast<float4*>(st + kOffLo + off) =
+                make_float4(tf32_rem(h.x), tf32_rem(h.y), tf32_rem(h.z), tf32_rem(h.w));
           }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
