@@ -356,7 +356,11 @@ def fit_target(X, R: int, init, max_outer: int) -> float:
 def _roofline_of(prof, storage: str, workload: str) -> dict:
     """Live HBM roofline of the dominant contraction (more device time) from a profile."""
     k = 0 if prof["contraction_ms"][0] >= prof["contraction_ms"][1] else 1
-    names = ["k_umma<0,...> (X * KR_right, tcgen05)", "k_umma<1,...> (X^T * KR_left, tcgen05)"]
+    # (FP32 storage: the second contraction runs as a row-major product on the context's
+    # transposed copy of the tensor, the default where the copy fits)
+    names = ["k_umma<0,...> (X * KR_right, tcgen05)",
+             "k_umma<0,...> (X^T * KR_left on the transposed tensor copy, tcgen05)"
+             if storage == "fp32" else "k_umma<1,...> (X^T * KR_left, tcgen05)"]
     kernel_ids = [f"k_umma_n_{storage}", f"k_umma_t_{storage}"]
     avg_ms = prof["contraction_ms"][k] / max(prof["contractions"][k], 1)
     bytes_ = prof["contraction_bytes"][k]

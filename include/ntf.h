@@ -103,7 +103,15 @@ typedef struct {
    * R <= 32 and I_2 >= 32.  0 (default): where it applies and the intermediate is at least
    * half the L2 size; 1: wherever it applies; -1: never.  Results equal to rounding. */
   int fuse_level;
-  int reserved;      /* 0 */
+  /* A transposed copy of the tensor kept on the device (X[P, Q] stored as [Q, P]), made once
+   * by ntf_create (numel x element-size bytes of device memory, owned by the context), on
+   * which the tensor-core engine runs the second contraction X^T W (Sec. IV-A) as a row-major
+   * product: for FP32 storage the operand split then needs no transpose in shared memory.
+   * Applies to the tensor-core engine when the tensor's leading extent P is a multiple of 16
+   * bytes.  0 (default): FP32 storage, when the copy takes at most half the free device
+   * memory; 1: FP32 or BF16 storage, wherever it applies; -1: never.  Results are equal to
+   * rounding either way (same products, same chunking rule). */
+  int tensor_copy;
 } ntf_params;
 
 /* Per-factor residuals of one update (Sec. IV-C), all Frobenius norms, and the KKT measures

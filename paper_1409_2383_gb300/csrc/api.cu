@@ -37,6 +37,7 @@ struct ntf_ctx {
   ntf_params prm{};
   GemmPlan pn{}, pt{};
   ntf::UmmaPlan un{}, ut{};      // tensor-core plans of the two contractions (on: used)
+  void* Xt = nullptr;            // the transposed copy of the tensor (params.tensor_copy)
   int post_split_left = 1, post_split_right = 1;
   int post4_split_left = 1, post4_split_right = 1;   // vectorised second level (R % 4 == 0)
   unsigned* post_count = nullptr;  // per-b-block counters of the vectorised slow level
@@ -177,6 +178,8 @@ ntf_status check_params(const ntf_params* p) {
     return fail(NTF_ERR_INVALID_ARG, "unknown contraction engine %d", p->contraction);
   if (p->fuse_level < -1 || p->fuse_level > 1)
     return fail(NTF_ERR_INVALID_ARG, "fuse_level must be -1, 0 or 1, not %d", p->fuse_level);
+  if (p->tensor_copy < -1 || p->tensor_copy > 1)
+    return fail(NTF_ERR_INVALID_ARG, "tensor_copy must be -1, 0 or 1, not %d", p->tensor_copy);
   if (!(p->kkt_dual_tol >= 0.0) || !(p->kkt_comp_tol >= 0.0))
     return fail(NTF_ERR_INVALID_ARG, "negative KKT tolerance");
   return NTF_OK;
@@ -658,6 +661,7 @@ void free_ctx(ntf_ctx* c) {
     if (e) cudaEventDestroy(e);
   cudaFree(c->arena[0]);
   cudaFree(c->arena[1]);
+  cudaFree(c->Xt);
   if (c->h_ctrl) pinned_release(c->h_ctrl);
   for (cudaEvent_t e : c->ev_sweep)
     if (e) cudaEventDestroy(e);
@@ -693,7 +697,7 @@ void ntf_default_params(ntf_params* p, int paper_mode) {
   p->kkt_dual_tol = 0.0;
   p->kkt_comp_tol = 0.0;
   p->fuse_level = 0;
-  p->reserved = 0;
+  p->tensor_copy = 0;
 }
 
 const char* ntf_status_string(ntf_status s) {
@@ -876,8 +880,34 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     if (e == cudaSuccess) {
       const bool okn = ntf::umma_plan(&c->un, false, dtype, d_tensor, c->P_R, c->Q_R, R, c->Wu,
                                       c->num_sms);
-      const bool okt = ntf::umma_plan(&c->ut, true, dtype, d_tensor, c->P_L, c->Q_L, R, c->Wu_b,
-                                      c->num_sms);
+      // the second contraction X[P_L, Q_L]^T W: on the transposed copy [Q_L, P_L] (a K-major
+      // product, params.tensor_copy) when there is one, else on X with M-contiguous tiles
+      const int64_t es = dtype == NTF_BF16 ? 2 : 4;
+      const bool copy = (p->tensor_copy == 1 || (p->tensor_copy == 0 && dtype != NTF_BF16)) &&
+                        (c->P_L * es) % 16 == 0 && R <= 64;
+      if (copy) {
+        size_t free_b = 0, total_b = 0;
+        const size_t bytes = static_cast<size_t>(c->numel * es);
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+            (p->tensor_copy == 1 || bytes <= free_b / 2)) {
+          if (cudaMalloc(&c->Xt, bytes) != cudaSuccess) {
+            cudaGetLastError();  // no room: the contraction runs on X
+            c->Xt = nullptr;
+          }
+        }
+        if (c->Xt)
+          e = ntf::launch_transpose(d_tensor, static_cast<int>(es), c->P_L, c->Q_L, c->Xt, c->st);
+      }
+      const bool okt = e == cudaSuccess &&
+                       (c->Xt ? ntf::umma_plan(&c->ut, false, dtype, c->Xt, c->Q_L, c->P_L, R,
+                                               c->Wu_b, c->num_sms)
+                              : ntf::umma_plan(&c->ut, true, dtype, d_tensor, c->P_L, c->Q_L, R,
+                                               c->Wu_b, c->num_sms));
+      if (!okt && c->Xt && e == cudaSuccess) {
+        e = cudaStreamSynchronize(c->st);
+        cudaFree(c->Xt);
+        c->Xt = nullptr;
+      }
       if (p->contraction == NTF_CONTRACT_TENSOR && !(okn && okt)) {
         free_ctx(c);
         return fail(NTF_ERR_UNSUPPORTED,

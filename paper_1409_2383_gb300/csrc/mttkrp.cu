@@ -602,6 +602,46 @@ cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R,
   return detail::gemm_t_typed(static_cast<const float*>(X), P, Q, R, W, plan, out, st);
 }
 
+// Transposed copy of the tensor, y[Q, P] = x[P, Q]^T: 32 x 32 tiles through shared memory
+// (rows of x read and rows of y written 32 elements at a time), tiles walked by a
+// grid-stride loop.  Runs once per context.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ x, int64_t P, int64_t Q,
+                                                   T* __restrict__ y) {
+  __shared__ T tile[32][33];
+  const int64_t tp = (P + 31) / 32, tq = (Q + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < tp * tq; t += gridDim.x) {
+    const int64_t p0 = (t / tq) * 32, q0 = (t % tq) * 32;
+#pragma unroll
+    for (int i = ty; i < 32; i += 8)
+      if (p0 + i < P && q0 + tx < Q) tile[i][tx] = x[(p0 + i) * Q + q0 + tx];
+    __syncthreads();
+#pragma unroll
+    for (int i = ty; i < 32; i += 8)
+      if (q0 + i < Q && p0 + tx < P) y[(q0 + i) * P + p0 + tx] = tile[tx][i];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* y,
+                             cudaStream_t st) {
+  if (P < 1 || Q < 1 || (es != 2 && es != 4)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = ((P + 31) / 32) * ((Q + 31) / 32);
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(tiles, int64_t{8} * sms));
+  if (es == 4)
+    k_transpose<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(x), P, Q,
+                                                static_cast<float*>(y));
+  else
+    k_transpose<uint16_t><<<blocks, 256, 0, st>>>(static_cast<const uint16_t*>(x), P, Q,
+                                                   static_cast<uint16_t*>(y));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float* out,
                               cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);

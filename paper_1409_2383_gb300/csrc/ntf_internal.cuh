@@ -146,6 +146,10 @@ cudaError_t launch_gemm_n(const void* X, int dtype, int64_t P, int64_t Q, int R,
 cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R, const float* W,
                           const GemmPlan& plan, float* out_or_partial, cudaStream_t st);
 // out[n] = sum_s partial[s * n + i]
+// y[Q, P] = x[P, Q]^T for elements of es = 2 or 4 bytes (the transposed tensor copy).
+cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* y,
+                             cudaStream_t st);
+
 cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float* out,
                               cudaStream_t st);
 // T[Ia, Ib, R]:  fast: out[a, r] = sum_b T[a, b, r] F[b, r];  slow: out[b, r] = sum_a T F[a, r]

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("tau_decr", ctypes.c_double), ("eps_abs", ctypes.c_double),
                 ("eps_rel", ctypes.c_double), ("contraction", ctypes.c_int),
                 ("kkt_dual_tol", ctypes.c_double), ("kkt_comp_tol", ctypes.c_double),
-                ("fuse_level", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("fuse_level", ctypes.c_int), ("tensor_copy", ctypes.c_int)]
 
 
 class TraceEntry(ctypes.Structure):

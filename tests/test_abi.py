@@ -84,7 +84,8 @@ def test_create_rejects_bad_params(lib):
     h = ctypes.c_void_p()
     dims = (ctypes.c_int64 * 3)(4, 5, 6)
     for bad in (dict(inner_iters=0), dict(rho0=-1.0), dict(mu=1.0, rho_policy=0),
-                dict(kr_source=3), dict(rho_policy=9), dict(eps_abs=-1.0)):
+                dict(kr_source=3), dict(rho_policy=9), dict(eps_abs=-1.0),
+                dict(fuse_level=2), dict(tensor_copy=-2)):
         p = ntf.default_params(**bad)
         assert lib.ntf_create(ctypes.byref(h), 3, dims, 3, 0, 16, ctypes.byref(p), None) == 1
 

@@ -123,6 +123,49 @@ def test_mttkrp_with_the_fused_second_level(ntf, dims, R, storage):
     assert abs(errs[1] - errs[-1]) <= 1e-5 * errs[-1], errs
 
 
+@pytest.mark.parametrize("dims,R", [((24, 40, 36), 7), ((100, 120, 140), 32),
+                                    ((20, 24, 16, 50), 16), ((64, 80, 48), 2),
+                                    ((72, 30, 40), 64), ((13, 17, 11), 5), ((128, 96, 200), 16)])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
+    """The second contraction X^T W on the context's transposed tensor copy (tensor_copy = 1:
+    a row-major tensor-core product) and on the tensor itself (-1): every mode against the
+    oracle at the MTTKRP tolerance and the two against each other; the copy takes its device
+    memory where the leading extent is a 16-byte multiple (not for 13 x 17 x 11; checked for
+    tensors of at least 2 MB, which the runtime does not place in pages it already holds);
+    short runs agree."""
+    X, fs = _problem(dims, R, seed=11 * R + len(dims), signed=False)
+    Xt = torch.as_tensor(X).to(torch.bfloat16).cuda() if storage == "bf16" else cuda(X)
+    Xref = torch.as_tensor(X).to(torch.bfloat16).double().numpy() if storage == "bf16" \
+        else X.astype(np.float64)
+    Fd = [cuda(F) for F in fs]
+    es = 2 if storage == "bf16" else 4
+    lead = dims[0] if len(dims) == 3 else dims[0] * dims[1]
+    got, used = {}, {}
+    for tc in (1, -1):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        with ntf.Context(Xt, R, ntf.default_params(tensor_copy=tc)) as ctx:
+            used[tc] = free0 - torch.cuda.mem_get_info()[0]
+            got[tc] = [host(ctx.mttkrp(n, Fd)) for n in range(len(dims))]
+        for n in range(len(dims)):
+            want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], n)
+            assert rel(got[tc][n], want) <= TOL, (tc, n, rel(got[tc][n], want))
+    for n in range(len(dims)):
+        assert rel(got[1][n], got[-1][n]) <= 4 * TOL, n
+    copied = (lead * es) % 16 == 0
+    if X.size * es >= 2 << 20:
+        assert (used[1] - used[-1] >= X.size * es) == copied, (used, X.size * es)
+    init = [np.random.default_rng(50 + n).random((d, R)).astype(np.float32)
+            for n, d in enumerate(dims)]
+    errs = {}
+    for tc in (1, -1):
+        with ntf.Context(Xt, R, ntf.default_params(tensor_copy=tc)) as ctx:
+            A, At, Y = [cuda(F) for F in init], [cuda(F) for F in init], ntf.zeros_state(dims, R)
+            errs[tc] = ctx.run(A, At, Y, 4)["rel_err"]
+    assert abs(errs[1] - errs[-1]) <= 1e-5 * errs[-1], errs
+
+
 @pytest.mark.parametrize("n", [1 << 20, 1000003])
 def test_to_bf16_from_pinned_host_memory(ntf, n):
     """The conversion reads page-locked host memory directly (copy and conversion in one
