@@ -328,12 +328,18 @@ def train_network(name: str, args):
     return net, rep
 
 
+# ntf_params.tensor_copy of every context the bench makes (--tensor-copy)
+TENSOR_COPY = 0
+
+
 def _params(kkt=None):
     from paper_1409_2383_gb300 import ntf
     if kkt is None:
-        return ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+        return ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0,
+                                  tensor_copy=TENSOR_COPY)
     return ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0,
-                              kkt_dual_tol=kkt[0], kkt_comp_tol=kkt[1])
+                              kkt_dual_tol=kkt[0], kkt_comp_tol=kkt[1],
+                              tensor_copy=TENSOR_COPY)
 
 
 def fit_target(X, R: int, init, max_outer: int) -> float:
@@ -356,11 +362,11 @@ def fit_target(X, R: int, init, max_outer: int) -> float:
 def _roofline_of(prof, storage: str, workload: str) -> dict:
     """Live HBM roofline of the dominant contraction (more device time) from a profile."""
     k = 0 if prof["contraction_ms"][0] >= prof["contraction_ms"][1] else 1
-    # (FP32 storage: the second contraction runs as a row-major product on the context's
-    # transposed copy of the tensor, the default where the copy fits)
+    # (the second contraction runs as a row-major product on the context's transposed copy
+    # of the tensor where the context made one)
     names = ["k_umma<0,...> (X * KR_right, tcgen05)",
              "k_umma<0,...> (X^T * KR_left on the transposed tensor copy, tcgen05)"
-             if storage == "fp32" else "k_umma<1,...> (X^T * KR_left, tcgen05)"]
+             if prof.get("tensor_copy_bytes") else "k_umma<1,...> (X^T * KR_left, tcgen05)"]
     kernel_ids = [f"k_umma_n_{storage}", f"k_umma_t_{storage}"]
     avg_ms = prof["contraction_ms"][k] / max(prof["contractions"][k], 1)
     bytes_ = prof["contraction_bytes"][k]
@@ -673,7 +679,8 @@ def run_kernel_case(args):
     engine = {"auto": ntf.NTF_CONTRACT_AUTO, "tensor": ntf.NTF_CONTRACT_TENSOR,
               "simt": ntf.NTF_CONTRACT_SIMT}[args.engine]
     times = {0: [], len(dims) - 1: []}
-    with ntf.Context(X, args.rank, ntf.default_params(contraction=engine)) as ctx:
+    with ntf.Context(X, args.rank,
+                     ntf.default_params(contraction=engine, tensor_copy=TENSOR_COPY)) as ctx:
         for it in range(args.warmup + args.steps):
             for n in (0, len(dims) - 1):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -751,7 +758,7 @@ def run_sweep_case(args):
     Xd, init = device_workload(args.workload, 0)
     if args.storage == "bf16":
         Xd = ntf.to_bf16(Xd)
-    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0)
+    p = ntf.default_params(paper_mode=False, eps_abs=0.0, eps_rel=0.0, tensor_copy=TENSOR_COPY)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         A = [f.clone() for f in init]
@@ -898,10 +905,15 @@ def main():
                          "each)")
     ap.add_argument("--study-cases", default="",
                     help="with --study: comma-separated indices of the scenarios to run")
+    ap.add_argument("--tensor-copy", type=int, default=0, choices=[-1, 0, 1],
+                    help="ntf_params.tensor_copy: the second contraction on a transposed copy "
+                         "of the tensor (0: FP32 storage where it fits, 1: also BF16, -1: never)")
     ap.add_argument("--realizations", type=int, default=10)
     ap.add_argument("--max-restarts", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global TENSOR_COPY
+    TENSOR_COPY = args.tensor_copy
     if args.study:
         run_study(args)
     elif args.kernel_case:

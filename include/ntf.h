@@ -108,9 +108,11 @@ typedef struct {
    * which the tensor-core engine runs the second contraction X^T W (Sec. IV-A) as a row-major
    * product: for FP32 storage the operand split then needs no transpose in shared memory.
    * Applies to the tensor-core engine when the tensor's leading extent P is a multiple of 16
-   * bytes.  0 (default): FP32 storage, when the copy takes at most half the free device
-   * memory; 1: FP32 or BF16 storage, wherever it applies; -1: never.  Results are equal to
-   * rounding either way (same products, same chunking rule). */
+   * bytes.  0 (default): where it applies and the copy takes at most half the free device
+   * memory, for FP32 storage, and for BF16 storage when the product is not cut into chunks
+   * along P, the rank is 17..32 and the Khatri-Rao table is streamed (P > 448): the cases
+   * where the row-major product measured faster than the M-contiguous one; 1: wherever it
+   * applies; -1: never.  Results are equal to rounding either way. */
   int tensor_copy;
 } ntf_params;
 
@@ -265,6 +267,8 @@ typedef struct {
   double contraction_bytes[2];/* tensor bytes each such launch reads (algorithmic)      */
   int64_t ws_rows_considered; /* warm start: rows offered a prediction                  */
   int64_t ws_rows_accepted;   /* warm start: rows whose prediction the judge kept       */
+  int64_t tensor_copy_bytes;  /* device bytes of the transposed tensor copy (0: none;
+                               * params.tensor_copy), on which [1] then runs             */
 } ntf_profile;
 
 ntf_status ntf_profile_enable(ntf_ctx* ctx, int enable);

@@ -883,8 +883,17 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
       // the second contraction X[P_L, Q_L]^T W: on the transposed copy [Q_L, P_L] (a K-major
       // product, params.tensor_copy) when there is one, else on X with M-contiguous tiles
       const int64_t es = dtype == NTF_BF16 ? 2 : 4;
-      const bool copy = (p->tensor_copy == 1 || (p->tensor_copy == 0 && dtype != NTF_BF16)) &&
-                        (c->P_L * es) % 16 == 0 && R <= 64;
+      const bool copy_ok = (c->P_L * es) % 16 == 0 && R <= 64;
+      bool copy = copy_ok && (p->tensor_copy == 1 || (p->tensor_copy == 0 && dtype != NTF_BF16));
+      if (copy_ok && p->tensor_copy == 0 && dtype == NTF_BF16) {
+        // BF16: the row-major product on the copy is the faster one for a single-chunk
+        // contraction with N = 32 and the table streamed through the stages; the
+        // M-contiguous one is faster at N = 64 and when the range is cut into chunks
+        ntf::UmmaPlan probe{};
+        copy = ntf::umma_plan(&probe, true, dtype, d_tensor, c->P_L, c->Q_L, R, c->Wu_b,
+                              c->num_sms) &&
+               probe.N == 32 && probe.args.chunks == 1 && !probe.wres;
+      }
       if (copy) {
         size_t free_b = 0, total_b = 0;
         const size_t bytes = static_cast<size_t>(c->numel * es);
@@ -1188,6 +1197,7 @@ ntf_status ntf_profile_get(ntf_ctx* c, ntf_profile* out) {
   out->kernel_launches = c->launches;
   out->ws_rows_considered = static_cast<int64_t>(c->h_ctrl->ws_rows[0]);
   out->ws_rows_accepted = static_cast<int64_t>(c->h_ctrl->ws_rows[1]);
+  out->tensor_copy_bytes = c->Xt ? c->numel * (c->dtype == NTF_BF16 ? 2 : 4) : 0;
   return NTF_OK;
 }
 

@@ -306,11 +306,13 @@ __device__ __forceinline__ void post_group(const Args& a, float (&v)[kN], int ti
 // two warps in a scheduler's 16384 registers.  At N = 64 the uncapped kernel takes 202
 // registers (13312 of a scheduler's registers for two warps) and nothing fits; capped at 168
 // (10752) the reductions and second tree levels (80-84 registers) do, for a few spilled bytes.
-template <int kN>
-constexpr int kUmmaMaxRegs = kN > 32 ? 168 : 144;
+// FP32 (ten warps): capped at 112 at N <= 32, so that two warps of a second tree level (84
+// registers) fit beside the three contraction warps a scheduler holds.
+template <int kN, bool kF32>
+constexpr int kUmmaMaxRegs = kN > 32 ? 168 : kF32 ? 112 : 144;
 
 template <bool kT, bool kF32, int kN, bool kWRes>
-__global__ void __maxnreg__(kUmmaMaxRegs<kN>)
+__global__ void __maxnreg__((kUmmaMaxRegs<kN, kF32>))
     k_umma(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw,
            Args a) {
   using C = Cfg<kT, kF32, kN, kWRes>;

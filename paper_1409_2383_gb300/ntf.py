@@ -69,7 +69,8 @@ class Profile(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("contractions", ctypes.c_int64 * 2), ("contraction_ms", ctypes.c_double * 2),
                 ("contraction_bytes", ctypes.c_double * 2),
-                ("ws_rows_considered", ctypes.c_int64), ("ws_rows_accepted", ctypes.c_int64)]
+                ("ws_rows_considered", ctypes.c_int64), ("ws_rows_accepted", ctypes.c_int64),
+                ("tensor_copy_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -389,7 +390,8 @@ class Context:
                 "contractions": list(p.contractions), "contraction_ms": list(p.contraction_ms),
                 "contraction_bytes": list(p.contraction_bytes),
                 "ws_rows_considered": p.ws_rows_considered,
-                "ws_rows_accepted": p.ws_rows_accepted}
+                "ws_rows_accepted": p.ws_rows_accepted,
+                "tensor_copy_bytes": p.tensor_copy_bytes}
 
     def trace_enable(self, enable: bool = True) -> None:
         _check(lib().ntf_trace_enable(self._h, 1 if enable else 0))

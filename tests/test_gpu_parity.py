@@ -130,9 +130,8 @@ def test_mttkrp_with_the_fused_second_level(ntf, dims, R, storage):
 def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
     """The second contraction X^T W on the context's transposed tensor copy (tensor_copy = 1:
     a row-major tensor-core product) and on the tensor itself (-1): every mode against the
-    oracle at the MTTKRP tolerance and the two against each other; the copy takes its device
-    memory where the leading extent is a 16-byte multiple (not for 13 x 17 x 11; checked for
-    tensors of at least 2 MB, which the runtime does not place in pages it already holds);
+    oracle at the MTTKRP tolerance and the two against each other; the copy is made where the
+    leading extent is a 16-byte multiple (not for 13 x 17 x 11), as the profile reports;
     short runs agree."""
     X, fs = _problem(dims, R, seed=11 * R + len(dims), signed=False)
     Xt = torch.as_tensor(X).to(torch.bfloat16).cuda() if storage == "bf16" else cuda(X)
@@ -143,10 +142,8 @@ def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
     lead = dims[0] if len(dims) == 3 else dims[0] * dims[1]
     got, used = {}, {}
     for tc in (1, -1):
-        torch.cuda.synchronize()
-        free0 = torch.cuda.mem_get_info()[0]
         with ntf.Context(Xt, R, ntf.default_params(tensor_copy=tc)) as ctx:
-            used[tc] = free0 - torch.cuda.mem_get_info()[0]
+            used[tc] = ctx.profile_get()["tensor_copy_bytes"]
             got[tc] = [host(ctx.mttkrp(n, Fd)) for n in range(len(dims))]
         for n in range(len(dims)):
             want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], n)
@@ -154,8 +151,7 @@ def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
     for n in range(len(dims)):
         assert rel(got[1][n], got[-1][n]) <= 4 * TOL, n
     copied = (lead * es) % 16 == 0
-    if X.size * es >= 2 << 20:
-        assert (used[1] - used[-1] >= X.size * es) == copied, (used, X.size * es)
+    assert used == {1: X.size * es if copied else 0, -1: 0}, used
     init = [np.random.default_rng(50 + n).random((d, R)).astype(np.float32)
             for n, d in enumerate(dims)]
     errs = {}
@@ -164,6 +160,31 @@ def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
             A, At, Y = [cuda(F) for F in init], [cuda(F) for F in init], ntf.zeros_state(dims, R)
             errs[tc] = ctx.run(A, At, Y, 4)["rel_err"]
     assert abs(errs[1] - errs[-1]) <= 1e-5 * errs[-1], errs
+
+
+@pytest.mark.parametrize("dims,R,storage,copied", [
+    ((512, 160, 128), 32, "bf16", True),    # one chunk, N = 32, streamed table
+    ((512, 160, 128), 16, "bf16", False),   # N = 16
+    ((512, 160, 128), 50, "bf16", False),   # N = 64
+    ((256, 160, 128), 20, "bf16", False),   # table resident in shared memory (P <= 448)
+    ((256, 160, 128), 20, "f32", True)])
+def test_default_tensor_copy_policy(ntf, dims, R, storage, copied):
+    """tensor_copy = 0 makes the transposed copy for FP32 storage and, for BF16, only where
+    the row-major product measured faster (one chunk, N = 32, streamed table); the mode-2
+    MTTKRP matches the oracle either way."""
+    X, fs = _problem(dims, R, seed=3 * R, signed=False)
+    Xt = torch.as_tensor(X).to(torch.bfloat16).cuda() if storage == "bf16" else cuda(X)
+    Xref = torch.as_tensor(X).to(torch.bfloat16).double().numpy() if storage == "bf16" \
+        else X.astype(np.float64)
+    es = 2 if storage == "bf16" else 4
+    used = {}
+    for tc in (0, -1):
+        with ntf.Context(Xt, R, ntf.default_params(tensor_copy=tc)) as ctx:
+            used[tc] = ctx.profile_get()["tensor_copy_bytes"]
+            M = host(ctx.mttkrp(2, [cuda(F) for F in fs]))
+        want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], 2)
+        assert rel(M, want) <= TOL, (tc, rel(M, want))
+    assert used == {0: X.size * es if copied else 0, -1: 0}, used
 
 
 @pytest.mark.parametrize("n", [1 << 20, 1000003])
