@@ -624,6 +624,37 @@ __global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ x, int6
   }
 }
 
+// The same for 16-bit elements with even P and Q: 64 x 64 tiles, rows of x read and rows of y
+// written as 32-bit pairs (128 bytes per warp access on both sides).
+__global__ void __launch_bounds__(256) k_transpose_pairs(const uint32_t* __restrict__ x,
+                                                         int64_t P, int64_t Q,
+                                                         uint32_t* __restrict__ y) {
+  __shared__ uint16_t tile[64][66];
+  const int64_t tp = (P + 63) / 64, tq = (Q + 63) / 64, Ph = P / 2, Qh = Q / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < tp * tq; t += gridDim.x) {
+    const int64_t p0 = (t / tq) * 64, q0 = (t % tq) * 64;
+#pragma unroll
+    for (int i = ty; i < 64; i += 8) {  // row p0 + i of x, columns q0 + 2 tx, q0 + 2 tx + 1
+      const int64_t qp = q0 / 2 + tx;
+      if (p0 + i < P && qp < Qh) {
+        const uint32_t v = x[(p0 + i) * Qh + qp];
+        tile[i][2 * tx] = static_cast<uint16_t>(v & 0xFFFFu);
+        tile[i][2 * tx + 1] = static_cast<uint16_t>(v >> 16);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = ty; i < 64; i += 8) {  // row q0 + i of y, columns p0 + 2 tx, p0 + 2 tx + 1
+      const int64_t pp = p0 / 2 + tx;
+      if (q0 + i < Q && pp < Ph)
+        y[(q0 + i) * Ph + pp] =
+            static_cast<uint32_t>(tile[2 * tx][i]) | (static_cast<uint32_t>(tile[2 * tx + 1][i]) << 16);
+    }
+    __syncthreads();
+  }
+}
+
 cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* y,
                              cudaStream_t st) {
   if (P < 1 || Q < 1 || (es != 2 && es != 4)) return cudaErrorInvalidValue;
@@ -631,6 +662,15 @@ cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* 
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  const bool pairs = es == 2 && P % 2 == 0 && Q % 2 == 0 &&
+                     reinterpret_cast<uintptr_t>(x) % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 4 == 0;
+  if (pairs) {
+    const int64_t tiles = ((P + 63) / 64) * ((Q + 63) / 64);
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(tiles, int64_t{8} * sms));
+    k_transpose_pairs<<<blocks, 256, 0, st>>>(static_cast<const uint32_t*>(x), P, Q,
+                                               static_cast<uint32_t*>(y));
+    return cudaGetLastError();
+  }
   const int64_t tiles = ((P + 31) / 32) * ((Q + 31) / 32);
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(tiles, int64_t{8} * sms));
   if (es == 4)

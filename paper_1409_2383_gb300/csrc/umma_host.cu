@@ -82,12 +82,13 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
   // that cannot become resident until such a kernel leaves its SM would hold back its whole
   // share of tiles.
   const int64_t ctas = num_sms > 8 ? num_sms - 2 : num_sms;
-  // Fewer tiles than SMs: split the contraction range into chunks (multiples of 64, at least
-  // 4 stages long) so that the work items, tiles x chunks, fill the grid's rounds evenly.  The
-  // split minimises the contraction length that the busiest CTA covers, rounds x (chunk
-  // length + 512 for an item's start-up), over at most 16 rounds.
+  // Fewer than four rounds of tiles: split the contraction range into chunks (multiples of
+  // 64, at least 4 stages long) so that the work items, tiles x chunks, fill the grid's
+  // rounds evenly.  The split minimises the contraction length that the busiest CTA covers,
+  // rounds x (chunk length + 512 for an item's start-up), over at most 16 rounds; one chunk
+  // where that is as good (4-way 200 x 200 x 200 x 50: 313 row tiles, 3 chunks, 939 items).
   int64_t chunks = 1, len = pad64(K);
-  if (tiles < num_sms) {
+  if (tiles < 4 * ctas) {
     int64_t best = -1;
     const int64_t cmax = std::max<int64_t>(1, std::min<int64_t>(K / 256, 16 * ctas / tiles));
     for (int64_t c = 1; c <= cmax; ++c) {

@@ -125,7 +125,8 @@ def test_mttkrp_with_the_fused_second_level(ntf, dims, R, storage):
 
 @pytest.mark.parametrize("dims,R", [((24, 40, 36), 7), ((100, 120, 140), 32),
                                     ((20, 24, 16, 50), 16), ((64, 80, 48), 2),
-                                    ((72, 30, 40), 64), ((13, 17, 11), 5), ((128, 96, 200), 16)])
+                                    ((72, 30, 40), 64), ((13, 17, 11), 5), ((128, 96, 200), 16),
+                                    ((16, 9, 7), 5)])   # odd trailing extent: element-wise copy
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
     """The second contraction X^T W on the context's transposed tensor copy (tensor_copy = 1:
