@@ -103,16 +103,22 @@ typedef struct {
    * R <= 32 and I_2 >= 32.  0 (default): where it applies and the intermediate is at least
    * half the L2 size; 1: wherever it applies; -1: never.  Results equal to rounding. */
   int fuse_level;
-  /* A transposed copy of the tensor kept on the device (X[P, Q] stored as [Q, P]), made once
-   * by ntf_create (numel x element-size bytes of device memory, owned by the context), on
-   * which the tensor-core engine runs the second contraction X^T W (Sec. IV-A) as a row-major
-   * product: for FP32 storage the operand split then needs no transpose in shared memory.
-   * Applies to the tensor-core engine when the tensor's leading extent P is a multiple of 16
-   * bytes.  0 (default): where it applies and the copy takes at most half the free device
-   * memory, for FP32 storage, and for BF16 storage when the product is not cut into chunks
-   * along P, the rank is 17..32 and the Khatri-Rao table is streamed (P > 448): the cases
-   * where the row-major product measured faster than the M-contiguous one; 1: wherever it
-   * applies; -1: never.  Results are equal to rounding either way. */
+  /* Copies of the tensor kept on the device for the tensor-core engine, made once by
+   * ntf_create and owned by the context (ntf_profile.tensor_copy_bytes reports their size):
+   * (a) a transposed copy (X[P, Q] stored as [Q, P], rows padded to 16-byte multiples), on
+   * which the second contraction X^T W (Sec. IV-A) runs as a row-major product: for FP32
+   * storage the operand split then needs no transpose in shared memory; (b) a copy of the
+   * first contraction's view with rows padded to 16-byte multiples, where the tensor's rows
+   * are not (the tensor-memory copies need that pitch).  A 3-way tensor whose trailing extent
+   * makes unaligned rows then uses the view X[I_1, I_2 I_3] for both contractions (the
+   * smaller padding).  0 (default): a copy is made where it takes at most half the free
+   * device memory: the padded copy and the transposed one wherever the tensor's own rows do
+   * not allow the tensor-core path, and the transposed one also for FP32 storage, and for
+   * BF16 storage when the product is not cut into chunks along P, the rank is 17..32 and the
+   * Khatri-Rao table is streamed (P > 448): the cases where the row-major product measured
+   * faster than the M-contiguous one; 1: both wherever they apply, any size; -1: never (the
+   * FMA kernels take what the tensor cores cannot).  Results are equal to rounding either
+   * way. */
   int tensor_copy;
 } ntf_params;
 

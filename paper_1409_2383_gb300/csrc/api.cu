@@ -38,6 +38,8 @@ struct ntf_ctx {
   GemmPlan pn{}, pt{};
   ntf::UmmaPlan un{}, ut{};      // tensor-core plans of the two contractions (on: used)
   void* Xt = nullptr;            // the transposed copy of the tensor (params.tensor_copy)
+  void* Xp = nullptr;            // the row-padded copy of X[P_R, Q_R] (params.tensor_copy)
+  int64_t copy_bytes = 0;        // device bytes of both copies
   int post_split_left = 1, post_split_right = 1;
   int post4_split_left = 1, post4_split_right = 1;   // vectorised second level (R % 4 == 0)
   unsigned* post_count = nullptr;  // per-b-block counters of the vectorised slow level
@@ -662,6 +664,7 @@ void free_ctx(ntf_ctx* c) {
   cudaFree(c->arena[0]);
   cudaFree(c->arena[1]);
   cudaFree(c->Xt);
+  cudaFree(c->Xp);
   if (c->h_ctrl) pinned_release(c->h_ctrl);
   for (cudaEvent_t e : c->ev_sweep)
     if (e) cudaEventDestroy(e);
@@ -760,13 +763,15 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     return fail(NTF_ERR_UNSUPPORTED, "tensor halves must each have < 2^31 entries");
   }
   // Skewed 3-way shapes (the paper's I x 50 x 50): when the rows of X[I_1 I_2, I_3] are not
-  // 16-byte multiples (TMA needs that pitch) but those of X[I_1, I_2 I_3] are, both passes use
-  // the second view (s_R = 1: factor 1 from X[I_1, I_2 I_3] KR(factors 2, 3), the others from
-  // its transpose as before), so that both contractions run on the tensor cores.
+  // 16-byte multiples (TMA needs that pitch), both passes use the second view (s_R = 1: factor
+  // 1 from X[I_1, I_2 I_3] KR(factors 2, 3), the others from its transpose as before): its
+  // rows are 16-byte multiples, or, when they are not either, a row-padded copy of it wastes
+  // a smaller fraction than one of X[I_1 I_2, I_3] (params.tensor_copy), so that both
+  // contractions run on the tensor cores.
   if (order == 3 && p->contraction != NTF_CONTRACT_SIMT) {
     const int64_t es = dtype == NTF_BF16 ? 2 : 4;
     const bool last_ok = (dims[2] * es) % 16 == 0, pair_ok = (dims[1] * dims[2] * es) % 16 == 0;
-    if (!last_ok && pair_ok) {
+    if (!last_ok && (pair_ok || p->tensor_copy != -1)) {
       c->s_R = 1;
       c->P_R = dims[0];
       c->Q_R = dims[1] * dims[2];
@@ -878,14 +883,41 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
     e = cudaMemsetAsync(c->Wu, 0, wu_bytes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->Wu_b, 0, wub_bytes, c->st);
     if (e == cudaSuccess) {
-      const bool okn = ntf::umma_plan(&c->un, false, dtype, d_tensor, c->P_R, c->Q_R, R, c->Wu,
-                                      c->num_sms);
+      // Copies of the tensor (params.tensor_copy), context-owned: a row-padded copy of
+      // X[P_R, Q_R] when its rows are not 16-byte multiples, and the transposed copy
+      // [Q_L, P_L] (rows padded likewise) for the second contraction.  Each is made only if
+      // it takes at most half the free device memory (any size for tensor_copy = 1).
+      const int64_t es = dtype == NTF_BF16 ? 2 : 4, al = 16 / es;
+      const bool copies = p->tensor_copy != -1 && R <= 64;
+      const auto fits = [&](size_t bytes) {
+        size_t free_b = 0, total_b = 0;
+        return p->tensor_copy == 1 ||
+               (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && bytes <= free_b / 2);
+      };
+      const void* xn = d_tensor;
+      int64_t ldn = c->Q_R;
+      if ((c->Q_R * es) % 16 != 0 && copies) {
+        const int64_t qp = (c->Q_R + al - 1) / al * al;
+        const size_t bytes = static_cast<size_t>(c->P_R * qp * es);
+        if (fits(bytes) && cudaMalloc(&c->Xp, bytes) == cudaSuccess) {
+          e = ntf::launch_pad_rows(d_tensor, static_cast<int>(es), c->P_R, c->Q_R, c->Xp, qp,
+                                   c->st);
+          xn = c->Xp;
+          ldn = qp;
+          c->copy_bytes += static_cast<int64_t>(bytes);
+        } else {
+          cudaGetLastError();  // no room: the first contraction runs on the FMA kernels
+          c->Xp = nullptr;
+        }
+      }
+      const bool okn = e == cudaSuccess && ntf::umma_plan(&c->un, false, dtype, xn, c->P_R,
+                                                          c->Q_R, R, c->Wu, c->num_sms, ldn);
       // the second contraction X[P_L, Q_L]^T W: on the transposed copy [Q_L, P_L] (a K-major
-      // product, params.tensor_copy) when there is one, else on X with M-contiguous tiles
-      const int64_t es = dtype == NTF_BF16 ? 2 : 4;
-      const bool copy_ok = (c->P_L * es) % 16 == 0 && R <= 64;
-      bool copy = copy_ok && (p->tensor_copy == 1 || (p->tensor_copy == 0 && dtype != NTF_BF16));
-      if (copy_ok && p->tensor_copy == 0 && dtype == NTF_BF16) {
+      // product) when there is one, else on X with M-contiguous tiles, which needs rows of X
+      // that are 16-byte multiples
+      const bool direct_ok = (c->Q_L * es) % 16 == 0;
+      bool copy = copies && (!direct_ok || p->tensor_copy == 1 || dtype != NTF_BF16);
+      if (copies && direct_ok && p->tensor_copy == 0 && dtype == NTF_BF16) {
         // BF16: the row-major product on the copy is the faster one for a single-chunk
         // contraction with N = 32 and the table streamed through the stages; the
         // M-contiguous one is faster at N = 64 and when the range is cut into chunks
@@ -894,28 +926,36 @@ ntf_status ntf_create(ntf_ctx** out, int order, const int64_t* dims, int rank, i
                               c->num_sms) &&
                probe.N == 32 && probe.args.chunks == 1 && !probe.wres;
       }
-      if (copy) {
-        size_t free_b = 0, total_b = 0;
-        const size_t bytes = static_cast<size_t>(c->numel * es);
-        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
-            (p->tensor_copy == 1 || bytes <= free_b / 2)) {
-          if (cudaMalloc(&c->Xt, bytes) != cudaSuccess) {
-            cudaGetLastError();  // no room: the contraction runs on X
-            c->Xt = nullptr;
-          }
+      int64_t ldt = c->P_L;
+      if (copy && e == cudaSuccess) {
+        ldt = (c->P_L + al - 1) / al * al;
+        const size_t bytes = static_cast<size_t>(c->Q_L * ldt * es);
+        if (fits(bytes) && cudaMalloc(&c->Xt, bytes) == cudaSuccess) {
+          e = ntf::launch_transpose(d_tensor, static_cast<int>(es), c->P_L, c->Q_L, c->Xt, c->st,
+                                    ldt);
+          c->copy_bytes += static_cast<int64_t>(bytes);
+        } else {
+          cudaGetLastError();  // no room: the contraction runs on X
+          c->Xt = nullptr;
         }
-        if (c->Xt)
-          e = ntf::launch_transpose(d_tensor, static_cast<int>(es), c->P_L, c->Q_L, c->Xt, c->st);
       }
       const bool okt = e == cudaSuccess &&
                        (c->Xt ? ntf::umma_plan(&c->ut, false, dtype, c->Xt, c->Q_L, c->P_L, R,
-                                               c->Wu_b, c->num_sms)
+                                               c->Wu_b, c->num_sms, ldt)
                               : ntf::umma_plan(&c->ut, true, dtype, d_tensor, c->P_L, c->Q_L, R,
                                                c->Wu_b, c->num_sms));
-      if (!okt && c->Xt && e == cudaSuccess) {
+      // a copy whose plan failed is not kept
+      if (e == cudaSuccess && ((!okt && c->Xt) || (!okn && c->Xp))) {
         e = cudaStreamSynchronize(c->st);
-        cudaFree(c->Xt);
-        c->Xt = nullptr;
+        if (!okt && c->Xt) {
+          cudaFree(c->Xt);
+          c->Xt = nullptr;
+        }
+        if (!okn && c->Xp) {
+          cudaFree(c->Xp);
+          c->Xp = nullptr;
+        }
+        c->copy_bytes = (c->Xt ? c->Q_L * ldt * es : 0) + (c->Xp ? c->P_R * ldn * es : 0);
       }
       if (p->contraction == NTF_CONTRACT_TENSOR && !(okn && okt)) {
         free_ctx(c);
@@ -1197,7 +1237,7 @@ ntf_status ntf_profile_get(ntf_ctx* c, ntf_profile* out) {
   out->kernel_launches = c->launches;
   out->ws_rows_considered = static_cast<int64_t>(c->h_ctrl->ws_rows[0]);
   out->ws_rows_accepted = static_cast<int64_t>(c->h_ctrl->ws_rows[1]);
-  out->tensor_copy_bytes = c->Xt ? c->numel * (c->dtype == NTF_BF16 ? 2 : 4) : 0;
+  out->tensor_copy_bytes = c->copy_bytes;
   return NTF_OK;
 }
 

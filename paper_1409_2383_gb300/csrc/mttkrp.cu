@@ -607,7 +607,7 @@ cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R,
 // grid-stride loop.  Runs once per context.
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ x, int64_t P, int64_t Q,
-                                                   T* __restrict__ y) {
+                                                   T* __restrict__ y, int64_t ldy) {
   __shared__ T tile[32][33];
   const int64_t tp = (P + 31) / 32, tq = (Q + 31) / 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ x, int6
     __syncthreads();
 #pragma unroll
     for (int i = ty; i < 32; i += 8)
-      if (q0 + i < Q && p0 + tx < P) y[(q0 + i) * P + p0 + tx] = tile[tx][i];
+      if (q0 + i < Q && p0 + tx < P) y[(q0 + i) * ldy + p0 + tx] = tile[tx][i];
     __syncthreads();
   }
 }
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ x, int6
 // written as 32-bit pairs (128 bytes per warp access on both sides).
 __global__ void __launch_bounds__(256) k_transpose_pairs(const uint32_t* __restrict__ x,
                                                          int64_t P, int64_t Q,
-                                                         uint32_t* __restrict__ y) {
+                                                         uint32_t* __restrict__ y, int64_t ldyh) {
   __shared__ uint16_t tile[64][66];
   const int64_t tp = (P + 63) / 64, tq = (Q + 63) / 64, Ph = P / 2, Qh = Q / 2;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -648,37 +648,68 @@ __global__ void __launch_bounds__(256) k_transpose_pairs(const uint32_t* __restr
     for (int i = ty; i < 64; i += 8) {  // row q0 + i of y, columns p0 + 2 tx, p0 + 2 tx + 1
       const int64_t pp = p0 / 2 + tx;
       if (q0 + i < Q && pp < Ph)
-        y[(q0 + i) * Ph + pp] =
+        y[(q0 + i) * ldyh + pp] =
             static_cast<uint32_t>(tile[2 * tx][i]) | (static_cast<uint32_t>(tile[2 * tx + 1][i]) << 16);
     }
     __syncthreads();
   }
 }
 
-cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* y,
-                             cudaStream_t st) {
-  if (P < 1 || Q < 1 || (es != 2 && es != 4)) return cudaErrorInvalidValue;
+// Padded copy of the tensor: y[p, q] = x[p, q] for q < Q, 0 for Q <= q < ldy.
+template <typename T>
+__global__ void k_pad_rows(const T* __restrict__ x, int64_t P, int64_t Q, T* __restrict__ y,
+                           int64_t ldy) {
+  const int64_t n = P * ldy;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = i / ldy, q = i - p * ldy;
+    y[i] = q < Q ? x[p * Q + q] : T(0);
+  }
+}
+
+cudaError_t launch_pad_rows(const void* x, int es, int64_t P, int64_t Q, void* y, int64_t ldy,
+                            cudaStream_t st) {
+  if (P < 1 || Q < 1 || ldy < Q || (es != 2 && es != 4)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const bool pairs = es == 2 && P % 2 == 0 && Q % 2 == 0 &&
+  const unsigned blocks =
+      static_cast<unsigned>(std::min<int64_t>((P * ldy + 255) / 256, int64_t{16} * sms));
+  if (es == 4)
+    k_pad_rows<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(x), P, Q,
+                                               static_cast<float*>(y), ldy);
+  else
+    k_pad_rows<uint16_t><<<blocks, 256, 0, st>>>(static_cast<const uint16_t*>(x), P, Q,
+                                                  static_cast<uint16_t*>(y), ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* y,
+                             cudaStream_t st, int64_t ldy) {
+  if (ldy == 0) ldy = P;
+  if (P < 1 || Q < 1 || ldy < P || (es != 2 && es != 4)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const bool pairs = es == 2 && P % 2 == 0 && Q % 2 == 0 && ldy % 2 == 0 &&
                      reinterpret_cast<uintptr_t>(x) % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 4 == 0;
   if (pairs) {
     const int64_t tiles = ((P + 63) / 64) * ((Q + 63) / 64);
     const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(tiles, int64_t{8} * sms));
     k_transpose_pairs<<<blocks, 256, 0, st>>>(static_cast<const uint32_t*>(x), P, Q,
-                                               static_cast<uint32_t*>(y));
+                                               static_cast<uint32_t*>(y), ldy / 2);
     return cudaGetLastError();
   }
   const int64_t tiles = ((P + 31) / 32) * ((Q + 31) / 32);
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(tiles, int64_t{8} * sms));
   if (es == 4)
     k_transpose<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(x), P, Q,
-                                                static_cast<float*>(y));
+                                                static_cast<float*>(y), ldy);
   else
     k_transpose<uint16_t><<<blocks, 256, 0, st>>>(static_cast<const uint16_t*>(x), P, Q,
-                                                   static_cast<uint16_t*>(y));
+                                                   static_cast<uint16_t*>(y), ldy);
   return cudaGetLastError();
 }
 

@@ -146,9 +146,14 @@ cudaError_t launch_gemm_n(const void* X, int dtype, int64_t P, int64_t Q, int R,
 cudaError_t launch_gemm_t(const void* X, int dtype, int64_t P, int64_t Q, int R, const float* W,
                           const GemmPlan& plan, float* out_or_partial, cudaStream_t st);
 // out[n] = sum_s partial[s * n + i]
-// y[Q, P] = x[P, Q]^T for elements of es = 2 or 4 bytes (the transposed tensor copy).
+// y[Q, P] = x[P, Q]^T for elements of es = 2 or 4 bytes (the transposed tensor copy), rows of
+// y ldy >= P elements apart (0: P).
 cudaError_t launch_transpose(const void* x, int es, int64_t P, int64_t Q, void* y,
-                             cudaStream_t st);
+                             cudaStream_t st, int64_t ldy = 0);
+// y[P, 0..Q) = x[P, Q], rows of y ldy >= Q elements apart, the rest of each row zero (the
+// padded tensor copy).
+cudaError_t launch_pad_rows(const void* x, int es, int64_t P, int64_t Q, void* y, int64_t ldy,
+                            cudaStream_t st);
 
 cudaError_t launch_sum_splits(const float* partial, int splits, int64_t n, float* out,
                               cudaStream_t st);
@@ -214,10 +219,10 @@ struct UmmaPlan {
   CUtensorMap tx{}, tw{};
 };
 // Plans the contraction of X viewed as [P, Q] (GEMM-T when transposed) with the split W table
-// at Wsplit (umma_wsplit_bytes bytes).  Returns false (plan.on = false) when the shape or
-// alignment does not admit the tensor-core path.
+// at Wsplit (umma_wsplit_bytes bytes); ld is the row pitch of X in elements (0: Q).  Returns
+// false (plan.on = false) when the shape or alignment does not admit the tensor-core path.
 bool umma_plan(UmmaPlan* plan, bool transposed, int dtype, const void* X, int64_t P, int64_t Q,
-               int R, void* Wsplit, int num_sms);
+               int R, void* Wsplit, int num_sms, int64_t ld = 0);
 size_t umma_wsplit_bytes(int64_t K, int R, int dtype);
 cudaError_t launch_kr_split(const Group& g, const UmmaPlan& plan, int R, void* Wsplit,
                             cudaStream_t st);

@@ -61,13 +61,15 @@ size_t umma_wsplit_bytes(int64_t K, int R, int dtype) {
 }
 
 bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P, int64_t Q,
-               int R, void* Wsplit, int num_sms) {
+               int R, void* Wsplit, int num_sms, int64_t ld) {
   *p = UmmaPlan{};
-  if (R < 1 || R > 64 || !X || !Wsplit || P < 1 || Q < 1 || num_sms < 1) return false;
+  if (ld == 0) ld = Q;
+  if (R < 1 || R > 64 || !X || !Wsplit || P < 1 || Q < 1 || ld < Q || num_sms < 1) return false;
   const bool f32 = dtype != NTF_BF16;
   const int es = f32 ? 4 : 2;
-  // TMA: 16-byte aligned base and row pitch
-  if (reinterpret_cast<uintptr_t>(X) % 16 != 0 || (Q * es) % 16 != 0) return false;
+  // TMA: 16-byte aligned base and row pitch (the tensor map's extent is Q: columns Q .. ld-1
+  // of a padded copy are never read)
+  if (reinterpret_cast<uintptr_t>(X) % 16 != 0 || (ld * es) % 16 != 0) return false;
   const int64_t M = transposed ? Q : P, K = transposed ? P : Q;
   if (M >= (int64_t{1} << 31) || K >= (int64_t{1} << 31)) return false;
   p->transposed = transposed;
@@ -111,7 +113,7 @@ bool umma_plan(UmmaPlan* p, bool transposed, int dtype, const void* X, int64_t P
   p->grid = static_cast<int>(std::min<int64_t>(tiles * chunks, ctas));
   const CUtensorMapDataType t =
       f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint64_t pitch = static_cast<uint64_t>(Q) * es;
+  const uint64_t pitch = static_cast<uint64_t>(ld) * es;
   bool ok;
   if (!transposed)  // K-major X tile: 128 rows x 128 bytes of the row
     ok = encode(&p->tx, t, X, Q, P, pitch, stage_k, 128, true);

@@ -51,7 +51,7 @@ def _problem(dims, R, seed=0, signed=False):
 
 
 SHAPES = [
-    ((13, 17, 11), 5),          # odd extents: unaligned fallback path
+    ((13, 17, 11), 5),          # odd extents: row-padded and transposed tensor copies
     ((24, 40, 36), 7),          # ragged rank, aligned rows
     ((64, 48, 40), 20),
     ((1, 5, 8), 3),             # a unit extent
@@ -131,16 +131,15 @@ def test_mttkrp_with_the_fused_second_level(ntf, dims, R, storage):
 def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
     """The second contraction X^T W on the context's transposed tensor copy (tensor_copy = 1:
     a row-major tensor-core product) and on the tensor itself (-1): every mode against the
-    oracle at the MTTKRP tolerance and the two against each other; the copy is made where the
-    leading extent is a 16-byte multiple (not for 13 x 17 x 11), as the profile reports;
-    short runs agree."""
+    oracle at the MTTKRP tolerance and the two against each other; the profile reports the
+    copies (rows padded to 16-byte multiples where the extents need it: 13 x 17 x 11, 16 x 9 x
+    7); short runs agree."""
     X, fs = _problem(dims, R, seed=11 * R + len(dims), signed=False)
     Xt = torch.as_tensor(X).to(torch.bfloat16).cuda() if storage == "bf16" else cuda(X)
     Xref = torch.as_tensor(X).to(torch.bfloat16).double().numpy() if storage == "bf16" \
         else X.astype(np.float64)
     Fd = [cuda(F) for F in fs]
     es = 2 if storage == "bf16" else 4
-    lead = dims[0] if len(dims) == 3 else dims[0] * dims[1]
     got, used = {}, {}
     for tc in (1, -1):
         with ntf.Context(Xt, R, ntf.default_params(tensor_copy=tc)) as ctx:
@@ -151,8 +150,7 @@ def test_mttkrp_on_the_transposed_copy(ntf, dims, R, storage):
             assert rel(got[tc][n], want) <= TOL, (tc, n, rel(got[tc][n], want))
     for n in range(len(dims)):
         assert rel(got[1][n], got[-1][n]) <= 4 * TOL, n
-    copied = (lead * es) % 16 == 0
-    assert used == {1: X.size * es if copied else 0, -1: 0}, used
+    assert used[-1] == 0 and used[1] >= X.size * es, used
     init = [np.random.default_rng(50 + n).random((d, R)).astype(np.float32)
             for n, d in enumerate(dims)]
     errs = {}

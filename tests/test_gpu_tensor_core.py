@@ -82,13 +82,34 @@ def test_tensor_core_mttkrp_skewed_fp32(ntf, dims, R):
     test_tensor_core_mttkrp_all_modes(ntf, dims, R, "f32")
 
 
-def test_skewed_bf16_has_no_aligned_view(ntf):
-    """BF16 I x 50 x 50: rows of 100 and 5000 bytes, neither a 16-byte multiple: the tensor
-    engine is refused (the default engine falls back to the FMA kernels)."""
-    X = torch.rand(64, 50, 50, device="cuda").to(torch.bfloat16)
-    with pytest.raises(ntf.NTFError) as ei:
-        ntf.Context(X, 4, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR))
-    assert "UNSUPPORTED" in str(ei.value)
+@pytest.mark.parametrize("dims,R", [((64, 50, 50), 4), ((300, 50, 50), 10), ((13, 17, 11), 5),
+                                    ((10, 6, 9, 7), 3)])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_unaligned_rows_run_on_padded_copies(ntf, dims, R, storage):
+    """Rows that are not 16-byte multiples in any matrix view (BF16 I x 50 x 50: 100 and 5000
+    bytes; odd extents): the tensor engine runs on the context's row-padded and transposed
+    copies of the tensor (every mode against the oracle); with the copies switched off
+    (tensor_copy = -1) it is refused where no matrix view has aligned rows (FP32 I x 50 x 50
+    has one, X[I, 2500]) and the default engine takes the FMA kernels."""
+    X, fs = _problem(dims, R, seed=sum(dims) + 7 * R)
+    Xt, Xref = _tensor(X, storage)
+    Fd = [torch.as_tensor(F).cuda() for F in fs]
+    with ntf.Context(Xt, R, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR)) as ctx:
+        assert ctx.profile_get()["tensor_copy_bytes"] >= X.size * (2 if storage == "bf16" else 4)
+        for n in range(len(dims)):
+            M = ctx.mttkrp(n, Fd).cpu().numpy()
+            want = o.mttkrp(Xref, [F.astype(np.float64) for F in fs], n)
+            assert rel(M, want) <= TOL, (n, rel(M, want))
+    es = 2 if storage == "bf16" else 4
+    trailing = [int(np.prod(dims[2:]))] if len(dims) == 4 else [dims[2], dims[1] * dims[2]]
+    if any(t * es % 16 == 0 for t in trailing):
+        ntf.Context(Xt, R, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR,
+                                              tensor_copy=-1)).close()
+    else:
+        with pytest.raises(ntf.NTFError) as ei:
+            ntf.Context(Xt, R, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR,
+                                                  tensor_copy=-1))
+        assert "UNSUPPORTED" in str(ei.value)
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
@@ -127,8 +148,9 @@ def test_skewed_run_matches_oracle(ntf):
     assert abs(rs["rel_err"] - o.rfe(X.astype(np.float64), st.aux)) <= 1e-4
 
 
-def test_tensor_engine_rejects_unaligned_rows(ntf):
+def test_tensor_engine_without_copies_rejects_unaligned_rows(ntf):
     X = torch.rand(13, 17, 11, device="cuda")
     with pytest.raises(ntf.NTFError) as ei:
-        ntf.Context(X, 4, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR))
+        ntf.Context(X, 4, ntf.default_params(contraction=ntf.NTF_CONTRACT_TENSOR,
+                                             tensor_copy=-1))
     assert "UNSUPPORTED" in str(ei.value)
