@@ -256,28 +256,41 @@ __global__ void __launch_bounds__(kPostMaxThreads<V>) k_post_fastv(const V* __re
   }
 }
 
-// The last step of the second tree level formed in the GEMM-N epilogue: one thread per
-// (a, r), the 32-row groups holding rows of a summed in increasing order.
-__global__ void k_post_part(const float* __restrict__ part, int64_t Ia, int64_t Ib, int R,
-                            float* __restrict__ out) {
-  const int64_t n = Ia * R;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t a = i / R;
-    const int r = static_cast<int>(i - a * R);
-    const int64_t g0 = (a * Ib) / 32, g1 = ((a + 1) * Ib - 1) / 32;
+// The last step of the second tree level formed in the GEMM-N epilogue: the 32-row groups
+// holding rows of a summed per row.  Each row a takes kPartWarps warps (lane = r), each the
+// sums of a quarter of its groups in increasing order, eight loads in flight; the quarters
+// are added in order 0, 1, ... through shared memory (a fixed order: deterministic).
+constexpr int kPartWarps = 4;
+__global__ void __launch_bounds__(256) k_post_part(const float* __restrict__ part, int64_t Ia,
+                                                   int64_t Ib, int R, float* __restrict__ out) {
+  __shared__ float s_sum[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp % kPartWarps;
+  const int64_t a = static_cast<int64_t>(blockIdx.x) * (8 / kPartWarps) + warp / kPartWarps;
+  float acc = 0.0f;
+  if (a < Ia && lane < R) {
+    const int64_t g0 = (a * Ib) / 32, g1 = ((a + 1) * Ib - 1) / 32, n = g1 - g0 + 1;
     // the first group may hold a's rows in its second slot; every later one in its first
-    float s = part[(g0 * 2 + (a - (g0 * 32) / Ib)) * R + r];
-    int64_t g = g0 + 1;
-    for (; g + 8 <= g1 + 1; g += 8) {  // eight independent loads in flight, added in order
-      float q[8];
+    const int64_t slot0 = a - (g0 * 32) / Ib;
+    const int64_t k0 = n * q / kPartWarps, k1 = n * (q + 1) / kPartWarps;
+    for (int64_t k = k0; k < k1; k += 8) {
+      float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) q[u] = part[((g + u) * 2) * R + r];
+      for (int u = 0; u < 8; ++u) {
+        const int64_t kk = k + u;
+        v[u] = kk < k1 ? part[((g0 + kk) * 2 + (kk == 0 ? slot0 : 0)) * R + lane] : 0.0f;
+      }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += q[u];
+      for (int u = 0; u < 8; ++u) acc += v[u];
     }
-    for (; g <= g1; ++g) s += part[(g * 2) * R + r];
-    out[i] = s;
+  }
+  s_sum[warp][lane] = acc;
+  __syncthreads();
+  if (q == 0 && a < Ia && lane < R) {
+    float t = s_sum[warp][lane];
+#pragma unroll
+    for (int j = 1; j < kPartWarps; ++j) t += s_sum[warp + j][lane];
+    out[a * R + lane] = t;
   }
 }
 
@@ -782,10 +795,11 @@ cudaError_t launch_post_fast4(const float* T, int64_t Ia, int64_t Ib, int R, con
 
 cudaError_t launch_post_part(const float* part, int64_t Ia, int64_t Ib, int R, float* out,
                              cudaStream_t st) {
-  if (Ib < 32) return cudaErrorInvalidValue;
-  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((Ia * R + 255) / 256, 4096));
+  if (R > 32 || Ia < 1 || Ib < 32) return cudaErrorInvalidValue;
+  const int64_t blocks = (Ia + 8 / kPartWarps - 1) / (8 / kPartWarps);
+  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
   prefer_shared_carveout<k_post_part>();
-  k_post_part<<<std::max(blocks, 1u), 256, 0, st>>>(part, Ia, Ib, R, out);
+  k_post_part<<<static_cast<unsigned>(blocks), 256, 0, st>>>(part, Ia, Ib, R, out);
   return cudaGetLastError();
 }
 
